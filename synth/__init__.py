@@ -1,0 +1,149 @@
+"""Seeded synthetic models standing in for the paper's hydrodynamics snapshots.
+
+This module only builds inputs: point clouds, neighbour lists (the mesh
+pre-processing that the paper delegates to Gmsh / Delaunay / the octree), the
+physical fields on the points, and the random sample that the ray set draws.
+It contains none of the method's own arithmetic and is used by both the CUDA
+path's tests/benchmark and the oracle, so neither depends on the other.
+
+A model is a dict with keys
+  pos [n,3] f64, vel [n,3] f64 (km/s), nbr_off [n+1] i64, nbr_idx [E] i32,
+  nu0 [L] f64 (Hz), chi0 [n,L], eta0 [n,L], dvw [n] (km/s), chi_c [n], eta_c [n],
+  n_freq, x_span, l_min, l_max, sample [n_sample] i32, rho [n], T [n], name.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+K_B = 1.380649e-23  # J/K
+AMU = 1.66053906660e-27  # kg
+NU_CO10 = 115.2712018e9  # Hz, CO J=1-0 (any line works: only ratios enter)
+
+
+def doppler_width(T, mass_amu=28.0):
+    """Thermal Doppler width sqrt(2kT/m) in km/s."""
+    return np.sqrt(2.0 * K_B * np.asarray(T, np.float64) / (mass_amu * AMU)) / 1e3
+
+
+def sample_indices(n: int, n_sample: int = 10000, seed: int = 0) -> np.ndarray:
+    """Uniform sample of point indices without replacement (all points if n <= n_sample)."""
+    if n <= n_sample:
+        return np.arange(n, dtype=np.int32)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5A]))
+    return np.sort(rng.choice(n, size=n_sample, replace=False)).astype(np.int32)
+
+
+def csr_from_pairs(n: int, a: np.ndarray, b: np.ndarray):
+    """Symmetric CSR (rows sorted ascending, no duplicates, no self loops)."""
+    a = np.asarray(a, np.int64)
+    b = np.asarray(b, np.int64)
+    src = np.concatenate([a, b])
+    dst = np.concatenate([b, a])
+    keep = src != dst
+    src, dst = src[keep], dst[keep]
+    key = np.unique(src * n + dst)
+    src, dst = key // n, key % n
+    off = np.zeros(n + 1, np.int64)
+    np.add.at(off, src + 1, 1)
+    off = np.cumsum(off)
+    return off, dst.astype(np.int32)
+
+
+def delaunay_csr(pos: np.ndarray):
+    """Neighbour CSR from the edges of the 3-D Delaunay tetrahedralisation."""
+    from scipy.spatial import Delaunay
+
+    tri = Delaunay(pos)
+    s = tri.simplices.astype(np.int64)
+    pairs = [(s[:, i], s[:, j]) for i in range(4) for j in range(i + 1, 4)]
+    a = np.concatenate([p[0] for p in pairs])
+    b = np.concatenate([p[1] for p in pairs])
+    return csr_from_pairs(len(pos), a, b)
+
+
+def grid_csr(m: int):
+    """26-neighbour CSR of an m^3 Cartesian grid, point id = (i*m + j)*m + k."""
+    idx = np.arange(m ** 3).reshape(m, m, m)
+    a_list, b_list = [], []
+    for di in (-1, 0, 1):
+        for dj in (-1, 0, 1):
+            for dk in (-1, 0, 1):
+                if di == dj == dk == 0:
+                    continue
+                src = idx[max(0, -di):m - max(0, di), max(0, -dj):m - max(0, dj),
+                          max(0, -dk):m - max(0, dk)].ravel()
+                a_list.append(src)
+                b_list.append(src + (di * m + dj) * m + dk)
+    return csr_from_pairs(m ** 3, np.concatenate(a_list), np.concatenate(b_list))
+
+
+def grid_model(m: int = 16, chi_line: float = 5.0, n_freq: int = 31, x_span: float = 4.0,
+               level: int = 0, floor: float = 1e-10):
+    """Homogeneous static cube: m^3 grid points x = i/(m-1), 26 neighbours, one line of
+    width 1 km/s, line-centre optical depth chi_line across the unit cube, S = 1
+    everywhere (the continuum floor has S = 1 too), no velocity."""
+    g = np.arange(m, dtype=np.float64) / (m - 1)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    n = len(pos)
+    off, nbr = grid_csr(m)
+    chi0 = np.full((n, 1), chi_line)
+    return dict(
+        name=f"grid{m}", pos=pos, vel=np.zeros((n, 3)), nbr_off=off, nbr_idx=nbr,
+        nu0=np.array([NU_CO10]), chi0=chi0, eta0=chi0.copy(), dvw=np.ones(n),
+        chi_c=np.full(n, floor * chi_line), eta_c=np.full(n, floor * chi_line),
+        n_freq=n_freq, x_span=x_span, l_min=level, l_max=level,
+        sample=sample_indices(n), rho=np.ones(n), T=np.full(n, 2000.0))
+
+
+def wind_model(n: int = 50000, seed: int = 2, n_freq: int = 50, x_span: float = 4.0,
+               level: int = 2, l_min: int | None = None, tau_radial: float = 10.0,
+               v_inf: float = 15.0, cont_frac: float = 1e-4, n_sample: int = 10000):
+    """Spherical stellar wind, r in [1, 100] stellar radii log-uniform (so the point
+    density falls as r^-3 and the element size grows as r), isotropic directions.
+    Density ~ r^-2, beta-law radial velocity v = v_inf (1 - 1/r)^0.5, temperature
+    T = 2000 K r^-0.7, CO-like thermal width, line-centre opacity ~ density scaled
+    to a radial line-centre optical depth tau_radial (static), line source function
+    S = T / 2000 K, weak continuum with the same source function."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x57]))
+    r = np.exp(rng.uniform(0.0, np.log(100.0), n))
+    mu = rng.uniform(-1.0, 1.0, n)
+    ph = rng.uniform(0.0, 2.0 * np.pi, n)
+    st = np.sqrt(1.0 - mu * mu)
+    rhat = np.stack([st * np.cos(ph), st * np.sin(ph), mu], axis=1)
+    pos = rhat * r[:, None]
+    off, nbr = delaunay_csr(pos)
+    vel = rhat * (v_inf * np.sqrt(1.0 - 1.0 / r))[:, None]
+    T = 2000.0 * r ** -0.7
+    rho = r ** -2.0
+    k = tau_radial / (1.0 - 1.0 / 100.0)
+    chi0 = (k * rho)[:, None]
+    S = T / 2000.0
+    eta0 = chi0 * S[:, None]
+    chi_c = cont_frac * chi0[:, 0]
+    return dict(
+        name=f"wind{n}", pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr,
+        nu0=np.array([NU_CO10]), chi0=chi0, eta0=eta0, dvw=doppler_width(T),
+        chi_c=chi_c, eta_c=chi_c * S, n_freq=n_freq, x_span=x_span,
+        l_min=level if l_min is None else l_min, l_max=level,
+        sample=sample_indices(n, n_sample, seed), rho=rho, T=T)
+
+
+def random_cloud(n: int = 40, seed: int = 0, n_lines: int = 1, n_freq: int = 7,
+                 x_span: float = 3.0, l_min: int = 0, l_max: int = 0, v_rms: float = 2.0):
+    """Small random point cloud in the unit cube with Delaunay neighbours and random
+    smooth-ish fields; for brute-force checks."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xC1]))
+    pos = rng.uniform(0.0, 1.0, (n, 3))
+    off, nbr = delaunay_csr(pos)
+    vel = rng.normal(0.0, v_rms, (n, 3))
+    T = rng.uniform(500.0, 3000.0, n)
+    nu0 = NU_CO10 * (1.0 + np.arange(n_lines) * 3e-4)
+    chi0 = rng.uniform(0.5, 8.0, (n, n_lines))
+    S = rng.uniform(0.2, 1.5, (n, n_lines))
+    chi_c = rng.uniform(0.01, 0.1, n)
+    return dict(
+        name=f"cloud{n}", pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr, nu0=nu0, chi0=chi0,
+        eta0=chi0 * S, dvw=doppler_width(T), chi_c=chi_c, eta_c=chi_c * S[:, 0],
+        n_freq=n_freq, x_span=x_span, l_min=l_min, l_max=l_max,
+        sample=sample_indices(n), rho=rng.uniform(0.1, 1.0, n), T=T)
