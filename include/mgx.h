@@ -1,0 +1,212 @@
+/*
+ * mgx.h -- C ABI of the GB300 radiation-field library (libmgx.so).
+ *
+ * The library computes, for every point of a 3-D point-cloud mesh, the mean
+ * intensity J of a set of spectral lines, following De Ceuster et al. (2020),
+ * "Magritte II: adaptive ray-tracing, mesh construction and reduction":
+ *   ray set    -- hierarchical, mesh-adaptive HEALPix directions (Section 2.1.3, Eq. 4)
+ *   trace      -- point-to-point long characteristics (Section 2.1, Fig. 2)
+ *   line data  -- Doppler-shifted opacity/emissivity with adaptive velocity and
+ *                 optical-depth sampling (Sections 2.1.1-2.1.2, Eq. 2)
+ *   solve      -- second-order Feautrier transfer equation per ray pair and
+ *                 frequency bin (Eq. 1)
+ *   J          -- direction-weighted mean intensity (Eq. 3)
+ *   reduction  -- the re-meshing criterion of Section 2.2.2 (Eqs. 6-8, Table 1)
+ *
+ * Conventions for every call:
+ *   - Every function returns an mgx_status; 0 is success, negative is an error.
+ *     A failing call leaves outputs undefined and stores a message retrievable
+ *     with mgx_last_error().  No function throws or aborts.
+ *   - Arguments are validated on the host before anything is launched.
+ *   - Input arrays are host pointers unless stated otherwise; the library copies
+ *     them, the caller keeps ownership.  Device memory allocated by the library
+ *     belongs to the context and is released by mgx_free_model / mgx_destroy.
+ *   - All work is enqueued on the CUDA stream given to mgx_create.  Calls that
+ *     return host results synchronise that stream; calls with device outputs do
+ *     not (the caller orders further work on the same stream).
+ *   - A context is not thread-safe: use one context per host thread.
+ *   - Array layouts are C order; [n][3] means 3 consecutive values per point.
+ */
+#ifndef MGX_H
+#define MGX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mgx_ctx mgx_ctx;
+typedef int32_t mgx_status;
+
+enum {
+    MGX_OK = 0,
+    MGX_EINVAL = -1, /* bad argument (null pointer, size, index out of range, NaN) */
+    MGX_ENOMEM = -2, /* device allocation failed                                   */
+    MGX_ECUDA = -3,  /* CUDA runtime error (message has the CUDA error string)     */
+    MGX_ESTATE = -4, /* call out of order (e.g. solve before set_lines)            */
+    MGX_ERANGE = -6  /* a size limit was exceeded (message says which)             */
+};
+
+/* arithmetic forms of the formal solution */
+enum {
+    MGX_FP64 = 0, /* plain form: every step in double precision                    */
+    MGX_FP32 = 1  /* single-precision bulk; double only for the distance increments
+                     along the ray and the compensated J sum                        */
+};
+
+/* Limits. */
+#define MGX_MAX_LINES 8      /* spectral lines per model                          */
+#define MGX_MAX_LEVEL 8      /* HEALPix level of a fixed ray set (nside 256)      */
+#define MGX_MAX_ADAPT_LEVEL 5 /* finest level of an adaptive ray set (nside 32)   */
+
+typedef struct {
+    double dtau_max;       /* Eq. 2: largest optical-depth increment (> 0)              */
+    double dv_max;         /* Section 2.1.1: largest change of projected velocity between
+                              consecutive samples, in units of the smaller of their two
+                              Doppler widths; <= 0 disables velocity sampling             */
+    double I_bdy;          /* intensity entering both ends of every ray                  */
+    int32_t precision;     /* MGX_FP64 or MGX_FP32                                       */
+    int32_t out_on_device; /* nonzero: J_out is a device pointer on the context's device */
+} mgx_solve_params;
+
+/* Create a context on CUDA device `device`, enqueuing on `stream` (a cudaStream_t;
+ * NULL selects the legacy default stream). */
+mgx_status mgx_create(int device, void *stream, mgx_ctx **out);
+
+/* Release the context and every model in it.  NULL is allowed. */
+void mgx_destroy(mgx_ctx *ctx);
+
+/* Message of the last failing call on this context ("" if none).  The pointer
+ * stays valid until the next call on the context. */
+const char *mgx_last_error(const mgx_ctx *ctx);
+
+/* Number of ray pairs of a ray set spanning levels l_min..l_max (Section 2.1.3):
+ * 6*4^l for a fixed level; otherwise the top half of the candidate pairs is
+ * refined at each level, e.g. 276 pairs (552 rays) for l_min = 1, l_max = 4.
+ * Returns -1 for invalid levels. */
+int64_t mgx_rayset_npairs(int32_t l_min, int32_t l_max);
+
+/* Load a point cloud with its neighbour graph (Section 2.2: "a point cloud and
+ * nearest neighbour information").
+ *   n        number of points, 1 <= n < 2^31
+ *   pos      [n][3] positions (any length unit; the opacity is per that unit)
+ *   vel      [n][3] velocities in km/s
+ *   nbr_off  [n+1] CSR row offsets, nbr_off[0] = 0, non-decreasing, total < 2^31
+ *   nbr_idx  [nbr_off[n]] neighbour indices in [0, n), no self references
+ * On success *model_id receives the model handle (>= 0). */
+mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                         const int64_t *nbr_off, const int32_t *nbr_idx, int32_t *model_id);
+
+/* Release a model's device memory.  The handle becomes invalid. */
+mgx_status mgx_free_model(mgx_ctx *ctx, int32_t model);
+
+/* Line data of a model (Sections 2.1.1-2.1.2; the profile is the Gaussian of
+ * Magritte I with its normalisation folded into chi0 and eta0).
+ *   n_lines   1..MGX_MAX_LINES
+ *   nu0       [n_lines] line-centre frequencies (> 0)
+ *   chi0      [n][n_lines] line-centre opacities (>= 0)
+ *   eta0      [n][n_lines] line-centre emissivities (>= 0)
+ *   dvw       [n] Doppler widths in km/s (> 0)
+ *   chi_c     [n] continuum opacities (> 0; keeps every optical depth positive)
+ *   eta_c     [n] continuum emissivities (>= 0)
+ *   n_freq    bins per line (>= 1): bin k of line l sits at
+ *             nu = nu0[l] (1 + x_k dvw[o] / c) in the comoving frame of the origin o,
+ *             x_k uniform on [-x_span, x_span] (x_0 = 0 if n_freq == 1)
+ *   x_span    >= 0
+ * J has n_lines*n_freq values per point, index l*n_freq + k. */
+mgx_status mgx_set_lines(mgx_ctx *ctx, int32_t model, int32_t n_lines, const double *nu0,
+                         const double *chi0, const double *eta0, const double *dvw,
+                         const double *chi_c, const double *eta_c, int32_t n_freq, double x_span);
+
+/* Build the ray set of every point (Section 2.1.3, Eq. 4, Fig. 1).
+ * l_min == l_max selects the fixed HEALPix set of that level (0..MGX_MAX_LEVEL).
+ * l_min < l_max (l_max <= MGX_MAX_ADAPT_LEVEL) builds the adaptive set: the
+ * directions from the point to the sample points are counted per pixel, and at
+ * each level the top half of the candidate antipodal pairs (by count, ties to
+ * the smaller nested index) is refined.  `sample` [n_sample] holds the indices
+ * of the global sample of points (the paper draws 10 000); the point itself and
+ * coincident points are skipped.  sample may be NULL when l_min == l_max.
+ * Each ray pair is stored as (level << 28) | nested pixel of the member with
+ * the smaller index; the pair's rays point along +r and -r, r = that pixel's
+ * centre; its weight is 2/(12 * 4^level). */
+mgx_status mgx_set_rays(mgx_ctx *ctx, int32_t model, int32_t l_min, int32_t l_max,
+                        int64_t n_sample, const int32_t *sample);
+
+/* Copy the ray sets to the host: out [n][mgx_rayset_npairs(l_min, l_max)],
+ * pairs of each point sorted ascending. */
+mgx_status mgx_get_rays(mgx_ctx *ctx, int32_t model, uint32_t *out);
+
+/* Trace the ray pairs of origins [o_begin, o_end) (Section 2.1, Fig. 2): from
+ * the current point, step to the neighbour that lies strictly further along the
+ * ray and closest to it (ties to the smaller index), until there is none.
+ * Half-ray h = ((o - o_begin) * npairs + p) * 2 + s, s = 0 along -r, 1 along +r.
+ *   off_out    [2*npairs*(o_end-o_begin) + 1] host: entries of half-ray h are
+ *              [off_out[h], off_out[h+1]) in the arrays below (always written)
+ *   idx_out    [capacity] point indices in trace order (may be NULL)
+ *   Z_out      [capacity] projected distances (x_n - x_o).d, bit-exact double
+ *   delta_out  [capacity] projected velocity differences (v_n - v_o).d in km/s
+ *              (double; may be NULL)
+ * If idx_out is NULL only off_out is filled.  If capacity < off_out[last] the
+ * call fails with MGX_ERANGE after filling off_out. */
+mgx_status mgx_trace(mgx_ctx *ctx, int32_t model, int64_t o_begin, int64_t o_end,
+                     int64_t *off_out, int32_t *idx_out, double *Z_out, double *delta_out,
+                     int64_t capacity);
+
+/* Mean intensity of every point of a model (Eqs. 1-3): traces all ray pairs,
+ * samples velocities and optical depths, solves the Feautrier equation for
+ * every bin, and sums 2 w u over the pairs in ascending pair order with
+ * compensated (Neumaier) double-precision summation.
+ *   J_out  [n][n_lines*n_freq] doubles, host or device per params->out_on_device
+ * The call synchronises the stream (the tracer's total length sizes the
+ * point-list arena; device-side checks are reported before returning).  Origins
+ * are processed in chunks whose traced point lists fit a 16 GiB arena. */
+mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params, void *J_out);
+
+/* Mesh-reduction criterion of Section 2.2.2 with tracer f (Eqs. 6-8):
+ *   Gf_i  = max over neighbours n of |(f_i - f_n)/(f_i + f_n)|  (0 if f_i + f_n = 0)
+ *   L_i   = mean distance to the neighbours (0 without neighbours)
+ *   ell_i = L_i * (f_small if Gf_i >= G_thres else f_large)
+ * The Gmsh re-meshing of the paper is replaced by thinning: point i is kept if
+ * u_i < min(1, (L_i/ell_i)^3) with u_i the SplitMix64 uniform of (seed, i)
+ * (state seed + (i+1)*0x9E3779B97F4A7C15, top 53 bits), or if it has no
+ * neighbours.  f [n] host; outputs [n] host (any may be NULL except keep);
+ * *n_kept receives the number of kept points. */
+mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double f_small,
+                           double f_large, double G_thres, uint64_t seed, double *Gf, double *L,
+                           double *ell, uint8_t *keep, int64_t *n_kept);
+
+/* Kernel-level profiling.  While enabled, every kernel launch of the context is
+ * bracketed by CUDA events on the context's stream and the work counters below
+ * are accumulated on the device; mgx_profile_read synchronises the stream and
+ * returns the totals since the last mgx_profile_enable(ctx, 1). */
+enum {
+    MGX_K_RAYS = 0,        /* ray-set construction                          */
+    MGX_K_TRACE_COUNT = 1, /* tracer, counting pass                          */
+    MGX_K_SCAN = 2,        /* prefix sum of half-ray lengths                 */
+    MGX_K_TRACE_EMIT = 3,  /* tracer, emitting pass                          */
+    MGX_K_SOLVE = 4,       /* formal solution and J                          */
+    MGX_K_OTHER = 5,       /* ingest, reduction                              */
+    MGX_K_COUNT = 6
+};
+
+typedef struct {
+    double ms[MGX_K_COUNT];        /* summed device time per kernel class (ms)      */
+    int64_t launches[MGX_K_COUNT]; /* kernel launches per class                      */
+    int64_t trace_points;          /* points emitted by the tracer (emit pass)       */
+    int64_t solves;                /* (origin, ray pair, bin) Feautrier solutions     */
+    int64_t updates;               /* (bin, optical-depth sub-interval) elimination steps */
+    int64_t samples;               /* (bin, velocity sample) line-optics evaluations  */
+} mgx_profile;
+
+/* enable != 0 starts (and resets) profiling; 0 stops it. */
+mgx_status mgx_profile_enable(mgx_ctx *ctx, int32_t enable);
+
+/* Totals since profiling was enabled (synchronises the stream). */
+mgx_status mgx_profile_read(mgx_ctx *ctx, mgx_profile *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGX_H */

@@ -1,0 +1,284 @@
+"""GB300 radiation-field library (Magritte II hot path) -- Python binding.
+
+Thin ctypes marshalling over the C ABI in ``include/mgx.h``; every step of
+the method runs in the CUDA kernels of ``libmgx.so``.  PyTorch supplies the
+CUDA stream (and device tensors for device-side outputs).  There is no CPU
+fallback: if the shared library is missing or fails to load, every call raises.
+
+The functions keep the C names (``mgx_create``, ``mgx_load_mesh`` ...); the
+``Context`` class is a convenience wrapper that owns one context.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgx.so")
+
+MGX_OK, MGX_EINVAL, MGX_ENOMEM, MGX_ECUDA, MGX_ESTATE, MGX_ERANGE = 0, -1, -2, -3, -4, -6
+MGX_FP64, MGX_FP32 = 0, 1
+MGX_MAX_LINES = 8
+
+# every symbol the header declares
+ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs", "mgx_load_mesh",
+               "mgx_free_model", "mgx_set_lines", "mgx_set_rays", "mgx_get_rays", "mgx_trace",
+               "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read")
+KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
+
+
+class MgxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mgx status {status}: {msg}")
+        self.status = status
+
+
+class SolveParams(C.Structure):
+    _fields_ = [("dtau_max", C.c_double), ("dv_max", C.c_double), ("I_bdy", C.c_double),
+                ("precision", C.c_int32), ("out_on_device", C.c_int32)]
+
+
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("trace_points", C.c_int64),
+                ("solves", C.c_int64), ("updates", C.c_int64), ("samples", C.c_int64)]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+
+    return _build.build(force=force)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmgx.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmgx.so not built ({path}); run paper_2011_14998_gb300.build()")
+    L = C.CDLL(path)
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    sig = {
+        "mgx_create": (i32, [C.c_int, vp, C.POINTER(vp)]),
+        "mgx_destroy": (None, [vp]),
+        "mgx_last_error": (C.c_char_p, [vp]),
+        "mgx_rayset_npairs": (i64, [i32, i32]),
+        "mgx_load_mesh": (i32, [vp, i64, vp, vp, vp, vp, C.POINTER(i32)]),
+        "mgx_free_model": (i32, [vp, i32]),
+        "mgx_set_lines": (i32, [vp, i32, i32, vp, vp, vp, vp, vp, vp, i32, dbl]),
+        "mgx_set_rays": (i32, [vp, i32, i32, i32, i64, vp]),
+        "mgx_get_rays": (i32, [vp, i32, vp]),
+        "mgx_trace": (i32, [vp, i32, i64, i64, vp, vp, vp, vp, i64]),
+        "mgx_solve_J": (i32, [vp, i32, C.POINTER(SolveParams), vp]),
+        "mgx_reduce_mesh": (i32, [vp, i32, vp, dbl, dbl, dbl, u64, vp, vp, vp, vp, C.POINTER(i64)]),
+        "mgx_profile_enable": (i32, [vp, i32]),
+        "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a) -> C.c_void_p | None:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data)
+    return C.c_void_p(a.data_ptr())  # torch tensor (host or device)
+
+
+def _arr(a, dtype):
+    """C-contiguous numpy view/copy, or a torch tensor passed through (pinned host buffers)."""
+    if hasattr(a, "data_ptr") and not isinstance(a, np.ndarray):
+        return a.contiguous()
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _check(ctx, status: int):
+    if status != MGX_OK:
+        msg = load_library().mgx_last_error(ctx)
+        raise MgxError(status, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------ C-named wrappers
+def mgx_create(device: int = 0, stream: int | None = None) -> C.c_void_p:
+    out = C.c_void_p()
+    st = load_library().mgx_create(int(device), C.c_void_p(stream) if stream else None, C.byref(out))
+    if st != MGX_OK:
+        raise MgxError(st, "mgx_create failed (no CUDA device?)")
+    return out
+
+
+def mgx_destroy(ctx) -> None:
+    load_library().mgx_destroy(ctx)
+
+
+def mgx_last_error(ctx) -> str:
+    return load_library().mgx_last_error(ctx).decode()
+
+
+def mgx_rayset_npairs(l_min: int, l_max: int) -> int:
+    return int(load_library().mgx_rayset_npairs(int(l_min), int(l_max)))
+
+
+def mgx_load_mesh(ctx, pos, vel, nbr_off, nbr_idx) -> int:
+    pos, vel = _arr(pos, np.float64), _arr(vel, np.float64)
+    nbr_off, nbr_idx = _arr(nbr_off, np.int64), _arr(nbr_idx, np.int32)
+    mid = C.c_int32(-1)
+    n = len(pos)
+    _check(ctx, load_library().mgx_load_mesh(ctx, n, _ptr(pos), _ptr(vel), _ptr(nbr_off), _ptr(nbr_idx),
+                                             C.byref(mid)))
+    return mid.value
+
+
+def mgx_free_model(ctx, model: int) -> None:
+    _check(ctx, load_library().mgx_free_model(ctx, int(model)))
+
+
+def mgx_set_lines(ctx, model, nu0, chi0, eta0, dvw, chi_c, eta_c, n_freq, x_span) -> None:
+    nu0 = _arr(nu0, np.float64)
+    arrs = [_arr(a, np.float64) for a in (chi0, eta0, dvw, chi_c, eta_c)]
+    _check(ctx, load_library().mgx_set_lines(ctx, int(model), len(nu0), _ptr(nu0), *[_ptr(a) for a in arrs],
+                                             int(n_freq), float(x_span)))
+
+
+def mgx_set_rays(ctx, model, l_min, l_max, sample=None) -> None:
+    smp = None if sample is None else _arr(sample, np.int32)
+    ns = 0 if smp is None else len(smp)
+    _check(ctx, load_library().mgx_set_rays(ctx, int(model), int(l_min), int(l_max), ns, _ptr(smp)))
+
+
+def mgx_get_rays(ctx, model, n, npairs) -> np.ndarray:
+    out = np.empty((n, npairs), np.uint32)
+    _check(ctx, load_library().mgx_get_rays(ctx, int(model), _ptr(out)))
+    return out
+
+
+def mgx_trace(ctx, model, o_begin, o_end, npairs, with_delta=False):
+    """Returns (off [n_half+1], idx, Z, delta-or-None)."""
+    n_half = (o_end - o_begin) * npairs * 2
+    off = np.empty(n_half + 1, np.int64)
+    L = load_library()
+    _check(ctx, L.mgx_trace(ctx, int(model), int(o_begin), int(o_end), _ptr(off), None, None, None, 0))
+    tot = int(off[-1])
+    idx = np.empty(max(tot, 1), np.int32)
+    Z = np.empty(max(tot, 1), np.float64)
+    de = np.empty(max(tot, 1), np.float64) if with_delta else None
+    _check(ctx, L.mgx_trace(ctx, int(model), int(o_begin), int(o_end), _ptr(off), _ptr(idx), _ptr(Z),
+                            _ptr(de), tot))
+    return off, idx[:tot], Z[:tot], (de[:tot] if with_delta else None)
+
+
+def mgx_solve_J(ctx, model, params: SolveParams, J_out) -> None:
+    _check(ctx, load_library().mgx_solve_J(ctx, int(model), C.byref(params), _ptr(J_out)))
+
+
+def mgx_reduce_mesh(ctx, model, f, f_small, f_large, G_thres, seed):
+    f = _arr(f, np.float64)
+    n = len(f)
+    Gf, L_, ell = np.empty(n), np.empty(n), np.empty(n)
+    keep = np.empty(n, np.uint8)
+    nk = C.c_int64(0)
+    _check(ctx, load_library().mgx_reduce_mesh(ctx, int(model), _ptr(f), float(f_small), float(f_large),
+                                               float(G_thres), C.c_uint64(int(seed) & (2**64 - 1)),
+                                               _ptr(Gf), _ptr(L_), _ptr(ell), _ptr(keep), C.byref(nk)))
+    return Gf, L_, ell, keep, int(nk.value)
+
+
+def mgx_profile_enable(ctx, enable: bool = True) -> None:
+    _check(ctx, load_library().mgx_profile_enable(ctx, int(bool(enable))))
+
+
+def mgx_profile_read(ctx) -> dict:
+    p = Profile()
+    _check(ctx, load_library().mgx_profile_read(ctx, C.byref(p)))
+    return dict(ms={k: p.ms[i] for i, k in enumerate(KERNEL_CLASSES)},
+                launches={k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
+                trace_points=int(p.trace_points), solves=int(p.solves), updates=int(p.updates),
+                samples=int(p.samples))
+
+
+def solve_params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, precision=MGX_FP64, out_on_device=False):
+    return SolveParams(float(dtau_max), float(dv_max), float(I_bdy), int(precision), int(bool(out_on_device)))
+
+
+# ------------------------------------------------------------ convenience class
+class Context:
+    """One library context bound to a CUDA device and a torch stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        self.ptr = mgx_create(self.device, stream.cuda_stream)
+        self.models: dict[int, dict] = {}
+
+    def close(self):
+        if self.ptr:
+            mgx_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, m: dict, rays: bool = True, sample=None, l_min=None, l_max=None) -> int:
+        """Load a model dict (see synth) and set its lines and ray set."""
+        mid = mgx_load_mesh(self.ptr, m["pos"], m["vel"], m["nbr_off"], m["nbr_idx"])
+        mgx_set_lines(self.ptr, mid, m["nu0"], m["chi0"], m["eta0"], m["dvw"], m["chi_c"], m["eta_c"],
+                      m["n_freq"], m["x_span"])
+        info = dict(n=len(m["pos"]), L=len(m["nu0"]), F=int(m["n_freq"]))
+        self.models[mid] = info
+        if rays:
+            self.set_rays(mid, m["l_min"] if l_min is None else l_min, m["l_max"] if l_max is None else l_max,
+                          m.get("sample") if sample is None else sample)
+        return mid
+
+    def set_rays(self, mid, l_min, l_max, sample=None):
+        mgx_set_rays(self.ptr, mid, l_min, l_max, sample if l_min < l_max else None)
+        self.models[mid]["npairs"] = mgx_rayset_npairs(l_min, l_max)
+
+    def rays(self, mid) -> np.ndarray:
+        i = self.models[mid]
+        return mgx_get_rays(self.ptr, mid, i["n"], i["npairs"])
+
+    def trace(self, mid, o_begin=0, o_end=None, with_delta=False):
+        i = self.models[mid]
+        return mgx_trace(self.ptr, mid, o_begin, i["n"] if o_end is None else o_end, i["npairs"], with_delta)
+
+    def solve_J(self, mid, precision=MGX_FP64, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, out=None):
+        """J [n, L*F] float64; `out` may be a CUDA float64 tensor (device output)."""
+        i = self.models[mid]
+        if out is not None:
+            p = solve_params(dtau_max, dv_max, I_bdy, precision, out_on_device=True)
+            mgx_solve_J(self.ptr, mid, p, out)
+            return out
+        J = np.empty((i["n"], i["L"] * i["F"]), np.float64)
+        mgx_solve_J(self.ptr, mid, solve_params(dtau_max, dv_max, I_bdy, precision, False), J)
+        return J
+
+    def reduce_mesh(self, mid, f, f_small, f_large, G_thres, seed):
+        return mgx_reduce_mesh(self.ptr, mid, f, f_small, f_large, G_thres, seed)
+
+    def profile(self, enable: bool = True):
+        mgx_profile_enable(self.ptr, enable)
+
+    def profile_read(self) -> dict:
+        return mgx_profile_read(self.ptr)
+
+    def free(self, mid):
+        mgx_free_model(self.ptr, mid)
+        self.models.pop(mid, None)

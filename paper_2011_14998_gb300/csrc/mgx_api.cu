@@ -1,0 +1,771 @@
+// mgx_api.cu -- host side of the C ABI declared in include/mgx.h.
+//
+// Owns the per-context device state (models, HEALPix tables, status word),
+// validates arguments, moves data, sequences the kernels of k_*.cu and maps
+// device-side error codes to mgx_status values.  No arithmetic of the method
+// runs here except building the constant HEALPix direction/antipode tables.
+#include <cub/device/device_scan.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "mgx_internal.cuh"
+
+using namespace mgx;
+
+namespace {
+
+struct Model {
+    bool live = false;
+    int32_t n = 0;
+    int64_t E = 0;
+    // mesh
+    double *x = nullptr, *y = nullptr, *z = nullptr, *vx = nullptr, *vy = nullptr, *vz = nullptr;
+    float *vxf = nullptr, *vyf = nullptr, *vzf = nullptr;
+    int32_t *off = nullptr, *nbr = nullptr;
+    // lines
+    bool has_lines = false;
+    int32_t L = 0, F = 0;
+    double x_span = 0.0;
+    double nu0[MGX_MAX_LINES] = {};
+    double *chi0 = nullptr, *eta0 = nullptr, *dvw = nullptr, *chic = nullptr, *etac = nullptr;
+    float *chi0f = nullptr, *eta0f = nullptr, *dvwf = nullptr, *chicf = nullptr, *etacf = nullptr;
+    // rays
+    bool has_rays = false;
+    int32_t lmin = 0, lmax = 0, npairs = 0;
+    uint32_t *rays = nullptr;
+};
+
+}  // namespace
+
+struct mgx_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    std::vector<Model> models;
+    int *d_status = nullptr;
+    int *h_status = nullptr;
+    // HEALPix tables of levels 0..tab_level
+    int tab_level = -1;
+    double *dir = nullptr;    // [level_offset(tab_level+1)][3]
+    int32_t *anti = nullptr;  // [level_offset(tab_level+1)]
+    std::vector<std::vector<uint32_t>> pair_lists;  // per level, host
+    std::vector<uint32_t *> pair_lists_dev;         // per level, device
+    size_t arena_budget = size_t(16) << 30;
+    // profiling
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[MGX_K_COUNT];
+    int64_t launches[MGX_K_COUNT] = {};
+    std::vector<cudaEvent_t> event_pool;
+    unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples
+    int64_t trace_points = 0, solves = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+mgx_status fail(mgx_ctx *c, mgx_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return code;
+}
+
+#define CK(call)                                                                                       \
+    do {                                                                                               \
+        cudaError_t e_ = (call);                                                                       \
+        if (e_ != cudaSuccess) {                                                                       \
+            cudaGetLastError();                                                                        \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? MGX_ENOMEM : MGX_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                            \
+        }                                                                                              \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(mgx_ctx *ctx, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMallocAsync(reinterpret_cast<void **>(p), count * sizeof(T), ctx->stream);
+}
+
+template <typename T>
+void dfree(mgx_ctx *ctx, T *&p) {
+    if (p) cudaFreeAsync(p, ctx->stream);
+    p = nullptr;
+}
+
+const char *dev_err_text(int code) {
+    switch (code) {
+        case kDevBadCsr: return "neighbour graph invalid (offsets not monotone or index out of range/self)";
+        case kDevNonFinite: return "non-finite position or velocity";
+        case kDevTraceGuard: return "tracer step guard hit";
+        case kDevTraceMismatch: return "trace emit pass disagrees with count pass";
+        case kDevSubdivLimit: return "more than 2^20 optical-depth sub-intervals in one step (dtau_max too small?)";
+        case kDevBadInput: return "line data out of range (chi0, eta0 >= 0; dvw, chi_c > 0; eta_c >= 0; finite)";
+        default: return "unknown device error";
+    }
+}
+
+// Synchronise the stream and turn a device status into an mgx_status.
+mgx_status sync_status(mgx_ctx *ctx) {
+    CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int code = *ctx->h_status;
+    if (code != 0) {
+        const mgx_status s = (code == kDevSubdivLimit || code == kDevTraceGuard) ? MGX_ERANGE : MGX_EINVAL;
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
+        cudaStreamSynchronize(ctx->stream);
+        return fail(ctx, s, "device check failed: %s", dev_err_text(code));
+    }
+    return MGX_OK;
+}
+
+cudaEvent_t take_event(mgx_ctx *c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Counts a kernel launch of class `slot` and, while profiling, brackets it
+// with CUDA events on the context's stream.
+struct Timed {
+    mgx_ctx *c;
+    int slot;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timed(mgx_ctx *c_, int slot_) : c(c_), slot(slot_) {
+        c->launches[slot] += 1;
+        if (c->prof) {
+            a = take_event(c);
+            b = take_event(c);
+            if (a && b) cudaEventRecord(a, c->stream);
+        }
+    }
+    ~Timed() {
+        if (a && b) {
+            cudaEventRecord(b, c->stream);
+            c->ev[slot].emplace_back(a, b);
+        }
+    }
+};
+
+void reset_profile(mgx_ctx *c) {
+    for (auto &v : c->ev) {
+        for (auto &pr : v) {
+            c->event_pool.push_back(pr.first);
+            c->event_pool.push_back(pr.second);
+        }
+        v.clear();
+    }
+    for (auto &l : c->launches) l = 0;
+    c->trace_points = 0;
+    c->solves = 0;
+    if (c->d_counters) cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream);
+}
+
+Model *get_model(mgx_ctx *ctx, int32_t id) {
+    if (id < 0 || size_t(id) >= ctx->models.size() || !ctx->models[id].live) return nullptr;
+    return &ctx->models[id];
+}
+
+DevMesh mesh_view(const Model &m) {
+    DevMesh d;
+    d.n = m.n;
+    d.x = m.x; d.y = m.y; d.z = m.z;
+    d.vx = m.vx; d.vy = m.vy; d.vz = m.vz;
+    d.vxf = m.vxf; d.vyf = m.vyf; d.vzf = m.vzf;
+    d.off = m.off;
+    d.nbr = m.nbr;
+    return d;
+}
+
+DevLines lines_view(const Model &m) {
+    DevLines d;
+    d.L = m.L;
+    d.F = m.F;
+    d.x_span = m.x_span;
+    for (int i = 0; i < MGX_MAX_LINES * MGX_MAX_LINES; ++i) d.ratio[i] = 1.0;
+    for (int l = 0; l < m.L; ++l)
+        for (int lp = 0; lp < m.L; ++lp) d.ratio[l * MGX_MAX_LINES + lp] = m.nu0[l] / m.nu0[lp];
+    d.chi0 = m.chi0; d.eta0 = m.eta0; d.dvw = m.dvw; d.chic = m.chic; d.etac = m.etac;
+    d.chi0f = m.chi0f; d.eta0f = m.eta0f; d.dvwf = m.dvwf; d.chicf = m.chicf; d.etacf = m.etacf;
+    return d;
+}
+
+DevRays rays_view(const mgx_ctx *ctx, const Model &m) {
+    DevRays r;
+    r.lmin = m.lmin;
+    r.lmax = m.lmax;
+    r.npairs = m.npairs;
+    r.rays = m.rays;
+    r.dir = ctx->dir;
+    return r;
+}
+
+// HEALPix direction and antipode tables up to `level`, plus the sorted list of
+// pair representatives (the member with the smaller index) of every level.
+mgx_status ensure_tables(mgx_ctx *ctx, int level) {
+    if (level <= ctx->tab_level) return MGX_OK;
+    const int64_t total = level_offset(level + 1);
+    std::vector<double> dir(size_t(total) * 3);
+    std::vector<int32_t> anti(static_cast<size_t>(total));
+    std::vector<std::vector<uint32_t>> lists(size_t(level) + 1);
+    for (int l = 0; l <= level; ++l) {
+        const int64_t np = hpx_npix(l), base = level_offset(l);
+        for (int64_t p = 0; p < np; ++p) {
+            double v[3];
+            hpx_pix2vec(l, p, v);
+            dir[size_t(base + p) * 3 + 0] = v[0];
+            dir[size_t(base + p) * 3 + 1] = v[1];
+            dir[size_t(base + p) * 3 + 2] = v[2];
+            const double w[3] = {-v[0], -v[1], -v[2]};
+            anti[size_t(base + p)] = int32_t(hpx_vec2pix(l, w));
+        }
+        for (int64_t p = 0; p < np; ++p) {
+            const int64_t a = anti[size_t(base + p)];
+            if (a == p || anti[size_t(base + a)] != p)
+                return fail(ctx, MGX_ECUDA, "internal: HEALPix antipode table inconsistent at level %d", l);
+            if (p < a) lists[size_t(l)].push_back(uint32_t(p));
+        }
+    }
+    double *ddir = nullptr;
+    int32_t *danti = nullptr;
+    CK(dalloc(ctx, &ddir, dir.size()));
+    CK(dalloc(ctx, &danti, anti.size()));
+    CK(cudaMemcpyAsync(ddir, dir.data(), dir.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(danti, anti.data(), anti.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<uint32_t *> dl(size_t(level) + 1, nullptr);
+    for (int l = 0; l <= level; ++l) {
+        CK(dalloc(ctx, &dl[size_t(l)], lists[size_t(l)].size()));
+        CK(cudaMemcpyAsync(dl[size_t(l)], lists[size_t(l)].data(), lists[size_t(l)].size() * sizeof(uint32_t),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    dfree(ctx, ctx->dir);
+    dfree(ctx, ctx->anti);
+    for (auto *p : ctx->pair_lists_dev) dfree(ctx, p);
+    ctx->dir = ddir;
+    ctx->anti = danti;
+    ctx->pair_lists = std::move(lists);
+    ctx->pair_lists_dev = std::move(dl);
+    ctx->tab_level = level;
+    return MGX_OK;
+}
+
+void free_lines(mgx_ctx *ctx, Model &m) {
+    dfree(ctx, m.chi0); dfree(ctx, m.eta0); dfree(ctx, m.dvw); dfree(ctx, m.chic); dfree(ctx, m.etac);
+    dfree(ctx, m.chi0f); dfree(ctx, m.eta0f); dfree(ctx, m.dvwf); dfree(ctx, m.chicf); dfree(ctx, m.etacf);
+    m.has_lines = false;
+}
+
+void free_model(mgx_ctx *ctx, Model &m) {
+    dfree(ctx, m.x); dfree(ctx, m.y); dfree(ctx, m.z);
+    dfree(ctx, m.vx); dfree(ctx, m.vy); dfree(ctx, m.vz);
+    dfree(ctx, m.vxf); dfree(ctx, m.vyf); dfree(ctx, m.vzf);
+    dfree(ctx, m.off); dfree(ctx, m.nbr);
+    free_lines(ctx, m);
+    dfree(ctx, m.rays);
+    m.has_rays = false;
+    m.live = false;
+}
+
+// inclusive prefix sum of n int64 values: out[i] = sum in[0..i]
+mgx_status scan_i64(mgx_ctx *ctx, const int64_t *in, int64_t *out, int64_t n) {
+    size_t tmp_bytes = 0;
+    CK(cub::DeviceScan::InclusiveSum(nullptr, tmp_bytes, in, out, n, ctx->stream));
+    void *tmp = nullptr;
+    CK(cudaMallocAsync(&tmp, tmp_bytes ? tmp_bytes : 1, ctx->stream));
+    CK(cub::DeviceScan::InclusiveSum(tmp, tmp_bytes, in, out, n, ctx->stream));
+    CK(cudaFreeAsync(tmp, ctx->stream));
+    return MGX_OK;
+}
+
+// Trace lengths of every half-ray of origins [o0, o1) and their offsets:
+// offs[0] = 0, offs[h+1] = offs[h] + length(h).
+mgx_status trace_offsets(mgx_ctx *ctx, Model &m, int32_t o0, int32_t o1, int64_t **offs_out) {
+    const int64_t n_half = int64_t(o1 - o0) * m.npairs * 2;
+    int64_t *lens = nullptr, *offs = nullptr;
+    CK(dalloc(ctx, &lens, size_t(n_half)));
+    CK(dalloc(ctx, &offs, size_t(n_half + 1)));
+    CK(cudaMemsetAsync(offs, 0, sizeof(int64_t), ctx->stream));
+    {
+        Timed t(ctx, MGX_K_TRACE_COUNT);
+        launch_trace_count(mesh_view(m), rays_view(ctx, m), o0, o1, lens, ctx->d_status, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    if (n_half > 0) {
+        Timed t(ctx, MGX_K_SCAN);
+        const mgx_status s = scan_i64(ctx, lens, offs + 1, n_half);
+        if (s != MGX_OK) return s;
+    }
+    dfree(ctx, lens);
+    *offs_out = offs;
+    return MGX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mgx_status mgx_create(int device, void *stream, mgx_ctx **out) {
+    if (!out) return MGX_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return MGX_EINVAL;
+    }
+    std::unique_ptr<mgx_ctx> c(new mgx_ctx());
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    mgx_ctx *ctx = c.get();
+    DeviceGuard g(device);
+    if (!g.ok) return MGX_ECUDA;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;  // keep freed stream-ordered memory cached in the process
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    CK(cudaMalloc(&c->d_status, sizeof(int)));
+    CK(cudaMemset(c->d_status, 0, sizeof(int)));
+    CK(cudaMallocHost(&c->h_status, sizeof(int)));
+    CK(cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_counters, 0, 2 * sizeof(unsigned long long)));
+    *out = c.release();
+    return MGX_OK;
+}
+
+void mgx_destroy(mgx_ctx *ctx) {
+    if (!ctx) return;
+    {
+        DeviceGuard g(ctx->device);
+        for (auto &m : ctx->models)
+            if (m.live) free_model(ctx, m);
+        dfree(ctx, ctx->dir);
+        dfree(ctx, ctx->anti);
+        for (auto *p : ctx->pair_lists_dev) dfree(ctx, p);
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(ctx->d_status);
+        cudaFreeHost(ctx->h_status);
+        cudaFree(ctx->d_counters);
+        reset_profile(ctx);
+        for (auto e : ctx->event_pool) cudaEventDestroy(e);
+        cudaGetLastError();
+    }
+    delete ctx;
+}
+
+const char *mgx_last_error(const mgx_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t mgx_rayset_npairs(int32_t l_min, int32_t l_max) {
+    if (l_min < 0 || l_max < l_min || l_max > MGX_MAX_LEVEL) return -1;
+    if (l_min < l_max && l_max > MGX_MAX_ADAPT_LEVEL) return -1;
+    return rayset_npairs(l_min, l_max);
+}
+
+mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const double *vel,
+                         const int64_t *nbr_off, const int32_t *nbr_idx, int32_t *model_id) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!pos || !vel || !nbr_off || !model_id) return fail(ctx, MGX_EINVAL, "load_mesh: null pointer");
+    if (n < 1 || n >= (int64_t(1) << 31)) return fail(ctx, MGX_EINVAL, "load_mesh: n = %lld out of range", (long long)n);
+    if (nbr_off[0] != 0) return fail(ctx, MGX_EINVAL, "load_mesh: nbr_off[0] must be 0");
+    const int64_t E = nbr_off[n];
+    if (E < 0 || E >= (int64_t(1) << 31)) return fail(ctx, MGX_EINVAL, "load_mesh: edge count %lld out of range", (long long)E);
+    if (E > 0 && !nbr_idx) return fail(ctx, MGX_EINVAL, "load_mesh: null nbr_idx");
+    DeviceGuard g(ctx->device);
+    Model m;
+    m.n = int32_t(n);
+    m.E = E;
+    double *pos_d = nullptr, *vel_d = nullptr;
+    int64_t *off64 = nullptr;
+    CK(dalloc(ctx, &pos_d, size_t(3 * n)));
+    CK(dalloc(ctx, &vel_d, size_t(3 * n)));
+    CK(dalloc(ctx, &off64, size_t(n + 1)));
+    CK(dalloc(ctx, &m.x, size_t(n))); CK(dalloc(ctx, &m.y, size_t(n))); CK(dalloc(ctx, &m.z, size_t(n)));
+    CK(dalloc(ctx, &m.vx, size_t(n))); CK(dalloc(ctx, &m.vy, size_t(n))); CK(dalloc(ctx, &m.vz, size_t(n)));
+    CK(dalloc(ctx, &m.vxf, size_t(n))); CK(dalloc(ctx, &m.vyf, size_t(n))); CK(dalloc(ctx, &m.vzf, size_t(n)));
+    CK(dalloc(ctx, &m.off, size_t(n + 1)));
+    CK(dalloc(ctx, &m.nbr, size_t(E)));
+    CK(cudaMemcpyAsync(pos_d, pos, size_t(3 * n) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(vel_d, vel, size_t(3 * n) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(off64, nbr_off, size_t(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    if (E > 0)
+        CK(cudaMemcpyAsync(m.nbr, nbr_idx, size_t(E) * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_ingest_mesh(m.n, pos_d, vel_d, off64, E, m.x, m.y, m.z, m.vx, m.vy, m.vz, m.vxf, m.vyf,
+                           m.vzf, m.off, m.nbr, ctx->d_status, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    dfree(ctx, pos_d);
+    dfree(ctx, vel_d);
+    dfree(ctx, off64);
+    m.live = true;
+    const mgx_status s = sync_status(ctx);
+    if (s != MGX_OK) {
+        free_model(ctx, m);
+        return s;
+    }
+    ctx->models.push_back(m);
+    *model_id = int32_t(ctx->models.size() - 1);
+    return MGX_OK;
+}
+
+mgx_status mgx_free_model(mgx_ctx *ctx, int32_t model) {
+    if (!ctx) return MGX_EINVAL;
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "free_model: no model %d", model);
+    DeviceGuard g(ctx->device);
+    free_model(ctx, *m);
+    return MGX_OK;
+}
+
+mgx_status mgx_set_lines(mgx_ctx *ctx, int32_t model, int32_t n_lines, const double *nu0,
+                         const double *chi0, const double *eta0, const double *dvw,
+                         const double *chi_c, const double *eta_c, int32_t n_freq, double x_span) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "set_lines: no model %d", model);
+    if (n_lines < 1 || n_lines > MGX_MAX_LINES) return fail(ctx, MGX_EINVAL, "set_lines: n_lines = %d not in 1..%d", n_lines, MGX_MAX_LINES);
+    if (!nu0 || !chi0 || !eta0 || !dvw || !chi_c || !eta_c) return fail(ctx, MGX_EINVAL, "set_lines: null pointer");
+    if (n_freq < 1 || int64_t(n_freq) * n_lines > (int64_t(1) << 20)) return fail(ctx, MGX_EINVAL, "set_lines: n_freq = %d out of range", n_freq);
+    if (!std::isfinite(x_span) || x_span < 0.0) return fail(ctx, MGX_EINVAL, "set_lines: x_span must be finite and >= 0");
+    for (int l = 0; l < n_lines; ++l)
+        if (!std::isfinite(nu0[l]) || !(nu0[l] > 0.0)) return fail(ctx, MGX_EINVAL, "set_lines: nu0[%d] must be > 0", l);
+    DeviceGuard g(ctx->device);
+    free_lines(ctx, *m);
+    const size_t n = size_t(m->n), nl = n * size_t(n_lines);
+    CK(dalloc(ctx, &m->chi0, nl)); CK(dalloc(ctx, &m->eta0, nl));
+    CK(dalloc(ctx, &m->dvw, n)); CK(dalloc(ctx, &m->chic, n)); CK(dalloc(ctx, &m->etac, n));
+    CK(dalloc(ctx, &m->chi0f, nl)); CK(dalloc(ctx, &m->eta0f, nl));
+    CK(dalloc(ctx, &m->dvwf, n)); CK(dalloc(ctx, &m->chicf, n)); CK(dalloc(ctx, &m->etacf, n));
+    CK(cudaMemcpyAsync(m->chi0, chi0, nl * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(m->eta0, eta0, nl * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(m->dvw, dvw, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(m->chic, chi_c, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(m->etac, eta_c, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_ingest_lines(m->n, n_lines, m->chi0, m->eta0, m->dvw, m->chic, m->etac, m->chi0f, m->eta0f,
+                            m->dvwf, m->chicf, m->etacf, ctx->d_status, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    m->L = n_lines;
+    m->F = n_freq;
+    m->x_span = x_span;
+    for (int l = 0; l < n_lines; ++l) m->nu0[l] = nu0[l];
+    const mgx_status s = sync_status(ctx);
+    if (s != MGX_OK) {
+        free_lines(ctx, *m);
+        return s;
+    }
+    m->has_lines = true;
+    return MGX_OK;
+}
+
+mgx_status mgx_set_rays(mgx_ctx *ctx, int32_t model, int32_t l_min, int32_t l_max, int64_t n_sample,
+                        const int32_t *sample) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "set_rays: no model %d", model);
+    const int64_t np = mgx_rayset_npairs(l_min, l_max);
+    if (np < 0) return fail(ctx, MGX_EINVAL, "set_rays: levels %d..%d invalid (fixed <= %d, adaptive <= %d)", l_min, l_max, MGX_MAX_LEVEL, MGX_MAX_ADAPT_LEVEL);
+    if (int64_t(m->n) * np >= (int64_t(1) << 40)) return fail(ctx, MGX_ERANGE, "set_rays: too many rays");
+    const bool adaptive = l_min < l_max;
+    if (adaptive) {
+        if (n_sample < 0 || (n_sample > 0 && !sample)) return fail(ctx, MGX_EINVAL, "set_rays: bad sample");
+        for (int64_t s = 0; s < n_sample; ++s)
+            if (sample[s] < 0 || sample[s] >= m->n) return fail(ctx, MGX_EINVAL, "set_rays: sample[%lld] out of range", (long long)s);
+    }
+    DeviceGuard g(ctx->device);
+    mgx_status s = ensure_tables(ctx, l_max);
+    if (s != MGX_OK) return s;
+    if (!m->rays || m->npairs != np) {
+        dfree(ctx, m->rays);
+        CK(dalloc(ctx, &m->rays, size_t(m->n) * size_t(np)));
+    }
+    m->lmin = l_min;
+    m->lmax = l_max;
+    m->npairs = int32_t(np);
+    if (!adaptive) {
+        Timed t(ctx, MGX_K_RAYS);
+        launch_rays_fixed(m->n, l_min, m->npairs, ctx->pair_lists_dev[size_t(l_min)], m->rays, ctx->stream);
+        CK(cudaGetLastError());
+    } else {
+        int32_t *smp = nullptr;
+        CK(dalloc(ctx, &smp, size_t(n_sample)));
+        if (n_sample > 0)
+            CK(cudaMemcpyAsync(smp, sample, size_t(n_sample) * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        Timed t(ctx, MGX_K_RAYS);
+        launch_rays_adaptive(mesh_view(*m), l_min, l_max, m->npairs, n_sample, smp, ctx->anti,
+                             ctx->pair_lists_dev[size_t(l_min)], int32_t(ctx->pair_lists[size_t(l_min)].size()),
+                             m->rays, ctx->d_status, ctx->stream);
+        CK(cudaGetLastError());
+        dfree(ctx, smp);
+    }
+    s = sync_status(ctx);
+    m->has_rays = (s == MGX_OK);
+    return s;
+}
+
+mgx_status mgx_get_rays(mgx_ctx *ctx, int32_t model, uint32_t *out) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m || !out) return fail(ctx, MGX_EINVAL, "get_rays: bad model or null output");
+    if (!m->has_rays) return fail(ctx, MGX_ESTATE, "get_rays: set_rays not called");
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(out, m->rays, size_t(m->n) * m->npairs * sizeof(uint32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MGX_OK;
+}
+
+mgx_status mgx_trace(mgx_ctx *ctx, int32_t model, int64_t o_begin, int64_t o_end, int64_t *off_out,
+                     int32_t *idx_out, double *Z_out, double *delta_out, int64_t capacity) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "trace: no model %d", model);
+    if (!m->has_rays) return fail(ctx, MGX_ESTATE, "trace: set_rays not called");
+    if (o_begin < 0 || o_end > m->n || o_begin > o_end) return fail(ctx, MGX_EINVAL, "trace: origin range invalid");
+    if (!off_out) return fail(ctx, MGX_EINVAL, "trace: null off_out");
+    if (idx_out && !Z_out) return fail(ctx, MGX_EINVAL, "trace: Z_out required with idx_out");
+    DeviceGuard g(ctx->device);
+    const int64_t n_half = (o_end - o_begin) * m->npairs * 2;
+    int64_t *offs = nullptr;
+    mgx_status s = trace_offsets(ctx, *m, int32_t(o_begin), int32_t(o_end), &offs);
+    if (s != MGX_OK) return s;
+    CK(cudaMemcpyAsync(off_out, offs, size_t(n_half + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_status(ctx);
+    if (s != MGX_OK || !idx_out) {
+        dfree(ctx, offs);
+        return s;
+    }
+    const int64_t total = off_out[n_half];
+    if (capacity < total) {
+        dfree(ctx, offs);
+        return fail(ctx, MGX_ERANGE, "trace: capacity %lld < %lld entries", (long long)capacity, (long long)total);
+    }
+    int32_t *idx = nullptr;
+    double *Z = nullptr, *de = nullptr;
+    CK(dalloc(ctx, &idx, size_t(total)));
+    CK(dalloc(ctx, &Z, size_t(total)));
+    if (delta_out) CK(dalloc(ctx, &de, size_t(total)));
+    {
+        Timed t(ctx, MGX_K_TRACE_EMIT);
+        launch_trace_emit(mesh_view(*m), rays_view(ctx, *m), int32_t(o_begin), int32_t(o_end), offs, 0, idx, Z,
+                          de, ctx->d_status, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    if (total > 0) {
+        CK(cudaMemcpyAsync(idx_out, idx, size_t(total) * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(Z_out, Z, size_t(total) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        if (delta_out)
+            CK(cudaMemcpyAsync(delta_out, de, size_t(total) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    dfree(ctx, idx);
+    dfree(ctx, Z);
+    dfree(ctx, de);
+    dfree(ctx, offs);
+    return sync_status(ctx);
+}
+
+mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, void *J_out) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "solve_J: no model %d", model);
+    if (!p || !J_out) return fail(ctx, MGX_EINVAL, "solve_J: null params or output");
+    if (!m->has_lines) return fail(ctx, MGX_ESTATE, "solve_J: set_lines not called");
+    if (!m->has_rays) return fail(ctx, MGX_ESTATE, "solve_J: set_rays not called");
+    if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0)) return fail(ctx, MGX_EINVAL, "solve_J: dtau_max must be > 0");
+    if (!std::isfinite(p->dv_max)) return fail(ctx, MGX_EINVAL, "solve_J: dv_max must be finite");
+    if (!std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J: I_bdy must be finite");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J: unknown precision");
+    DeviceGuard g(ctx->device);
+    const int32_t n = m->n, np = m->npairs;
+    const int64_t n_half = int64_t(n) * np * 2;
+    int64_t *offs = nullptr;
+    mgx_status s = trace_offsets(ctx, *m, 0, n, &offs);
+    if (s != MGX_OK) return s;
+    // half-ray offsets at origin boundaries decide the chunks
+    std::vector<int64_t> obound(size_t(n) + 1);
+    CK(cudaMemcpy2DAsync(obound.data(), sizeof(int64_t), offs, size_t(2 * np) * sizeof(int64_t), sizeof(int64_t),
+                         size_t(n) + 1, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_status(ctx);
+    if (s != MGX_OK) {
+        dfree(ctx, offs);
+        return s;
+    }
+    const int64_t total = obound[size_t(n)];
+    const int64_t budget = int64_t(ctx->arena_budget / (sizeof(int32_t) + sizeof(double)));
+    std::vector<int32_t> cuts{0};
+    int64_t chunk_max = 0;
+    while (cuts.back() < n) {
+        const int32_t a = cuts.back();
+        int32_t b = a + 1;
+        while (b < n && obound[size_t(b) + 1] - obound[size_t(a)] <= budget) ++b;
+        chunk_max = std::max(chunk_max, obound[size_t(b)] - obound[size_t(a)]);
+        cuts.push_back(b);
+    }
+    ctx->trace_points += total;
+    ctx->solves += int64_t(n) * np * int64_t(m->L) * m->F;
+    int32_t *aidx = nullptr;
+    double *aZ = nullptr;
+    CK(dalloc(ctx, &aidx, size_t(chunk_max)));
+    CK(dalloc(ctx, &aZ, size_t(chunk_max)));
+    const int64_t NB = int64_t(m->L) * m->F;
+    double *J = nullptr;
+    if (p->out_on_device) {
+        J = static_cast<double *>(J_out);
+    } else {
+        CK(dalloc(ctx, &J, size_t(n) * size_t(NB)));
+    }
+    const DevMesh dm = mesh_view(*m);
+    const DevLines dl = lines_view(*m);
+    const DevRays dr = rays_view(ctx, *m);
+    for (size_t c = 0; c + 1 < cuts.size(); ++c) {
+        const int32_t o0 = cuts[c], o1 = cuts[c + 1];
+        const int64_t h0 = int64_t(o0) * np * 2;
+        const int64_t base = obound[size_t(o0)];
+        {
+            Timed t(ctx, MGX_K_TRACE_EMIT);
+            launch_trace_emit(dm, dr, o0, o1, offs + h0, base, aidx, aZ, nullptr, ctx->d_status, ctx->stream);
+        }
+        CK(cudaGetLastError());
+        SolveArgs a;
+        a.dtau_max = p->dtau_max;
+        a.dv_max = p->dv_max;
+        a.I_bdy = p->I_bdy;
+        a.o_begin = o0;
+        a.o_end = o1;
+        a.n_tiles = int32_t((NB + 31) / 32);
+        a.offs = offs + h0;
+        a.base = base;
+        a.idx = aidx;
+        a.Z = aZ;
+        a.J = J;
+        a.status = ctx->d_status;
+        a.counters = ctx->prof ? ctx->d_counters : nullptr;
+        {
+            Timed t(ctx, MGX_K_SOLVE);
+            launch_solve(dm, dl, dr, a, p->precision, ctx->stream);
+        }
+        CK(cudaGetLastError());
+    }
+    (void)n_half;
+    if (!p->out_on_device)
+        CK(cudaMemcpyAsync(J_out, J, size_t(n) * size_t(NB) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, aidx);
+    dfree(ctx, aZ);
+    dfree(ctx, offs);
+    if (!p->out_on_device) dfree(ctx, J);
+    return sync_status(ctx);
+}
+
+mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double f_small, double f_large,
+                           double G_thres, uint64_t seed, double *Gf, double *L, double *ell, uint8_t *keep,
+                           int64_t *n_kept) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "reduce_mesh: no model %d", model);
+    if (!f || !keep) return fail(ctx, MGX_EINVAL, "reduce_mesh: null f or keep");
+    if (!(f_small > 0.0) || !(f_large > 0.0) || !std::isfinite(f_small) || !std::isfinite(f_large) ||
+        !std::isfinite(G_thres))
+        return fail(ctx, MGX_EINVAL, "reduce_mesh: f_small, f_large must be > 0 and finite");
+    DeviceGuard g(ctx->device);
+    const size_t n = size_t(m->n);
+    double *fd = nullptr, *gd = nullptr, *ld = nullptr, *ed = nullptr;
+    uint8_t *kd = nullptr;
+    CK(dalloc(ctx, &fd, n));
+    CK(dalloc(ctx, &kd, n));
+    if (Gf) CK(dalloc(ctx, &gd, n));
+    if (L) CK(dalloc(ctx, &ld, n));
+    if (ell) CK(dalloc(ctx, &ed, n));
+    CK(cudaMemcpyAsync(fd, f, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_reduce(mesh_view(*m), fd, f_small, f_large, G_thres, seed, gd, ld, ed, kd, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(keep, kd, n, cudaMemcpyDeviceToHost, ctx->stream));
+    if (Gf) CK(cudaMemcpyAsync(Gf, gd, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (L) CK(cudaMemcpyAsync(L, ld, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ell) CK(cudaMemcpyAsync(ell, ed, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, fd); dfree(ctx, kd); dfree(ctx, gd); dfree(ctx, ld); dfree(ctx, ed);
+    const mgx_status s = sync_status(ctx);
+    if (s != MGX_OK) return s;
+    if (n_kept) {
+        int64_t k = 0;
+        for (size_t i = 0; i < n; ++i) k += keep[i] != 0;
+        *n_kept = k;
+    }
+    return MGX_OK;
+}
+
+mgx_status mgx_profile_enable(mgx_ctx *ctx, int32_t enable) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    DeviceGuard g(ctx->device);
+    reset_profile(ctx);
+    ctx->prof = enable != 0;
+    CK(cudaGetLastError());
+    return MGX_OK;
+}
+
+mgx_status mgx_profile_read(mgx_ctx *ctx, mgx_profile *out) {
+    if (!ctx || !out) return MGX_EINVAL;
+    ctx->err.clear();
+    DeviceGuard g(ctx->device);
+    unsigned long long cnt[2] = {0, 0};
+    CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memset(out, 0, sizeof *out);
+    for (int k = 0; k < MGX_K_COUNT; ++k) {
+        double ms = 0.0;
+        for (auto &pr : ctx->ev[k]) {
+            float t = 0.0f;
+            CK(cudaEventElapsedTime(&t, pr.first, pr.second));
+            ms += double(t);
+        }
+        out->ms[k] = ms;
+        out->launches[k] = ctx->launches[k];
+    }
+    out->trace_points = ctx->trace_points;
+    out->solves = ctx->solves;
+    out->updates = int64_t(cnt[0]);
+    out->samples = int64_t(cnt[1]);
+    return MGX_OK;
+}
+
+}  // extern "C"

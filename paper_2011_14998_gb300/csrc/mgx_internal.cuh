@@ -1,0 +1,115 @@
+// mgx_internal.cuh -- device-side views and launch entry points shared by the
+// CUDA translation units of libmgx.  Nothing here is part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mgx.h"
+
+namespace mgx {
+
+constexpr double kC = 299792.458;  // speed of light, km/s
+
+// First error wins; kernels report through a device status word.
+enum DevErr : int {
+    kDevOk = 0,
+    kDevBadCsr = 1,        // neighbour index out of range / offsets not monotone
+    kDevNonFinite = 2,     // NaN or inf in an input array
+    kDevTraceGuard = 3,    // a half-ray exceeded n points (cannot happen for valid input)
+    kDevTraceMismatch = 4, // emit pass disagrees with the count pass
+    kDevSubdivLimit = 5,   // more than kMaxSubdiv optical-depth sub-intervals in one step
+    kDevBadInput = 6,      // value outside its documented range
+};
+
+constexpr int kMaxSubdiv = 1 << 20;
+
+__device__ __forceinline__ void dev_fail(int *status, int code) {
+    atomicCAS(status, 0, code);
+}
+
+// HEALPix direction tables of levels 0..lmax are concatenated; level l starts at
+// pixel offset 4 (4^l - 1) (= sum of 12 4^k for k < l).
+__host__ __device__ __forceinline__ int64_t level_offset(int l) {
+    return 4 * ((int64_t(1) << (2 * l)) - 1);
+}
+
+struct DevMesh {
+    int32_t n;
+    const double *x, *y, *z;     // positions, structure of arrays
+    const double *vx, *vy, *vz;  // velocities km/s
+    const float *vxf, *vyf, *vzf;
+    const int32_t *off;  // [n+1]
+    const int32_t *nbr;  // [E]
+};
+
+struct DevLines {
+    int32_t L, F;
+    double x_span;
+    double ratio[MGX_MAX_LINES * MGX_MAX_LINES];  // nu0[l] / nu0[lp] at [l*MAX + lp]
+    const double *chi0, *eta0;  // [n][L]
+    const double *dvw, *chic, *etac;
+    const float *chi0f, *eta0f;
+    const float *dvwf, *chicf, *etacf;
+};
+
+struct DevRays {
+    int32_t lmin, lmax, npairs;
+    const uint32_t *rays;  // [n][npairs], (level << 28) | pixel
+    const double *dir;     // [level_offset(lmax+1)][3] pixel-centre unit vectors
+};
+
+struct SolveArgs {
+    double dtau_max, dv_max, I_bdy;
+    int32_t o_begin, o_end;   // origins of this chunk
+    int32_t n_tiles;          // frequency tiles of 32 bins per origin
+    const int64_t *offs;      // [2 npairs (o_end - o_begin) + 1] arena offsets (absolute)
+    int64_t base;             // offs[first half-ray of the chunk]
+    const int32_t *idx;       // arena point ids (relative to base)
+    const double *Z;          // arena projected distances
+    double *J;                // [n][L*F]
+    int *status;
+    unsigned long long *counters;  // nullable: [0] elimination updates, [1] optics samples
+};
+
+// ---- ingest (k_mesh.cu)
+void launch_ingest_mesh(int32_t n, const double *pos_aos, const double *vel_aos, const int64_t *off64,
+                        int64_t E, double *x, double *y, double *z, double *vx, double *vy,
+                        double *vz, float *vxf, float *vyf, float *vzf, int32_t *off32,
+                        const int32_t *nbr, int *status, cudaStream_t st);
+void launch_ingest_lines(int32_t n, int32_t L, const double *chi0, const double *eta0,
+                         const double *dvw, const double *chic, const double *etac, float *chi0f,
+                         float *eta0f, float *dvwf, float *chicf, float *etacf, int *status,
+                         cudaStream_t st);
+
+// ---- ray sets (k_rays.cu)
+void launch_rays_fixed(int32_t n, int32_t level, int32_t npairs, const uint32_t *pairs,
+                       uint32_t *rays, cudaStream_t st);
+void launch_rays_adaptive(const DevMesh &m, int32_t lmin, int32_t lmax, int32_t npairs,
+                          int64_t n_sample, const int32_t *sample, const int32_t *anti,
+                          const uint32_t *pairs_lmin, int32_t n_pairs_lmin, uint32_t *rays,
+                          int *status, cudaStream_t st);
+
+// ---- tracing (k_trace.cu)
+void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
+                        int64_t *lens, int *status, cudaStream_t st);
+void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
+                       const int64_t *offs, int64_t base, int32_t *idx, double *Z, double *delta,
+                       int *status, cudaStream_t st);
+
+// ---- formal solution (k_solve.cu)
+void launch_solve(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a,
+                  int precision, cudaStream_t st);
+
+// ---- reduction criterion (k_reduce.cu)
+void launch_reduce(const DevMesh &m, const double *f, double f_small, double f_large,
+                   double G_thres, uint64_t seed, double *Gf, double *L, double *ell,
+                   uint8_t *keep, cudaStream_t st);
+
+// ---- host HEALPix tables (hpx_host.cpp)
+int64_t hpx_npix(int l);
+void hpx_pix2vec(int l, int64_t p, double v[3]);
+int64_t hpx_vec2pix(int l, const double d[3]);
+int64_t rayset_npairs(int lmin, int lmax);
+
+}  // namespace mgx

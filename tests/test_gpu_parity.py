@@ -1,0 +1,254 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Ray sets and traced point lists are compared bit for bit; J of the FP64 plain
+form within 1e-10 relative and of the FP32 form within 1e-4 relative (over the
+bins where J exceeds 1e-6 of the point's maximum; absolute error bounded
+everywhere).  Sizes span several 32-bin tiles and ragged tails.
+"""
+import numpy as np
+import pytest
+
+from helpers import j_rel_err
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2011_14998_gb300 as mgx
+
+    mgx.build()
+    c = mgx.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def grid16():
+    import synth
+
+    return synth.grid_model(16)
+
+
+@pytest.fixture(scope="module")
+def wind_small():
+    import synth
+
+    return synth.wind_model(1500, seed=21, n_freq=50)
+
+
+@pytest.fixture(scope="module")
+def cloud_multi():
+    import synth
+
+    return synth.random_cloud(120, seed=3, n_lines=3, n_freq=13, x_span=3.5, l_min=0, l_max=2, v_rms=1.5)
+
+
+def _oracle(orc, m, **kw):
+    return orc.OracleModel(m, **kw)
+
+
+# ------------------------------------------------------------------ ray sets
+@pytest.mark.parametrize("lmin,lmax", [(0, 0), (2, 2), (0, 2), (1, 3), (0, 3)])
+def test_rayset_bit_exact(ctx, orc, wind_small, lmin, lmax):
+    m = wind_small
+    mid = ctx.load(m, l_min=lmin, l_max=lmax)
+    got = ctx.rays(mid)
+    ref = orc.rayset(m["pos"], lmin, lmax, m["sample"])
+    ctx.free(mid)
+    assert got.shape == ref.shape
+    assert np.array_equal(got, ref), int((got != ref).any(axis=1).sum())
+
+
+def test_rayset_adaptive_cloud_l4(ctx, orc):
+    import synth
+
+    m = synth.random_cloud(300, seed=8)
+    mid = ctx.load(m, l_min=1, l_max=4)
+    got = ctx.rays(mid)
+    ctx.free(mid)
+    assert got.shape == (300, 276)
+    assert np.array_equal(got, orc.rayset(m["pos"], 1, 4, m["sample"]))
+
+
+# ------------------------------------------------------------------ tracer
+def _trace_all_oracle(orc, om, o_begin, o_end):
+    idx, Z, off = [], [], [0]
+    for o in range(o_begin, o_end):
+        for ray in om.rays[o]:
+            d = orc.pix2vec(int(ray >> 28), int(ray & 0x0FFFFFFF))
+            for s in (-1.0, 1.0):
+                i, z = om.trace_half(o, s * d)
+                idx.append(i)
+                Z.append(z)
+                off.append(off[-1] + len(i))
+    return np.array(off), np.concatenate(idx), np.concatenate(Z)
+
+
+@pytest.mark.parametrize("which", ["grid16", "wind_small", "cloud_multi"])
+def test_trace_bit_exact(ctx, orc, which, request):
+    m = request.getfixturevalue(which)
+    mid = ctx.load(m)
+    n = len(m["pos"])
+    o1 = min(n, 400)
+    off, idx, Z, de = ctx.trace(mid, 0, o1, with_delta=True)
+    om = _oracle(orc, m, rays=ctx.rays(mid))
+    ctx.free(mid)
+    roff, ridx, rZ = _trace_all_oracle(orc, om, 0, o1)
+    assert np.array_equal(off, roff)
+    assert np.array_equal(idx, ridx)
+    assert np.array_equal(Z, rZ)  # bit-exact doubles
+    # projected velocity difference (v_n - v_o).d
+    hh = np.repeat(np.arange(len(off) - 1), np.diff(off))
+    o = hh // (2 * om.rays.shape[1])
+    sgn = np.where(hh % 2 == 0, -1.0, 1.0)
+    ray = om.rays[o, (hh // 2) % om.rays.shape[1]]
+    d = np.stack([orc.pix2vec(int(r >> 28), int(r & 0x0FFFFFFF)) for r in ray]) * sgn[:, None]
+    dv = m["vel"][idx] - m["vel"][o]
+    assert np.allclose(de, (dv * d).sum(1), rtol=0, atol=1e-12)
+
+
+# ------------------------------------------------------------------ J
+def test_grid_J_fp64_and_fp32(ctx, orc, grid16):
+    import paper_2011_14998_gb300 as mgx
+
+    m = grid16
+    mid = ctx.load(m)
+    Jg64 = ctx.solve_J(mid, precision=mgx.MGX_FP64, dtau_max=0.5)
+    Jg32 = ctx.solve_J(mid, precision=mgx.MGX_FP32, dtau_max=0.5)
+    ctx.free(mid)
+    Jo = _oracle(orc, m).solve_J(orc.params(dtau_max=0.5))
+    r64, a64 = j_rel_err(Jg64, Jo)
+    r32, a32 = j_rel_err(Jg32, Jo)
+    assert r64 < FP64_TOL and a64 < 1e-12, (r64, a64)
+    assert r32 < FP32_TOL, r32
+
+
+@pytest.mark.parametrize("dv_max", [1.0 / 3.0, 0.0])
+def test_wind_J_fp64_and_fp32(ctx, orc, wind_small, dv_max):
+    import paper_2011_14998_gb300 as mgx
+
+    m = wind_small
+    mid = ctx.load(m)
+    Jg64 = ctx.solve_J(mid, precision=mgx.MGX_FP64, dv_max=dv_max)
+    Jg32 = ctx.solve_J(mid, precision=mgx.MGX_FP32, dv_max=dv_max)
+    rays = ctx.rays(mid)
+    ctx.free(mid)
+    origins = np.arange(0, len(m["pos"]), 3)
+    Jo = _oracle(orc, m, rays=rays).solve_J(orc.params(dv_max=dv_max), origins=origins)
+    r64, _ = j_rel_err(Jg64[origins], Jo)
+    r32, _ = j_rel_err(Jg32[origins], Jo)
+    assert r64 < FP64_TOL, r64
+    assert r32 < FP32_TOL, r32
+
+
+def test_multiline_adaptive_J(ctx, orc, cloud_multi):
+    import paper_2011_14998_gb300 as mgx
+
+    m = cloud_multi
+    mid = ctx.load(m)
+    rays = ctx.rays(mid)
+    Jg64 = ctx.solve_J(mid, precision=mgx.MGX_FP64, dtau_max=0.3, I_bdy=0.2)
+    Jg32 = ctx.solve_J(mid, precision=mgx.MGX_FP32, dtau_max=0.3, I_bdy=0.2)
+    ctx.free(mid)
+    Jo = _oracle(orc, m, rays=rays).solve_J(orc.params(dtau_max=0.3, I_bdy=0.2))
+    assert Jg64.shape == (120, 39)
+    r64, _ = j_rel_err(Jg64, Jo)
+    r32, _ = j_rel_err(Jg32, Jo)
+    assert r64 < FP64_TOL, r64
+    assert r32 < FP32_TOL, r32
+
+
+def test_J_device_output_matches_host(ctx, wind_small):
+    import torch
+
+    import paper_2011_14998_gb300 as mgx
+
+    m = wind_small
+    mid = ctx.load(m)
+    Jh = ctx.solve_J(mid, precision=mgx.MGX_FP32)
+    out = torch.empty(Jh.shape, dtype=torch.float64, device="cuda")
+    ctx.solve_J(mid, precision=mgx.MGX_FP32, out=out)
+    torch.cuda.synchronize()
+    ctx.free(mid)
+    assert np.array_equal(out.cpu().numpy(), Jh)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_single_point_and_isolated_points(ctx, orc):
+    import paper_2011_14998_gb300 as mgx
+
+    one = np.ones((1, 1))
+    m = dict(pos=np.zeros((1, 3)), vel=np.zeros((1, 3)), nbr_off=np.zeros(2, np.int64),
+             nbr_idx=np.zeros(0, np.int32), nu0=np.array([1e11]), chi0=one, eta0=one, dvw=np.ones(1),
+             chi_c=np.ones(1), eta_c=np.ones(1), n_freq=5, x_span=2.0, l_min=1, l_max=1)
+    mid = ctx.load(m)
+    for prec in (mgx.MGX_FP64, mgx.MGX_FP32):
+        J = ctx.solve_J(mid, precision=prec, I_bdy=0.3)
+        assert np.allclose(J, 0.3, rtol=1e-6)  # no medium: u = I_bdy on every ray
+    ctx.free(mid)
+    # two connected points plus an isolated one
+    m2 = dict(pos=np.array([[0.0, 0, 0], [0.3, 0.1, 0.05], [3.0, 3, 3]]), vel=np.zeros((3, 3)),
+              nbr_off=np.array([0, 1, 2, 2]), nbr_idx=np.array([1, 0], np.int32), nu0=np.array([1e11]),
+              chi0=np.full((3, 1), 4.0), eta0=np.full((3, 1), 2.0), dvw=np.ones(3), chi_c=np.full(3, 0.1),
+              eta_c=np.full(3, 0.05), n_freq=4, x_span=1.0, l_min=0, l_max=0)
+    mid = ctx.load(m2)
+    Jg = ctx.solve_J(mid, precision=mgx.MGX_FP64, dtau_max=0.1)
+    rays = ctx.rays(mid)
+    ctx.free(mid)
+    Jo = orc.OracleModel(m2, rays=rays).solve_J(orc.params(dtau_max=0.1))
+    assert j_rel_err(Jg, Jo)[0] < FP64_TOL
+
+
+def test_single_bin_and_zero_span(ctx, orc):
+    import synth
+
+    import paper_2011_14998_gb300 as mgx
+
+    m = synth.random_cloud(60, seed=12, n_freq=1, x_span=0.0)
+    mid = ctx.load(m)
+    Jg = ctx.solve_J(mid, precision=mgx.MGX_FP64)
+    rays = ctx.rays(mid)
+    ctx.free(mid)
+    Jo = orc.OracleModel(m, rays=rays).solve_J(orc.params())
+    assert j_rel_err(Jg, Jo)[0] < FP64_TOL
+
+
+def test_invalid_inputs_are_rejected(ctx):
+    import paper_2011_14998_gb300 as mgx
+
+    pos = np.zeros((3, 3))
+    with pytest.raises(mgx.MgxError):  # neighbour index out of range
+        mgx.mgx_load_mesh(ctx.ptr, pos, pos, np.array([0, 1, 1, 1]), np.array([7], np.int32))
+    with pytest.raises(mgx.MgxError):  # self reference
+        mgx.mgx_load_mesh(ctx.ptr, pos, pos, np.array([0, 1, 1, 1]), np.array([0], np.int32))
+    bad = pos.copy()
+    bad[1, 1] = np.nan
+    with pytest.raises(mgx.MgxError):
+        mgx.mgx_load_mesh(ctx.ptr, bad, pos, np.array([0, 0, 0, 0]), np.zeros(0, np.int32))
+    mid = mgx.mgx_load_mesh(ctx.ptr, np.random.default_rng(0).normal(size=(3, 3)), pos, np.array([0, 0, 0, 0]),
+                            np.zeros(0, np.int32))
+    with pytest.raises(mgx.MgxError) as e:  # solve before set_lines
+        mgx.mgx_solve_J(ctx.ptr, mid, mgx.solve_params(), np.zeros((3, 1)))
+    assert e.value.status == mgx.MGX_ESTATE
+    one = np.ones((3, 1))
+    with pytest.raises(mgx.MgxError):  # negative width
+        mgx.mgx_set_lines(ctx.ptr, mid, [1e11], one, one, -one[:, 0], one[:, 0], one[:, 0], 3, 1.0)
+    with pytest.raises(mgx.MgxError):  # adaptive above the supported level
+        mgx.mgx_set_rays(ctx.ptr, mid, 0, 7, np.arange(3))
+    mgx.mgx_free_model(ctx.ptr, mid)
+
+
+# ------------------------------------------------------------------ reduction
+def test_reduce_bit_exact(ctx, orc, wind_small):
+    m = wind_small
+    mid = ctx.load(m, rays=False)
+    f = m["rho"] * np.exp(np.random.default_rng(2).normal(0, 0.4, len(m["rho"])))
+    Gf, L, ell, keep, nk = ctx.reduce_mesh(mid, f, 1.0, 2.15, 0.21, seed=77)
+    ctx.free(mid)
+    rGf, rL, rell, rkeep = orc.reduce(m["pos"], m["nbr_off"], m["nbr_idx"], f, 1.0, 2.15, 0.21, seed=77)
+    assert np.array_equal(Gf, rGf) and np.array_equal(L, rL) and np.array_equal(ell, rell)
+    assert np.array_equal(keep, rkeep) and nk == int(rkeep.sum())
