@@ -45,7 +45,8 @@ class Model(C.Structure):
 
 
 class Params(C.Structure):
-    _fields_ = [("dtau_max", C.c_double), ("dv_max", C.c_double), ("I_bdy", C.c_double)]
+    _fields_ = [("dtau_max", C.c_double), ("dv_max", C.c_double), ("I_bdy", C.c_double),
+                ("decide32", C.c_int32)]
 
 
 def lib():
@@ -66,7 +67,7 @@ def lib():
                 "orc_trace_half": (i64, [vp, i64, vp, i64, vp, vp]),
                 "orc_profile_arg": (dbl, [dbl, dbl, dbl, dbl, dbl, dbl]),
                 "orc_bin_x": (dbl, [i32, dbl, i32]),
-                "orc_subdivide": (i64, [i64, vp, vp, vp, i64, dbl, i64, vp, vp, vp]),
+                "orc_subdivide": (i64, [i64, vp, vp, vp, i64, dbl, i32, i64, vp, vp, vp]),
                 "orc_feautrier": (dbl, [i64, vp, vp, i64, dbl, vp]),
                 "orc_pair_line": (i64, [vp, vp, i64, C.c_uint32, i32, i32, i64, vp, vp, vp]),
                 "orc_vline_size": (i64, [vp, vp, i64, C.c_uint32, vp]),
@@ -201,8 +202,10 @@ class OracleModel:
         return J
 
 
-def params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0) -> Params:
-    return Params(dtau_max, dv_max, I_bdy)
+def params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, decide32=False) -> Params:
+    """decide32: take the velocity-sample count and Eq. 2's n_inter in single
+    precision, the precision in which the single-precision kernel decides them."""
+    return Params(dtau_max, dv_max, I_bdy, int(bool(decide32)))
 
 
 def feautrier(dtau, S, io, I_bdy=0.0, all_rows=False):
@@ -214,15 +217,15 @@ def feautrier(dtau, S, io, I_bdy=0.0, all_rows=False):
     return u if all_rows else uo
 
 
-def subdivide(s, chi, eta, io, dtau_max, max_pts=1 << 20):
+def subdivide(s, chi, eta, io, dtau_max, max_pts=1 << 20, decide32=False):
     s = np.ascontiguousarray(s, np.float64)
     chi = np.ascontiguousarray(chi, np.float64)
     eta = np.ascontiguousarray(eta, np.float64)
     dtau = np.empty(max_pts)
     S = np.empty(max_pts + 1)
     ioo = C.c_int64(0)
-    M = lib().orc_subdivide(len(s), _p(s), _p(chi), _p(eta), int(io), float(dtau_max), max_pts,
-                            _p(dtau), _p(S), C.byref(ioo))
+    M = lib().orc_subdivide(len(s), _p(s), _p(chi), _p(eta), int(io), float(dtau_max), int(decide32),
+                            max_pts, _p(dtau), _p(S), C.byref(ioo))
     if M < 0:
         raise ValueError("too many sub-points")
     return dtau[:M].copy(), S[:M + 1].copy(), int(ioo.value)

@@ -300,6 +300,10 @@ typedef struct {
     double dtau_max; /* Eq. 2 */
     double dv_max;   /* velocity step limit, in units of the smaller Doppler width (<= 0: off) */
     double I_bdy;    /* boundary intensity entering both ends of every ray    */
+    int32_t decide32; /* take the two integer decisions (velocity-sample count,
+                         Eq. 2's n_inter) in single precision, as the
+                         single-precision form of the solver does; everything
+                         else stays double */
 } orc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -466,10 +470,17 @@ static void build_vline(const orc_model *m, const orc_params *pr, int64_t o, con
             sample_of_point(m, id, fz[k - nb - 1], de, &cur);
         }
         if (k > 0 && pr->dv_max > 0.0) {
-            const double jump = fabs(cur.delta - prev.delta);
-            const double lim = pr->dv_max * fmin(prev.dvw, cur.dvw);
-            if (jump > lim) {
-                const int64_t parts = (int64_t)ceil(jump / lim);
+            int64_t parts = 1;
+            if (pr->decide32) {
+                const float jump = fabsf((float)cur.delta - (float)prev.delta);
+                const float lim = (float)pr->dv_max * fminf((float)prev.dvw, (float)cur.dvw);
+                if (jump > lim) parts = (int64_t)ceilf(jump / lim);
+            } else {
+                const double jump = fabs(cur.delta - prev.delta);
+                const double lim = pr->dv_max * fmin(prev.dvw, cur.dvw);
+                if (jump > lim) parts = (int64_t)ceil(jump / lim);
+            }
+            if (parts > 1) {
                 for (int64_t j = 1; j < parts; ++j) {
                     sample_lerp(L, &prev, &cur, (double)j / (double)parts, &mid);
                     vline_push(v, &mid);
@@ -511,8 +522,8 @@ static void line_optics(const orc_model *m, const orc_vline *v, double dv_o, int
  * sub-divided line, and the index of the origin.  Returns M, or -1 when the
  * line would exceed max_pts. */
 int64_t orc_subdivide(int64_t mv, const double *s, const double *chi, const double *eta,
-                      int64_t io, double dtau_max, int64_t max_pts, double *dtau, double *S,
-                      int64_t *io_out)
+                      int64_t io, double dtau_max, int32_t decide32, int64_t max_pts, double *dtau,
+                      double *S, int64_t *io_out)
 {
     int64_t M = 0;
     S[0] = eta[0] / chi[0];
@@ -520,7 +531,8 @@ int64_t orc_subdivide(int64_t mv, const double *s, const double *chi, const doub
     for (int64_t i = 0; i + 1 < mv; ++i) {
         const double ds = s[i + 1] - s[i];
         const double cmax = fmax(chi[i], chi[i + 1]);
-        int64_t ni = (int64_t)ceil(cmax * ds / dtau_max);
+        int64_t ni = decide32 ? (int64_t)ceilf((float)cmax * (float)ds / (float)dtau_max)
+                              : (int64_t)ceil(cmax * ds / dtau_max);
         if (ni < 1) ni = 1;
         if (M + ni > max_pts) return -1;
         const double h = ds / (double)ni;
@@ -546,11 +558,11 @@ int64_t orc_subdivide(int64_t mv, const double *s, const double *chi, const doub
 }
 
 static int64_t orc_subdivide_v(const orc_vline *v, const double *chi, const double *eta,
-                               double dtau_max, int64_t max_pts, double *dtau, double *S, int64_t *io)
+                               const orc_params *pr, int64_t max_pts, double *dtau, double *S, int64_t *io)
 {
     double *s = (double *)malloc(sizeof(double) * (size_t)v->m);
     for (int64_t i = 0; i < v->m; ++i) s[i] = v->p[i].s;
-    const int64_t M = orc_subdivide(v->m, s, chi, eta, v->io, dtau_max, max_pts, dtau, S, io);
+    const int64_t M = orc_subdivide(v->m, s, chi, eta, v->io, pr->dtau_max, pr->decide32, max_pts, dtau, S, io);
     free(s);
     return M;
 }
@@ -616,7 +628,7 @@ int64_t orc_pair_line(const orc_model *m, const orc_params *pr, int64_t o, uint3
     double *chi = (double *)malloc(sizeof(double) * (size_t)v.m);
     double *eta = (double *)malloc(sizeof(double) * (size_t)v.m);
     line_optics(m, &v, m->dvw[o], l, k, chi, eta);
-    const int64_t M = orc_subdivide_v(&v, chi, eta, pr->dtau_max, max_pts, dtau, S, io);
+    const int64_t M = orc_subdivide_v(&v, chi, eta, pr, max_pts, dtau, S, io);
     free(chi);
     free(eta);
     vline_free(&v);
@@ -671,8 +683,7 @@ int orc_solve_J(const orc_model *m, const orc_params *pr, int64_t n_orig, const 
                 for (int k = 0; k < F; ++k) {
                     line_optics(m, &v, m->dvw[o], l, k, chi, eta);
                     int64_t io = 0;
-                    const int64_t M = orc_subdivide_v(&v, chi, eta, pr->dtau_max, max_pts,
-                                                      dtau, S, &io);
+                    const int64_t M = orc_subdivide_v(&v, chi, eta, pr, max_pts, dtau, S, &io);
                     if (M < 0) {
                         bad = 1;
                         break;

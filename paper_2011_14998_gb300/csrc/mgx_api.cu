@@ -370,12 +370,16 @@ void mgx_destroy(mgx_ctx *ctx) {
         dfree(ctx, ctx->dir);
         dfree(ctx, ctx->anti);
         for (auto *p : ctx->pair_lists_dev) dfree(ctx, p);
+        reset_profile(ctx);  // before the counters are freed: it clears them on the stream
         cudaStreamSynchronize(ctx->stream);
-        cudaFree(ctx->d_status);
-        cudaFreeHost(ctx->h_status);
-        cudaFree(ctx->d_counters);
-        reset_profile(ctx);
         for (auto e : ctx->event_pool) cudaEventDestroy(e);
+        ctx->event_pool.clear();
+        cudaFree(ctx->d_status);
+        ctx->d_status = nullptr;
+        cudaFreeHost(ctx->h_status);
+        ctx->h_status = nullptr;
+        cudaFree(ctx->d_counters);
+        ctx->d_counters = nullptr;
         cudaGetLastError();
     }
     delete ctx;

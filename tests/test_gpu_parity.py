@@ -120,9 +120,11 @@ def test_grid_J_fp64_and_fp32(ctx, orc, grid16):
     Jg64 = ctx.solve_J(mid, precision=mgx.MGX_FP64, dtau_max=0.5)
     Jg32 = ctx.solve_J(mid, precision=mgx.MGX_FP32, dtau_max=0.5)
     ctx.free(mid)
-    Jo = _oracle(orc, m).solve_J(orc.params(dtau_max=0.5))
+    om = _oracle(orc, m)
+    Jo = om.solve_J(orc.params(dtau_max=0.5))
+    Jo32 = om.solve_J(orc.params(dtau_max=0.5, decide32=True))
     r64, a64 = j_rel_err(Jg64, Jo)
-    r32, a32 = j_rel_err(Jg32, Jo)
+    r32, a32 = j_rel_err(Jg32, Jo32)
     assert r64 < FP64_TOL and a64 < 1e-12, (r64, a64)
     assert r32 < FP32_TOL, r32
 
@@ -138,9 +140,11 @@ def test_wind_J_fp64_and_fp32(ctx, orc, wind_small, dv_max):
     rays = ctx.rays(mid)
     ctx.free(mid)
     origins = np.arange(0, len(m["pos"]), 3)
-    Jo = _oracle(orc, m, rays=rays).solve_J(orc.params(dv_max=dv_max), origins=origins)
+    om = _oracle(orc, m, rays=rays)
+    Jo = om.solve_J(orc.params(dv_max=dv_max), origins=origins)
+    Jo32 = om.solve_J(orc.params(dv_max=dv_max, decide32=True), origins=origins)
     r64, _ = j_rel_err(Jg64[origins], Jo)
-    r32, _ = j_rel_err(Jg32[origins], Jo)
+    r32, _ = j_rel_err(Jg32[origins], Jo32)
     assert r64 < FP64_TOL, r64
     assert r32 < FP32_TOL, r32
 
@@ -154,10 +158,12 @@ def test_multiline_adaptive_J(ctx, orc, cloud_multi):
     Jg64 = ctx.solve_J(mid, precision=mgx.MGX_FP64, dtau_max=0.3, I_bdy=0.2)
     Jg32 = ctx.solve_J(mid, precision=mgx.MGX_FP32, dtau_max=0.3, I_bdy=0.2)
     ctx.free(mid)
-    Jo = _oracle(orc, m, rays=rays).solve_J(orc.params(dtau_max=0.3, I_bdy=0.2))
+    om = _oracle(orc, m, rays=rays)
+    Jo = om.solve_J(orc.params(dtau_max=0.3, I_bdy=0.2))
+    Jo32 = om.solve_J(orc.params(dtau_max=0.3, I_bdy=0.2, decide32=True))
     assert Jg64.shape == (120, 39)
     r64, _ = j_rel_err(Jg64, Jo)
-    r32, _ = j_rel_err(Jg32, Jo)
+    r32, _ = j_rel_err(Jg32, Jo32)
     assert r64 < FP64_TOL, r64
     assert r32 < FP32_TOL, r32
 

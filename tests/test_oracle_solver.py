@@ -219,3 +219,14 @@ def test_J_weights_sum_to_one(orc):
     om = orc.OracleModel(m)
     J = om.solve_J(orc.params(I_bdy=0.5))
     assert np.allclose(J, 0.5, rtol=1e-12)
+
+
+def test_decision_precision_flag(orc):
+    # chi (5 + 5e-10) * ds 0.2 / dtau_max 0.5 is just above 2 in double precision
+    # (3 sub-intervals) and exactly 2 in single precision (2 sub-intervals)
+    s = np.array([0.0, 0.2])
+    chi = np.array([5.0 + 5e-10, 5.0 + 5e-10])
+    d64, _, _ = orc.subdivide(s, chi, chi, 0, 0.5)
+    d32, _, _ = orc.subdivide(s, chi, chi, 0, 0.5, decide32=True)
+    assert len(d64) == 3 and len(d32) == 2
+    assert d64.sum() == pytest.approx(d32.sum(), rel=1e-15)
