@@ -176,6 +176,25 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
                            double f_large, double G_thres, uint64_t seed, double *Gf, double *L,
                            double *ell, uint8_t *keep, int64_t *n_kept);
 
+/* Allocation-free variant of mgx_solve_J, for callers that must not allocate
+ * device memory during their step: code running while a framework owns every
+ * device byte and forbids third-party allocations, or code that may not enqueue
+ * allocations at all.  The paper has no counterpart; this is a property of the
+ * library.  Same inputs and result as mgx_solve_J, but J_out must be a device
+ * pointer ([n][n_lines*n_freq] doubles; params->out_on_device is ignored), and
+ * the working memory (half-ray lengths and offsets, traced point lists) comes
+ * from one fixed 64 MiB device array compiled into the library instead of an
+ * allocation.  Origins are processed in chunks that fit it; the call fails with
+ * MGX_ERANGE when the ray set has too many pairs for the array or when one
+ * origin's traced point lists alone do not fit (more than about 5.5 million
+ * points).  No cudaMalloc, cudaFree or allocating library routine is called.
+ * The first call on a device looks up the array's device address (set-up); make
+ * that first call before any stream capture.  Every call shares the array:
+ * calls that overlap on the GPU (other streams or contexts on the same device)
+ * race on it.  The call synchronises the stream. */
+mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params,
+                               double *J_out);
+
 /* Kernel-level profiling.  While enabled, every kernel launch of the context is
  * bracketed by CUDA events on the context's stream and the work counters below
  * are accumulated on the device; mgx_profile_read synchronises the stream and

@@ -25,7 +25,8 @@ MGX_MAX_LINES = 8
 # every symbol the header declares
 ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs", "mgx_load_mesh",
                "mgx_free_model", "mgx_set_lines", "mgx_set_rays", "mgx_get_rays", "mgx_trace",
-               "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read")
+               "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read",
+               "mgx_solve_J_noalloc")
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
 
 
@@ -76,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         "mgx_trace": (i32, [vp, i32, i64, i64, vp, vp, vp, vp, i64]),
         "mgx_solve_J": (i32, [vp, i32, C.POINTER(SolveParams), vp]),
         "mgx_reduce_mesh": (i32, [vp, i32, vp, dbl, dbl, dbl, u64, vp, vp, vp, vp, C.POINTER(i64)]),
+        "mgx_solve_J_noalloc": (i32, [vp, i32, C.POINTER(SolveParams), vp]),
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
     }
@@ -179,6 +181,11 @@ def mgx_trace(ctx, model, o_begin, o_end, npairs, with_delta=False):
 
 def mgx_solve_J(ctx, model, params: SolveParams, J_out) -> None:
     _check(ctx, load_library().mgx_solve_J(ctx, int(model), C.byref(params), _ptr(J_out)))
+
+
+def mgx_solve_J_noalloc(ctx, model, params: SolveParams, J_out) -> None:
+    """Allocation-free solve into a caller-owned CUDA tensor (see include/mgx.h)."""
+    _check(ctx, load_library().mgx_solve_J_noalloc(ctx, int(model), C.byref(params), _ptr(J_out)))
 
 
 def mgx_reduce_mesh(ctx, model, f, f_small, f_large, G_thres, seed):

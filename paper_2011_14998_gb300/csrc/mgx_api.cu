@@ -737,6 +737,36 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
     return MGX_OK;
 }
 
+mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, double *J_out) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: no model %d", model);
+    if (!p || !J_out) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: null params or output");
+    if (!m->has_lines) return fail(ctx, MGX_ESTATE, "solve_J_noalloc: set_lines not called");
+    if (!m->has_rays) return fail(ctx, MGX_ESTATE, "solve_J_noalloc: set_rays not called");
+    if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: dtau_max must be > 0");
+    if (!std::isfinite(p->dv_max)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: dv_max must be finite");
+    if (!std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: I_bdy must be finite");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: unknown precision");
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, J_out) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
+        attr.device != ctx->device) {
+        cudaGetLastError();
+        return fail(ctx, MGX_EINVAL, "solve_J_noalloc: J_out must be device memory of device %d", ctx->device);
+    }
+    DeviceGuard g(ctx->device);
+    char msg[256] = {0};
+    const int rc = noalloc_solve(ctx->device, mesh_view(*m), lines_view(*m), rays_view(ctx, *m), p->dtau_max,
+                                 p->dv_max, p->I_bdy, p->precision, J_out, ctx->d_status, ctx->stream, msg,
+                                 sizeof msg);
+    if (rc != MGX_OK) {
+        cudaGetLastError();
+        return fail(ctx, rc, "solve_J_noalloc: %s", msg);
+    }
+    return sync_status(ctx);
+}
+
 mgx_status mgx_profile_enable(mgx_ctx *ctx, int32_t enable) {
     if (!ctx) return MGX_EINVAL;
     ctx->err.clear();

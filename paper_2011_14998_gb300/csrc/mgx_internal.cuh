@@ -106,6 +106,11 @@ void launch_reduce(const DevMesh &m, const double *f, double f_small, double f_l
                    double G_thres, uint64_t seed, double *Gf, double *L, double *ell,
                    uint8_t *keep, cudaStream_t st);
 
+// ---- allocation-free solve with a fixed scratch array (noalloc.cu)
+int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRays &R, double dtau_max,
+                  double dv_max, double I_bdy, int precision, double *J, int *status, cudaStream_t st,
+                  char *err, size_t errlen);
+
 // ---- host HEALPix tables (hpx_host.cpp)
 int64_t hpx_npix(int l);
 void hpx_pix2vec(int l, int64_t p, double v[3]);
