@@ -90,7 +90,8 @@ int64_t mgx_rayset_npairs(int32_t l_min, int32_t l_max);
 /* Load a point cloud with its neighbour graph (Section 2.2: "a point cloud and
  * nearest neighbour information").
  *   n        number of points, 1 <= n < 2^31
- *   pos      [n][3] positions (any length unit; the opacity is per that unit)
+ *   pos      [n][3] positions, |coordinate| <= 1e30 (any length unit; opacities are per
+ *            that unit)
  *   vel      [n][3] velocities in km/s
  *   nbr_off  [n+1] CSR row offsets, nbr_off[0] = 0, non-decreasing, total < 2^31
  *   nbr_idx  [nbr_off[n]] neighbour indices in [0, n), no self references

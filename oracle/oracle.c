@@ -300,10 +300,11 @@ typedef struct {
     double dtau_max; /* Eq. 2 */
     double dv_max;   /* velocity step limit, in units of the smaller Doppler width (<= 0: off) */
     double I_bdy;    /* boundary intensity entering both ends of every ray    */
-    int32_t decide32; /* take the two integer decisions (velocity-sample count,
-                         Eq. 2's n_inter) in single precision, as the
-                         single-precision form of the solver does; everything
-                         else stays double */
+    int32_t decide32; /* take the two integer decisions in single precision, as
+                         the single-precision form of the solver does: the
+                         velocity-sample count as ceil(|d delta| / limit) and
+                         Eq. 2's n_inter as ceil((chi_max ds) fl32(1/dtau_max));
+                         everything else stays double */
 } orc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -531,7 +532,7 @@ int64_t orc_subdivide(int64_t mv, const double *s, const double *chi, const doub
     for (int64_t i = 0; i + 1 < mv; ++i) {
         const double ds = s[i + 1] - s[i];
         const double cmax = fmax(chi[i], chi[i + 1]);
-        int64_t ni = decide32 ? (int64_t)ceilf((float)cmax * (float)ds / (float)dtau_max)
+        int64_t ni = decide32 ? (int64_t)ceilf(((float)cmax * (float)ds) * (float)(1.0 / dtau_max))
                               : (int64_t)ceil(cmax * ds / dtau_max);
         if (ni < 1) ni = 1;
         if (M + ni > max_pts) return -1;

@@ -1,9 +1,11 @@
 """In-tree build of libmgx.so for sm_103a (nvcc, one -gencode, parallel compiles).
 
-Translation units of the tracer, ray sets and reduction are compiled without
-fused multiply-add contraction (-fmad=false) on top of their explicitly rounded
-intrinsics, and all host code without floating-point contraction, so that the
-traced rays and HEALPix tables are reproducible bit for bit.
+The ray-set and reduction translation units are compiled without fused
+multiply-add contraction (-fmad=false) on top of their explicitly rounded
+intrinsics (the tracer's double-precision path uses the same intrinsics, which
+are never contracted, while its single-precision screen may use FMA), and all
+host code without floating-point contraction, so that the traced rays and
+HEALPix tables are reproducible bit for bit.
 """
 from __future__ import annotations
 
@@ -17,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-EXACT_FP = {"k_trace.cu", "k_rays.cu", "k_reduce.cu", "hpx_host.cpp"}
+EXACT_FP = {"k_rays.cu", "k_reduce.cu", "hpx_host.cpp"}
 
 
 def _nvcc() -> str:

@@ -19,7 +19,9 @@
 //         interior row:  Fh = dtbar + D Fh,        D = 1/(1 + dt Fh), zh = D (dtbar S + zh)
 //     with Fh = F_i / dtau_i and zh = z_i / dtau_i of the textbook 1+B form, so
 //     no quantity overflows for small dtau and no difference of nearly equal
-//     numbers is formed.
+//     numbers is formed.  The boundary row is the interior row applied to the
+//     state (Fh, D, zh, dtbar) = (1, 1, I, dt/2), and one reciprocal
+//     1 / (chi (1 + dt Fh)) per row yields both D and D S = D eta / chi.
 // The two half-sweeps meet at the origin row, which gives u without back
 // substitution:  u_o = (dtbar S_o + zh- + zh+) / (dtbar + D- Fh- + D+ Fh+),
 // an empty half contributing (zh, D Fh) = (I, 1).  J accumulates 2 w u in
@@ -36,27 +38,36 @@ namespace {
 template <typename R>
 struct Ar;
 
+// Double precision (plain form): the Gaussian exp(-a^2) and Eq. 2's n_inter
+// exactly as defined, with IEEE divisions.
 template <>
 struct Ar<double> {
+    static constexpr double kArgScale = 1.0;
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
     static __device__ __forceinline__ double gauss(double a) { return exp(-(a * a)); }
-    static __device__ __forceinline__ double arg(double A, double B, double de, double dv) {
-        return (A + B * de) / dv;
+    static __device__ __forceinline__ double ninter(double cm, double hs, double dtau_max, double) {
+        return ceil(cm * hs / dtau_max);
     }
 };
 
+// Single precision: the profile constants are prescaled by sqrt(log2 e), so
+// exp(-a^2) = 2^(-a'^2) is one ex2.approx; reciprocals are rcp.approx; Eq. 2's
+// ratio is formed as (chi_max * ds) * fl32(1 / dtau_max).
 template <>
 struct Ar<float> {
+    static constexpr double kArgScale = 1.2011224087864498;  // sqrt(log2(e))
     static __device__ __forceinline__ float rcp(float x) {
         float r;
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
         return r;
     }
-    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
-    static __device__ __forceinline__ float gauss(float a) { return __expf(-(a * a)); }
-    static __device__ __forceinline__ float arg(float A, float B, float de, float dv) {
-        return (A + B * de) * rcp(dv);
+    static __device__ __forceinline__ float gauss(float a) {
+        float r;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-(a * a)));
+        return r;
+    }
+    static __device__ __forceinline__ float ninter(float cm, float hs, float, float inv_dtau_max) {
+        return ceilf((cm * hs) * inv_dtau_max);
     }
 };
 
@@ -105,143 +116,214 @@ __device__ __forceinline__ void load_sample(const Data<R> &D, int32_t L, int32_t
     }
 }
 
+// Total opacity and emissivity of a sample for this lane's bin.  Lines past
+// the model's count have chi0 = eta0 = 0 and contribute nothing.
 template <typename R, int NL>
-__device__ __forceinline__ void lerp_sample(const Sample<R, NL> &a, const Sample<R, NL> &b, R t,
-                                            Sample<R, NL> &s) {
-    s.delta = a.delta + (b.delta - a.delta) * t;
-    s.dv = a.dv + (b.dv - a.dv) * t;
-    s.chic = a.chic + (b.chic - a.chic) * t;
-    s.etac = a.etac + (b.etac - a.etac) * t;
+__device__ __forceinline__ void optics(const Sample<R, NL> &s, const R (&A)[NL], const R (&B)[NL], R &chi,
+                                       R &eta) {
+    chi = s.chic;
+    eta = s.etac;
+    const R rdv = Ar<R>::rcp(s.dv);
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        s.chi0[l] = a.chi0[l] + (b.chi0[l] - a.chi0[l]) * t;
-        s.eta0[l] = a.eta0[l] + (b.eta0[l] - a.eta0[l]) * t;
+        const R g = Ar<R>::gauss((A[l] + B[l] * s.delta) * rdv);
+        chi += s.chi0[l] * g;
+        eta += s.eta0[l] * g;
     }
 }
 
 template <typename R, int NL>
-__device__ __forceinline__ void optics(const Sample<R, NL> &s, const R (&A)[NL], const R (&B)[NL],
-                                       int32_t L, R &chi, R &eta) {
-    chi = s.chic;
-    eta = s.etac;
+__device__ __forceinline__ void shfl_sample(const Sample<R, NL> &s, int j, Sample<R, NL> &o) {
+    o.delta = __shfl_sync(0xffffffffu, s.delta, j);
+    o.dv = __shfl_sync(0xffffffffu, s.dv, j);
+    o.chic = __shfl_sync(0xffffffffu, s.chic, j);
+    o.etac = __shfl_sync(0xffffffffu, s.etac, j);
 #pragma unroll
     for (int l = 0; l < NL; ++l) {
-        if (l < L) {
-            const R g = Ar<R>::gauss(Ar<R>::arg(A[l], B[l], s.delta, s.dv));
-            chi += s.chi0[l] * g;
-            eta += s.eta0[l] * g;
+        o.chi0[l] = __shfl_sync(0xffffffffu, s.chi0[l], j);
+        o.eta0[l] = __shfl_sync(0xffffffffu, s.eta0[l], j);
+    }
+}
+
+// State of the elimination along one half of a pair line.  Starting from
+// (Fh, D, zh, dtp) = (1, 1, I, 0) the interior row below reproduces the
+// second-order boundary row (Fh = 1 + dt/2, zh = D (S dt/2 + I)), and a half
+// without points leaves exactly the empty-half coupling (D Fh, zh) = (1, I).
+template <typename R>
+struct Sweep {
+    R Fh, Dm, zh, dtp;  // scaled 1+B quantities of the last eliminated row, its dtau
+    R chi_c, eta_c;     // optics of the current (not yet eliminated) sub-point
+    R chi_p, eta_p;     // optics of the current velocity sample
+};
+
+// Eliminate the row of the current sub-point once the increment dt beyond it
+// is known.  One reciprocal R = 1 / (chi (1 + dt Fh)) gives D = chi R and
+// D S = eta R.
+template <typename R>
+__device__ __forceinline__ void row(Sweep<R> &w, R dt) {
+    const R dtb = (w.dtp + dt) * R(0.5);
+    w.Fh = dtb + w.Dm * w.Fh;
+    const R rr = Ar<R>::rcp(w.chi_c * (R(1) + dt * w.Fh));
+    w.Dm = w.chi_c * rr;
+    w.zh = w.Dm * w.zh + dtb * (w.eta_c * rr);
+    w.dtp = dt;
+}
+
+// One velocity sample q at distance hs beyond the previous one: line optics,
+// Eq. 2 sub-intervals with linear chi and eta, elimination rows.
+template <typename R, int NL>
+__device__ __forceinline__ void sample_step(const Sample<R, NL> &q, R hs, R dtau_max, R inv_dtau_max,
+                                            const R (&A)[NL], const R (&B)[NL], Sweep<R> &w, int *status,
+                                            unsigned &n_upd) {
+    R chi_q, eta_q;
+    optics<R, NL>(q, A, B, chi_q, eta_q);
+    const R nr = Ar<R>::ninter(fmax(w.chi_p, chi_q), hs, dtau_max, inv_dtau_max);
+    if (nr <= R(1)) {
+        row(w, hs * (w.chi_p + chi_q) * R(0.5));
+        w.chi_c = chi_q;
+        w.eta_c = eta_q;
+        ++n_upd;
+    } else {
+        int ni = int(fmin(nr, R(kMaxSubdiv)));
+        if (nr > R(kMaxSubdiv)) dev_fail(status, kDevSubdivLimit);
+        const R rni = R(1) / R(ni);
+        const R hh = hs * rni * R(0.5);
+        const R dchi = (chi_q - w.chi_p) * rni, deta = (eta_q - w.eta_p) * rni;
+        R cprev = w.chi_p;
+        for (int i = 1; i < ni; ++i) {
+            const R ci = w.chi_p + dchi * R(i);
+            row(w, hh * (cprev + ci));
+            w.chi_c = ci;
+            w.eta_c = w.eta_p + deta * R(i);
+            cprev = ci;
+        }
+        row(w, hh * (cprev + chi_q));
+        w.chi_c = chi_q;
+        w.eta_c = eta_q;
+        n_upd += unsigned(ni);
+    }
+    w.chi_p = chi_q;
+    w.eta_p = eta_q;
+}
+
+// One interval between consecutive traced points (far -> near): adaptive
+// velocity sampling (Section 2.1.1), then each sample's optics and rows.
+template <typename R, int NL>
+__device__ __forceinline__ void interval(const Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds,
+                                         const SolveArgs &a, R dtau_max, R inv_dtau_max, R dv_max,
+                                         const R (&A)[NL], const R (&B)[NL], Sweep<R> &w, unsigned &n_upd,
+                                         unsigned &n_smp) {
+    int nv = 1;
+    if (dv_max > R(0)) {
+        const R jump = fabs(nxt.delta - cur.delta);
+        const R lim = dv_max * fmin(cur.dv, nxt.dv);
+        if (jump > lim) {
+            const R nvr = ceil(jump / lim);
+            if (nvr > R(kMaxSubdiv)) {
+                dev_fail(a.status, kDevSubdivLimit);
+                nv = kMaxSubdiv;
+            } else {
+                nv = int(nvr);
+            }
         }
     }
+    n_smp += unsigned(nv);
+    if (nv == 1) {
+        sample_step<R, NL>(nxt, ds, dtau_max, inv_dtau_max, A, B, w, a.status, n_upd);
+        return;
+    }
+    const R rnv = R(1) / R(nv);
+    const R hs = ds * rnv;
+    Sample<R, NL> q = cur, st;
+    st.delta = (nxt.delta - cur.delta) * rnv;
+    st.dv = (nxt.dv - cur.dv) * rnv;
+    st.chic = (nxt.chic - cur.chic) * rnv;
+    st.etac = (nxt.etac - cur.etac) * rnv;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        st.chi0[l] = (nxt.chi0[l] - cur.chi0[l]) * rnv;
+        st.eta0[l] = (nxt.eta0[l] - cur.eta0[l]) * rnv;
+    }
+    for (int j = 1; j < nv; ++j) {
+        const R t = R(j);
+        q.delta = cur.delta + st.delta * t;
+        q.dv = cur.dv + st.dv * t;
+        q.chic = cur.chic + st.chic * t;
+        q.etac = cur.etac + st.etac * t;
+#pragma unroll
+        for (int l = 0; l < NL; ++l) {
+            q.chi0[l] = cur.chi0[l] + st.chi0[l] * t;
+            q.eta0[l] = cur.eta0[l] + st.eta0[l] * t;
+        }
+        sample_step<R, NL>(q, hs, dtau_max, inv_dtau_max, A, B, w, a.status, n_upd);
+    }
+    sample_step<R, NL>(nxt, hs, dtau_max, inv_dtau_max, A, B, w, a.status, n_upd);
 }
 
 // Eliminate one half of a pair line from its far end up to (excluding) the
-// origin row.  Returns the origin row's coupling (P = D Fh, Q = zh) and the
-// last optical-depth increment.
+// origin row.  The warp stages 32 traced points at a time: lane j loads entry
+// kb - j (coalesced ids and distances, gathered point data, its projected
+// velocity and its distance to the farther neighbour), then the warp walks the
+// chunk, broadcasting each point with shuffles.  Returns the origin row's
+// coupling (P = D Fh, Q = zh) and the last optical-depth increment.
 template <typename R, int NL>
-__device__ void half_sweep(const Data<R> &D, const SolveArgs &a, int32_t L, int64_t beg, int32_t cnt,
-                           R vox, R voy, R voz, R d0, R d1, R d2, const Sample<R, NL> &origin,
-                           const R (&A)[NL], const R (&B)[NL], R &P, R &Q, R &dtl,
-                           unsigned &n_upd, unsigned &n_smp) {
-    const R I = R(a.I_bdy);
-    if (cnt == 0) {
-        P = R(1);
-        Q = I;
-        dtl = R(0);
-        return;
-    }
-    const R dtau_max = R(a.dtau_max), dv_max = R(a.dv_max);
-    Sample<R, NL> cur, nxt, q;
-    int64_t e = beg + cnt - 1;
-    load_sample<R, NL>(D, L, __ldg(a.idx + e), vox, voy, voz, d0, d1, d2, cur);
-    double zcur = __ldg(a.Z + e);
-    R chi_p, eta_p;
-    optics<R, NL>(cur, A, B, L, chi_p, eta_p);
-    R S_c = Ar<R>::div(eta_p, chi_p);
-    bool first = true;
-    R Fh = R(0), Dm = R(1), zh = R(0), dtp = R(0);
-    for (int32_t k = cnt - 1; k >= 0; --k) {
-        double znext;
-        if (k > 0) {
-            load_sample<R, NL>(D, L, __ldg(a.idx + beg + k - 1), vox, voy, voz, d0, d1, d2, nxt);
-            znext = __ldg(a.Z + beg + k - 1);
-        } else {
-            nxt = origin;
-            znext = 0.0;
-        }
-        const R ds = R(zcur - znext);  // distance increment, differenced in double
-        int nv = 1;
-        if (dv_max > R(0)) {
-            const R jump = fabs(nxt.delta - cur.delta);
-            const R lim = dv_max * fmin(cur.dv, nxt.dv);
-            if (jump > lim) {
-                const R nvr = ceil(jump / lim);
-                if (nvr > R(kMaxSubdiv)) {
-                    dev_fail(a.status, kDevSubdivLimit);
-                    nv = kMaxSubdiv;
-                } else {
-                    nv = int(nvr);
-                }
-            }
-        }
-        const R hs = ds / R(nv);
-        for (int j = 1; j <= nv; ++j) {
-            if (j == nv) {
-                q = nxt;
+__device__ void half_sweep(const Data<R> &D, const SolveArgs &a, int32_t L, int lane, int64_t beg,
+                           int32_t cnt, R vox, R voy, R voz, R d0, R d1, R d2, const Sample<R, NL> &origin,
+                           const R (&A)[NL], const R (&B)[NL], R &P, R &Q, R &dtl, unsigned &n_upd,
+                           unsigned &n_smp) {
+    Sweep<R> w;
+    w.Fh = R(1);
+    w.Dm = R(1);
+    w.zh = R(a.I_bdy);
+    w.dtp = R(0);
+    if (cnt > 0) {
+        const R dtau_max = R(a.dtau_max), inv_dtau_max = R(1.0 / a.dtau_max), dv_max = R(a.dv_max);
+        Sample<R, NL> cur, nxt, st;
+        for (int32_t kb = cnt - 1; kb >= 0; kb -= 32) {
+            const int32_t nch = kb + 1 < 32 ? kb + 1 : 32;
+            R sds = R(0);
+            if (lane < nch) {
+                const int32_t k = kb - lane;
+                const double zk = __ldg(a.Z + beg + k);
+                const double zf = (k + 1 < cnt) ? __ldg(a.Z + beg + k + 1) : zk;
+                sds = R(zf - zk);  // distance increment, differenced in double
+                load_sample<R, NL>(D, L, __ldg(a.idx + beg + k), vox, voy, voz, d0, d1, d2, st);
             } else {
-                lerp_sample<R, NL>(cur, nxt, R(j) / R(nv), q);
+                st = origin;
             }
-            R chi_q, eta_q;
-            optics<R, NL>(q, A, B, L, chi_q, eta_q);
-            ++n_smp;
-            const R cm = fmax(chi_p, chi_q);
-            R nr = ceil(cm * hs / dtau_max);
-            int ni = nr < R(1) ? 1 : (nr > R(kMaxSubdiv) ? kMaxSubdiv + 1 : int(nr));
-            if (ni > kMaxSubdiv) {
-                dev_fail(a.status, kDevSubdivLimit);
-                ni = kMaxSubdiv;
-            }
-            const R hh = hs / R(ni);
-            n_upd += unsigned(ni);
-            R cprev = chi_p;
-            for (int i = 1; i <= ni; ++i) {
-                R ci, ei;
-                if (i == ni) {
-                    ci = chi_q;
-                    ei = eta_q;
-                } else {
-                    const R t = R(i) / R(ni);
-                    ci = chi_p + (chi_q - chi_p) * t;
-                    ei = eta_p + (eta_q - eta_p) * t;
+            for (int j = 0; j < nch; ++j) {
+                shfl_sample<R, NL>(st, j, nxt);
+                const R ds = __shfl_sync(0xffffffffu, sds, j);
+                if (kb == cnt - 1 && j == 0) {  // the far end: its row follows with the first increment
+                    cur = nxt;
+                    optics<R, NL>(cur, A, B, w.chi_p, w.eta_p);
+                    w.chi_c = w.chi_p;
+                    w.eta_c = w.eta_p;
+                    continue;
                 }
-                const R dt = hh * (cprev + ci) * R(0.5);
-                if (first) {
-                    Fh = R(1) + dt * R(0.5);
-                    Dm = Ar<R>::rcp(R(1) + dt * Fh);
-                    zh = Dm * (S_c * dt * R(0.5) + I);
-                    first = false;
-                } else {
-                    const R dtb = (dtp + dt) * R(0.5);
-                    Fh = dtb + Dm * Fh;
-                    Dm = Ar<R>::rcp(R(1) + dt * Fh);
-                    zh = Dm * (dtb * S_c + zh);
-                }
-                dtp = dt;
-                S_c = Ar<R>::div(ei, ci);
-                cprev = ci;
+                interval<R, NL>(cur, nxt, ds, a, dtau_max, inv_dtau_max, dv_max, A, B, w, n_upd, n_smp);
+                cur = nxt;
             }
-            chi_p = chi_q;
-            eta_p = eta_q;
         }
-        cur = nxt;
-        zcur = znext;
+        interval<R, NL>(cur, origin, R(__ldg(a.Z + beg)), a, dtau_max, inv_dtau_max, dv_max, A, B, w, n_upd,
+                        n_smp);
     }
-    P = Dm * Fh;
-    Q = zh;
-    dtl = dtp;
+    P = w.Dm * w.Fh;
+    Q = w.zh;
+    dtl = w.dtp;
 }
 
+template <typename R>
+struct Occ {
+    static constexpr int kMinBlocks = 1;
+};
+template <>
+struct Occ<float> {
+    static constexpr int kMinBlocks = 2;  // 16 warps per SM without spills
+};
+
 template <typename R, int NL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, Occ<R>::kMinBlocks)
 k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t item = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -265,16 +347,16 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
 #pragma unroll
     for (int lp = 0; lp < NL; ++lp) {
         const double r = (lp < L) ? Ln.ratio[l * MGX_MAX_LINES + lp] : 1.0;
-        A[lp] = R(kC * (r - 1.0) + r * ub);
-        B[lp] = R(r * (1.0 + ub / kC));
+        A[lp] = R((kC * (r - 1.0) + r * ub) * Ar<R>::kArgScale);
+        B[lp] = R(r * (1.0 + ub / kC) * Ar<R>::kArgScale);
     }
     const R vox = __ldg(D.vx + o), voy = __ldg(D.vy + o), voz = __ldg(D.vz + o);
     Sample<R, NL> org;
     load_sample<R, NL>(D, L, o, vox, voy, voz, R(0), R(0), R(0), org);
     org.delta = R(0);
     R chi_o, eta_o;
-    optics<R, NL>(org, A, B, L, chi_o, eta_o);
-    const R S_o = Ar<R>::div(eta_o, chi_o);
+    optics<R, NL>(org, A, B, chi_o, eta_o);
+    const R S_o = eta_o / chi_o;
 
     double sum = 0.0, comp = 0.0;
     unsigned n_upd = 0, n_smp = 0;
@@ -289,19 +371,18 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
         {
             const int64_t beg = a.offs[hb] - a.base;
             const int32_t cnt = int32_t(a.offs[hb + 1] - a.offs[hb]);
-            half_sweep<R, NL>(D, a, L, beg, cnt, vox, voy, voz, -r0, -r1, -r2, org, A, B, P0, Q0, t0, n_upd,
-                              n_smp);
+            half_sweep<R, NL>(D, a, L, lane, beg, cnt, vox, voy, voz, -r0, -r1, -r2, org, A, B, P0, Q0, t0,
+                              n_upd, n_smp);
         }
         {
             const int64_t beg = a.offs[hb + 1] - a.base;
             const int32_t cnt = int32_t(a.offs[hb + 2] - a.offs[hb + 1]);
-            half_sweep<R, NL>(D, a, L, beg, cnt, vox, voy, voz, r0, r1, r2, org, A, B, P1, Q1, t1, n_upd,
-                              n_smp);
+            half_sweep<R, NL>(D, a, L, lane, beg, cnt, vox, voy, voz, r0, r1, r2, org, A, B, P1, Q1, t1,
+                              n_upd, n_smp);
         }
         const R dtb = (t0 + t1) * R(0.5);
-        const R u = Ar<R>::div(dtb * S_o + Q0 + Q1, dtb + P0 + P1);
-        const double w2 = 2.0 / double(int64_t(12) << (2 * lev));
-        const double xv = w2 * double(u);
+        const R u = (dtb * S_o + Q0 + Q1) / (dtb + P0 + P1);
+        const double xv = a.w2[lev] * double(u);
         const double t = sum + xv;  // Neumaier compensated sum
         if (fabs(sum) >= fabs(xv)) comp += (sum - t) + xv;
         else comp += (xv - t) + sum;

@@ -29,6 +29,8 @@ struct Model {
     double *x = nullptr, *y = nullptr, *z = nullptr, *vx = nullptr, *vy = nullptr, *vz = nullptr;
     float *vxf = nullptr, *vyf = nullptr, *vzf = nullptr;
     int32_t *off = nullptr, *nbr = nullptr;
+    float4 *phi = nullptr, *plo = nullptr;
+    float g0 = 0.0f;
     // lines
     bool has_lines = false;
     int32_t L = 0, F = 0;
@@ -116,7 +118,7 @@ void dfree(mgx_ctx *ctx, T *&p) {
 const char *dev_err_text(int code) {
     switch (code) {
         case kDevBadCsr: return "neighbour graph invalid (offsets not monotone or index out of range/self)";
-        case kDevNonFinite: return "non-finite position or velocity";
+        case kDevNonFinite: return "non-finite position or velocity, or a coordinate beyond 1e30";
         case kDevTraceGuard: return "tracer step guard hit";
         case kDevTraceMismatch: return "trace emit pass disagrees with count pass";
         case kDevSubdivLimit: return "more than 2^20 optical-depth sub-intervals in one step (dtau_max too small?)";
@@ -202,6 +204,9 @@ DevMesh mesh_view(const Model &m) {
     d.vxf = m.vxf; d.vyf = m.vyf; d.vzf = m.vzf;
     d.off = m.off;
     d.nbr = m.nbr;
+    d.phi = m.phi;
+    d.plo = m.plo;
+    d.g0 = m.g0;
     return d;
 }
 
@@ -289,6 +294,7 @@ void free_model(mgx_ctx *ctx, Model &m) {
     dfree(ctx, m.vx); dfree(ctx, m.vy); dfree(ctx, m.vz);
     dfree(ctx, m.vxf); dfree(ctx, m.vyf); dfree(ctx, m.vzf);
     dfree(ctx, m.off); dfree(ctx, m.nbr);
+    dfree(ctx, m.phi); dfree(ctx, m.plo);
     free_lines(ctx, m);
     dfree(ctx, m.rays);
     m.has_rays = false;
@@ -417,6 +423,11 @@ mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const doubl
     CK(dalloc(ctx, &m.vxf, size_t(n))); CK(dalloc(ctx, &m.vyf, size_t(n))); CK(dalloc(ctx, &m.vzf, size_t(n)));
     CK(dalloc(ctx, &m.off, size_t(n + 1)));
     CK(dalloc(ctx, &m.nbr, size_t(E)));
+    CK(dalloc(ctx, &m.phi, size_t(n)));
+    CK(dalloc(ctx, &m.plo, size_t(n)));
+    unsigned int *xmax = nullptr;
+    CK(dalloc(ctx, &xmax, 1));
+    CK(cudaMemsetAsync(xmax, 0, sizeof(unsigned int), ctx->stream));
     CK(cudaMemcpyAsync(pos_d, pos, size_t(3 * n) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(vel_d, vel, size_t(3 * n) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(off64, nbr_off, size_t(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
@@ -425,9 +436,12 @@ mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const doubl
     {
         Timed t(ctx, MGX_K_OTHER);
         launch_ingest_mesh(m.n, pos_d, vel_d, off64, E, m.x, m.y, m.z, m.vx, m.vy, m.vz, m.vxf, m.vyf,
-                           m.vzf, m.off, m.nbr, ctx->d_status, ctx->stream);
+                           m.vzf, m.off, m.nbr, m.phi, m.plo, xmax, ctx->d_status, ctx->stream);
     }
     CK(cudaGetLastError());
+    unsigned int xmax_h = 0;
+    CK(cudaMemcpyAsync(&xmax_h, xmax, sizeof xmax_h, cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, xmax);
     dfree(ctx, pos_d);
     dfree(ctx, vel_d);
     dfree(ctx, off64);
@@ -436,6 +450,12 @@ mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const doubl
     if (s != MGX_OK) {
         free_model(ctx, m);
         return s;
+    }
+    {
+        float xm;
+        std::memcpy(&xm, &xmax_h, sizeof xm);
+        const double u = 1.0 / 16777216.0;  // 2^-24
+        m.g0 = float(32.0 * u * u * double(xm) * (1.0 + 1e-6)) + 1e-37f;
     }
     ctx->models.push_back(m);
     *model_id = int32_t(ctx->models.size() - 1);
@@ -680,6 +700,7 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         a.J = J;
         a.status = ctx->d_status;
         a.counters = ctx->prof ? ctx->d_counters : nullptr;
+        fill_pair_weights(a);
         {
             Timed t(ctx, MGX_K_SOLVE);
             launch_solve(dm, dl, dr, a, p->precision, ctx->stream);

@@ -41,6 +41,8 @@ struct DevMesh {
     const float *vxf, *vyf, *vzf;
     const int32_t *off;  // [n+1]
     const int32_t *nbr;  // [E]
+    const float4 *phi, *plo;  // positions split as double ~ hi + lo, both float (w unused)
+    float g0;                 // 32 u^2 max_n (|x|+|y|+|z|): split-representation error floor
 };
 
 struct DevLines {
@@ -70,13 +72,20 @@ struct SolveArgs {
     double *J;                // [n][L*F]
     int *status;
     unsigned long long *counters;  // nullable: [0] elimination updates, [1] optics samples
+    double w2[MGX_MAX_LEVEL + 1];  // 2 w_l = 2 / (12 4^l), pair weight of level l (Eq. 4)
 };
+
+// Fill SolveArgs::w2 (host).
+inline void fill_pair_weights(SolveArgs &a) {
+    for (int l = 0; l <= MGX_MAX_LEVEL; ++l) a.w2[l] = 2.0 / double(int64_t(12) << (2 * l));
+}
 
 // ---- ingest (k_mesh.cu)
 void launch_ingest_mesh(int32_t n, const double *pos_aos, const double *vel_aos, const int64_t *off64,
                         int64_t E, double *x, double *y, double *z, double *vx, double *vy,
                         double *vz, float *vxf, float *vyf, float *vzf, int32_t *off32,
-                        const int32_t *nbr, int *status, cudaStream_t st);
+                        const int32_t *nbr, float4 *phi, float4 *plo, unsigned int *xmax_bits,
+                        int *status, cudaStream_t st);
 void launch_ingest_lines(int32_t n, int32_t L, const double *chi0, const double *eta0,
                          const double *dvw, const double *chic, const double *etac, float *chi0f,
                          float *eta0f, float *dvwf, float *chicf, float *etacf, int *status,

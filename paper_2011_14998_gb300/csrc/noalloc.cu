@@ -141,6 +141,7 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
         a.J = J;
         a.status = status;
         a.counters = nullptr;
+        fill_pair_weights(a);
         launch_solve(m, Ln, R, a, precision, st);
         if ((ce = cudaGetLastError()) != cudaSuccess) {
             snprintf(err, errlen, "CUDA error in the allocation-free solve: %s", cudaGetErrorString(ce));
