@@ -326,7 +326,9 @@ def run_mgx(args):
                      "oracle_sample": acc_oracle},
         "kernel_ms_per_step": step_ms,
         "work_per_step": {"solves": solves_per_step, "trace_points": prof32["trace_points"] // args.steps,
-                          "updates": prof32["updates"] // args.steps, "samples": prof32["samples"] // args.steps},
+                          "updates": prof32["updates"] // args.steps, "samples": prof32["samples"] // args.steps,
+                          "trace_steps": prof32["trace_steps"] // args.steps,
+                          "trace_steps_redone_fp64": prof32["trace_exact_steps"] // args.steps},
         "roofline": {"kernel": "k_solve<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                      "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",

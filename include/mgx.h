@@ -161,7 +161,7 @@ mgx_status mgx_trace(mgx_ctx *ctx, int32_t model, int64_t o_begin, int64_t o_end
  *   J_out  [n][n_lines*n_freq] doubles, host or device per params->out_on_device
  * The call synchronises the stream (the tracer's total length sizes the
  * point-list arena; device-side checks are reported before returning).  Origins
- * are processed in chunks whose traced point lists fit a 16 GiB arena. */
+ * are processed in chunks whose traced point ids fit a 16 GiB arena. */
 mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params, void *J_out);
 
 /* Mesh-reduction criterion of Section 2.2.2 with tracer f (Eqs. 6-8):
@@ -187,7 +187,7 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
  * from one fixed 64 MiB device array compiled into the library instead of an
  * allocation.  Origins are processed in chunks that fit it; the call fails with
  * MGX_ERANGE when the ray set has too many pairs for the array or when one
- * origin's traced point lists alone do not fit (more than about 5.5 million
+ * origin's traced point lists alone do not fit (more than about 14 million
  * points).  No cudaMalloc, cudaFree or allocating library routine is called.
  * The first call on a device looks up the array's device address (set-up); make
  * that first call before any stream capture.  Every call shares the array:
@@ -217,6 +217,9 @@ typedef struct {
     int64_t solves;                /* (origin, ray pair, bin) Feautrier solutions     */
     int64_t updates;               /* (bin, optical-depth sub-interval) elimination steps */
     int64_t samples;               /* (bin, velocity sample) line-optics evaluations  */
+    int64_t trace_steps;           /* tracer steps of the counting pass               */
+    int64_t trace_exact_steps;     /* of those, steps the single-precision screen could
+                                      not decide, redone in double precision          */
 } mgx_profile;
 
 /* enable != 0 starts (and resets) profiling; 0 stops it. */

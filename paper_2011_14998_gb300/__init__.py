@@ -43,7 +43,8 @@ class SolveParams(C.Structure):
 
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("trace_points", C.c_int64),
-                ("solves", C.c_int64), ("updates", C.c_int64), ("samples", C.c_int64)]
+                ("solves", C.c_int64), ("updates", C.c_int64), ("samples", C.c_int64),
+                ("trace_steps", C.c_int64), ("trace_exact_steps", C.c_int64)]
 
 
 _lib = None
@@ -210,7 +211,8 @@ def mgx_profile_read(ctx) -> dict:
     return dict(ms={k: p.ms[i] for i, k in enumerate(KERNEL_CLASSES)},
                 launches={k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
                 trace_points=int(p.trace_points), solves=int(p.solves), updates=int(p.updates),
-                samples=int(p.samples))
+                samples=int(p.samples), trace_steps=int(p.trace_steps),
+                trace_exact_steps=int(p.trace_exact_steps))
 
 
 def solve_params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, precision=MGX_FP64, out_on_device=False):

@@ -11,7 +11,7 @@ __global__ void k_ingest_points(int32_t n, const double *__restrict__ pos,
                                 const double *__restrict__ vel, const int64_t *__restrict__ off64,
                                 int64_t E, double *x, double *y, double *z, double *vx, double *vy,
                                 double *vz, float *vxf, float *vyf, float *vzf, int32_t *off32,
-                                float4 *phi, float4 *plo, unsigned int *xmax_bits, int *status) {
+                                float4 *phi, unsigned int *xmax_bits, int *status) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i > n) return;
     const int64_t o = off64[i];
@@ -32,11 +32,7 @@ __global__ void k_ingest_points(int32_t n, const double *__restrict__ pos,
     vxf[i] = float(ux);
     vyf[i] = float(uy);
     vzf[i] = float(uz);
-    // double = hi + lo + r with hi = fl32(x), lo = fl32(x - hi), |r| <= u^2 |x|
-    const float hx = __double2float_rn(px), hy = __double2float_rn(py), hz = __double2float_rn(pz);
-    phi[i] = make_float4(hx, hy, hz, 0.0f);
-    plo[i] = make_float4(__double2float_rn(px - double(hx)), __double2float_rn(py - double(hy)),
-                         __double2float_rn(pz - double(hz)), 0.0f);
+    phi[i] = make_float4(__double2float_rn(px), __double2float_rn(py), __double2float_rn(pz), 0.0f);
     const float s = __double2float_ru(fabs(px) + fabs(py) + fabs(pz));
     if (isfinite(s)) atomicMax(xmax_bits, __float_as_uint(s));  // non-negative: bit order = value order
 }
@@ -54,12 +50,31 @@ __global__ void k_check_nbr(int32_t n, const int32_t *__restrict__ off, const in
 void launch_ingest_mesh(int32_t n, const double *pos_aos, const double *vel_aos, const int64_t *off64,
                         int64_t E, double *x, double *y, double *z, double *vx, double *vy,
                         double *vz, float *vxf, float *vyf, float *vzf, int32_t *off32,
-                        const int32_t *nbr, float4 *phi, float4 *plo, unsigned int *xmax_bits,
-                        int *status, cudaStream_t st) {
+                        const int32_t *nbr, float4 *phi, unsigned int *xmax_bits, int *status,
+                        cudaStream_t st) {
     const int tb = 256;
     k_ingest_points<<<unsigned((n + 1 + tb - 1) / tb), tb, 0, st>>>(
-        n, pos_aos, vel_aos, off64, E, x, y, z, vx, vy, vz, vxf, vyf, vzf, off32, phi, plo, xmax_bits, status);
+        n, pos_aos, vel_aos, off64, E, x, y, z, vx, vy, vz, vxf, vyf, vzf, off32, phi, xmax_bits, status);
     k_check_nbr<<<unsigned((n + tb - 1) / tb), tb, 0, st>>>(n, off32, nbr, status);
+}
+
+// neighbour records for the tracer's single-precision screen: the position of
+// nbr[e] rounded to float, next to its id, in CSR order
+__global__ void k_pack_neighbours(int32_t n, const int32_t *__restrict__ off, const int32_t *__restrict__ nbr,
+                                  const float4 *__restrict__ phi, float4 *__restrict__ nrec) {
+    const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (i >= n) return;
+    for (int32_t e = off[i]; e < off[i + 1]; ++e) {
+        const int32_t j = nbr[e];
+        const float4 h = phi[j];
+        nrec[e] = make_float4(h.x, h.y, h.z, __int_as_float(j));
+    }
+}
+
+void launch_pack_neighbours(int32_t n, const int32_t *off, const int32_t *nbr, const float4 *phi, float4 *nrec,
+                            cudaStream_t st) {
+    const int tb = 256;
+    k_pack_neighbours<<<unsigned((n + tb - 1) / tb), tb, 0, st>>>(n, off, nbr, phi, nrec);
 }
 
 __global__ void k_ingest_lines(int32_t n, int32_t L, const double *__restrict__ chi0,

@@ -232,7 +232,7 @@ __device__ __forceinline__ void interval(const Sample<R, NL> &cur, const Sample<
         sample_step<R, NL>(nxt, ds, dtau_max, inv_dtau_max, A, B, w, a.status, n_upd);
         return;
     }
-    const R rnv = R(1) / R(nv);
+    const R rnv = Ar<R>::rcp(R(nv));
     const R hs = ds * rnv;
     Sample<R, NL> q = cur, st;
     st.delta = (nxt.delta - cur.delta) * rnv;
@@ -266,11 +266,28 @@ __device__ __forceinline__ void interval(const Sample<R, NL> &cur, const Sample<
 // velocity and its distance to the farther neighbour), then the warp walks the
 // chunk, broadcasting each point with shuffles.  Returns the origin row's
 // coupling (P = D Fh, Q = zh) and the last optical-depth increment.
+// Projected distance Z = (x_n - x_o).d exactly as the tracer and its
+// definition form it (explicitly rounded double operations in fixed order).
+__device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t id, double xo, double yo, double zo, double d0,
+                                          double d1, double d2) {
+    const double dx = __dsub_rn(__ldg(m.x + id), xo);
+    const double dy = __dsub_rn(__ldg(m.y + id), yo);
+    const double dz = __dsub_rn(__ldg(m.z + id), zo);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2));
+}
+
+// Eliminate one half of a pair line from its far end up to (excluding) the
+// origin row.  The warp stages 32 traced points at a time: lane j takes entry
+// kb - j (coalesced ids, gathered point data), forms its exact Z and projected
+// velocity, and gets the distance to the farther entry from its neighbour lane;
+// then the warp walks the chunk, broadcasting each point with shuffles.
+// Returns the origin row's coupling (P = D Fh, Q = zh) and the last
+// optical-depth increment.
 template <typename R, int NL>
-__device__ void half_sweep(const Data<R> &D, const SolveArgs &a, int32_t L, int lane, int64_t beg,
-                           int32_t cnt, R vox, R voy, R voz, R d0, R d1, R d2, const Sample<R, NL> &origin,
-                           const R (&A)[NL], const R (&B)[NL], R &P, R &Q, R &dtl, unsigned &n_upd,
-                           unsigned &n_smp) {
+__device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &a, int32_t L, int lane,
+                           int64_t beg, int32_t cnt, double xo, double yo, double zo, double e0, double e1,
+                           double e2, R vox, R voy, R voz, const Sample<R, NL> &origin, const R (&A)[NL],
+                           const R (&B)[NL], R &P, R &Q, R &dtl, unsigned &n_upd, unsigned &n_smp) {
     Sweep<R> w;
     w.Fh = R(1);
     w.Dm = R(1);
@@ -278,19 +295,23 @@ __device__ void half_sweep(const Data<R> &D, const SolveArgs &a, int32_t L, int 
     w.dtp = R(0);
     if (cnt > 0) {
         const R dtau_max = R(a.dtau_max), inv_dtau_max = R(1.0 / a.dtau_max), dv_max = R(a.dv_max);
+        const R d0 = R(e0), d1 = R(e1), d2 = R(e2);
         Sample<R, NL> cur, nxt, st;
+        double zcarry = 0.0;  // Z of the entry just beyond the current chunk (farther)
         for (int32_t kb = cnt - 1; kb >= 0; kb -= 32) {
             const int32_t nch = kb + 1 < 32 ? kb + 1 : 32;
-            R sds = R(0);
+            double zk = 0.0;
             if (lane < nch) {
-                const int32_t k = kb - lane;
-                const double zk = __ldg(a.Z + beg + k);
-                const double zf = (k + 1 < cnt) ? __ldg(a.Z + beg + k + 1) : zk;
-                sds = R(zf - zk);  // distance increment, differenced in double
-                load_sample<R, NL>(D, L, __ldg(a.idx + beg + k), vox, voy, voz, d0, d1, d2, st);
+                const int32_t id = __ldg(a.idx + beg + kb - lane);
+                zk = exact_Z(m, id, xo, yo, zo, e0, e1, e2);
+                load_sample<R, NL>(D, L, id, vox, voy, voz, d0, d1, d2, st);
             } else {
                 st = origin;
             }
+            double zf = __shfl_up_sync(0xffffffffu, zk, 1);
+            if (lane == 0) zf = (kb == cnt - 1) ? zk : zcarry;
+            const R sds = R(zf - zk);  // distance increment, differenced in double
+            zcarry = __shfl_sync(0xffffffffu, zk, nch - 1);
             for (int j = 0; j < nch; ++j) {
                 shfl_sample<R, NL>(st, j, nxt);
                 const R ds = __shfl_sync(0xffffffffu, sds, j);
@@ -305,8 +326,7 @@ __device__ void half_sweep(const Data<R> &D, const SolveArgs &a, int32_t L, int 
                 cur = nxt;
             }
         }
-        interval<R, NL>(cur, origin, R(__ldg(a.Z + beg)), a, dtau_max, inv_dtau_max, dv_max, A, B, w, n_upd,
-                        n_smp);
+        interval<R, NL>(cur, origin, R(zcarry), a, dtau_max, inv_dtau_max, dv_max, A, B, w, n_upd, n_smp);
     }
     P = w.Dm * w.Fh;
     Q = w.zh;
@@ -351,6 +371,7 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
         B[lp] = R(r * (1.0 + ub / kC) * Ar<R>::kArgScale);
     }
     const R vox = __ldg(D.vx + o), voy = __ldg(D.vy + o), voz = __ldg(D.vz + o);
+    const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
     Sample<R, NL> org;
     load_sample<R, NL>(D, L, o, vox, voy, voz, R(0), R(0), R(0), org);
     org.delta = R(0);
@@ -365,20 +386,20 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
         const uint32_t ray = __ldg(Rs.rays + int64_t(o) * Rs.npairs + p);
         const int lev = int(ray >> 28);
         const double *rv = Rs.dir + 3 * (level_offset(lev) + (ray & 0x0FFFFFFFu));
-        const R r0 = R(rv[0]), r1 = R(rv[1]), r2 = R(rv[2]);
+        const double r0 = rv[0], r1 = rv[1], r2 = rv[2];
         R P0, Q0, t0, P1, Q1, t1;
         const int64_t hb = h0 + 2 * int64_t(p);
         {
             const int64_t beg = a.offs[hb] - a.base;
             const int32_t cnt = int32_t(a.offs[hb + 1] - a.offs[hb]);
-            half_sweep<R, NL>(D, a, L, lane, beg, cnt, vox, voy, voz, -r0, -r1, -r2, org, A, B, P0, Q0, t0,
-                              n_upd, n_smp);
+            half_sweep<R, NL>(m, D, a, L, lane, beg, cnt, xo, yo, zo, -r0, -r1, -r2, vox, voy, voz, org, A, B,
+                              P0, Q0, t0, n_upd, n_smp);
         }
         {
             const int64_t beg = a.offs[hb + 1] - a.base;
             const int32_t cnt = int32_t(a.offs[hb + 2] - a.offs[hb + 1]);
-            half_sweep<R, NL>(D, a, L, lane, beg, cnt, vox, voy, voz, r0, r1, r2, org, A, B, P1, Q1, t1,
-                              n_upd, n_smp);
+            half_sweep<R, NL>(m, D, a, L, lane, beg, cnt, xo, yo, zo, r0, r1, r2, vox, voy, voz, org, A, B,
+                              P1, Q1, t1, n_upd, n_smp);
         }
         const R dtb = (t0 + t1) * R(0.5);
         const R u = (dtb * S_o + Q0 + Q1) / (dtb + P0 + P1);

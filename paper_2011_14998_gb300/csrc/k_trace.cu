@@ -9,13 +9,11 @@
 // lists and distances are bit-reproducible.
 //
 // GB300 executes double precision at a small fraction of its single-precision
-// rate, so each step first screens the neighbours in single precision:
-// positions are held as float hi + lo pairs (x = hi + lo to 2^-48 |x|), the
-// offset x_n - x_o, Z and q are formed in float, and each gets a rigorous
-// bound on its distance from the double-precision value (derived from the
-// unit roundoff u = 2^-24; three to four times the worst case):
-//     |Z32 - Z| <= eZ = 16 u S + g0,           S = |dx| + |dy| + |dz|,
-//     |q32 - q| <= eq = 256 u S^2 + 32 g0 S,   g0 = 32 u^2 max_n |x_n|_1.
+// rate, so each step first screens the neighbours in single precision: each
+// CSR edge carries its neighbour's position rounded to float, the offset
+// x_n - x_o, Z and q are formed in float, and each gets a rigorous bound on its
+// distance from the double-precision value (derived from the unit roundoff
+// u = 2^-24 and the positions' own rounding; see step_screen).
 // A neighbour is surely (not) forward when Z32 - Z_c clears eZ plus the
 // rounding of Z_c; the step is decided in single precision when one surely
 // forward neighbour's interval [q32 - eq, q32 + eq] lies strictly below the
@@ -23,9 +21,14 @@
 // lattice meshes, ambiguous forward tests) the step is redone exactly in
 // double precision.  The winner's Z is always computed exactly in double.
 //
+// The fast path carries the winner's single-precision Z and its error bound
+// into the next step's forward test, so it executes no double-precision
+// operation at all; the exact Z is formed only on undecided steps (and for
+// the inspection output of mgx_trace).
+//
 // Two passes share the walk: the count pass stores the half-ray lengths, which
-// are prefix-summed into arena offsets; the emit pass writes point ids and
-// distances at those offsets.
+// are prefix-summed into arena offsets; the emit pass writes the point ids at
+// those offsets (the solver re-forms each point's exact Z from its position).
 #include "mgx_internal.cuh"
 
 namespace mgx {
@@ -39,55 +42,47 @@ struct Step {
     double Z;
 };
 
-// The defining rule, exactly in double precision.
-__device__ Step step_exact(const DevMesh &m, int32_t c, double xo, double yo, double zo, double d0, double d1,
-                           double d2, double zc) {
-    int32_t best = -1;
-    double qbest = 0.0, zbest = 0.0;
-    const int32_t e1 = m.off[c + 1];
-    for (int32_t e = m.off[c]; e < e1; ++e) {
-        const int32_t nb = __ldg(m.nbr + e);
-        const double dx = __dsub_rn(__ldg(m.x + nb), xo);
-        const double dy = __dsub_rn(__ldg(m.y + nb), yo);
-        const double dz = __dsub_rn(__ldg(m.z + nb), zo);
-        const double zn = __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2));
-        if (!(zn > zc)) continue;
-        const double ex = __dsub_rn(dx, __dmul_rn(zn, d0));
-        const double ey = __dsub_rn(dy, __dmul_rn(zn, d1));
-        const double ez = __dsub_rn(dz, __dmul_rn(zn, d2));
-        const double q = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-        if (best < 0 || q < qbest || (q == qbest && nb < best)) {
-            best = nb;
-            qbest = q;
-            zbest = zn;
-        }
-    }
-    return Step{best, zbest};
+__device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t c, double xo, double yo, double zo, double d0,
+                                          double d1, double d2) {
+    const double dx = __dsub_rn(__ldg(m.x + c), xo);
+    const double dy = __dsub_rn(__ldg(m.y + c), yo);
+    const double dz = __dsub_rn(__ldg(m.z + c), zo);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2));
 }
 
-// Single-precision screen; falls back to step_exact when it cannot decide.
-__device__ __forceinline__ Step step_filtered(const DevMesh &m, int32_t c, float4 oh, float4 ol, double xo,
-                                              double yo, double zo, double d0, double d1, double d2, float f0,
-                                              float f1, float f2, double zc) {
-    const float zc32 = __double2float_rn(zc);
-    const float zcm = 4.0f * kU * fabsf(zc32);
+struct FStep {
+    int32_t next;  // -1: the half-ray ends; -2: undecided
+    float z32;     // single-precision Z of next; when undecided, H (see step_contenders)
+    float ez;      // bound on |z32 - Z(next)|, Z the double-precision value
+};
+
+// Single-precision screen of one step over the neighbour records of c (the
+// float position of each neighbour stored next to its id, read sequentially).
+// zc32 approximates the double Z of the current point within ezc; Xo is
+// |x_o|_1 in float.  With hi-only positions the bounds carry the rounding of
+// both positions: eZ = 3u (X_n + X_o) + 12u S + g0, eq = 32u (X_n + X_o) S +
+// 128u S^2 + 32 g0 S (about 2.5 to 3 times the worst case).  Returns
+// next = -2 when it cannot decide.
+__device__ __forceinline__ FStep step_screen(const DevMesh &m, int32_t c, float4 oh, float Xo, float f0, float f1,
+                                             float f2, float zc32, float ezc) {
+    const float zcm = ezc + 4.0f * kU * fabsf(zc32);
     int32_t best = -1, lo1_id = -1;
-    float hib = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+    float hib = INFINITY, lo1 = INFINITY, lo2 = INFINITY, zb = 0.0f, ezb = 0.0f;
     const int32_t e1 = m.off[c + 1];
     for (int32_t e = m.off[c]; e < e1; ++e) {
-        const int32_t nb = __ldg(m.nbr + e);
-        const float4 h = __ldg(m.phi + nb), l = __ldg(m.plo + nb);
-        const float dx = (h.x - oh.x) + (l.x - ol.x);
-        const float dy = (h.y - oh.y) + (l.y - ol.y);
-        const float dz = (h.z - oh.z) + (l.z - ol.z);
+        const float4 rec = __ldg(m.nrec + e);
+        const int32_t nb = __float_as_int(rec.w);
+        const float dx = rec.x - oh.x, dy = rec.y - oh.y, dz = rec.z - oh.z;
         const float S = fabsf(dx) + fabsf(dy) + fabsf(dz);
+        const float XS = fabsf(rec.x) + fabsf(rec.y) + fabsf(rec.z) + Xo;
         const float z32 = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
+        const float ez = fmaf(3.0f * kU, XS, fmaf(12.0f * kU, S, m.g0));
         const float diff = z32 - zc32;
-        const float E = fmaf(16.0f * kU, S, m.g0) + zcm + 4.0f * kU * fabsf(diff);
+        const float E = ez + zcm + 4.0f * kU * fabsf(diff);
         if (diff < -E) continue;  // surely not forward
-        const float ex = fmaf(-z32, f0, dx), ey = fmaf(-z32, f1, dy), ez = fmaf(-z32, f2, dz);
-        const float q = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-        const float eq = fmaf(256.0f * kU * S, S, 32.0f * m.g0 * S) + 1e-37f;  // floor covers subnormals
+        const float ex = fmaf(-z32, f0, dx), ey = fmaf(-z32, f1, dy), ez2 = fmaf(-z32, f2, dz);
+        const float q = fmaf(ez2, ez2, fmaf(ey, ey, ex * ex));
+        const float eq = fmaf(fmaf(32.0f * kU, XS, 128.0f * kU * S), S, fmaf(32.0f * m.g0, S, 1e-37f));
         const float lo = q - eq, hi = q + eq;
         if (lo < lo1) {
             lo2 = lo1;
@@ -99,88 +94,168 @@ __device__ __forceinline__ Step step_filtered(const DevMesh &m, int32_t c, float
         if (diff > E && hi < hib) {  // surely forward
             hib = hi;
             best = nb;
+            zb = z32;
+            ezb = ez;
         }
     }
-    if (lo1_id < 0) return Step{-1, 0.0};  // no neighbour can be forward
-    if (best >= 0 && best == lo1_id && hib < lo2) {
-        const double dx = __dsub_rn(__ldg(m.x + best), xo);
-        const double dy = __dsub_rn(__ldg(m.y + best), yo);
-        const double dz = __dsub_rn(__ldg(m.z + best), zo);
-        return Step{best, __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2))};
-    }
-    return step_exact(m, c, xo, yo, zo, d0, d1, d2, zc);
+    if (lo1_id < 0) return FStep{-1, 0.0f, 0.0f};  // no neighbour can be forward
+    if (best >= 0 && best == lo1_id && hib < lo2) return FStep{best, zb, ezb};
+    return FStep{-2, hib, 0.0f};
 }
 
-template <bool EMIT>
+// An undecided step, exactly: only neighbours that are not surely backward and
+// whose interval reaches down to H (the smallest upper bound of a surely
+// forward neighbour, or infinity) can be the winner; every other neighbour has
+// a strictly larger double-precision q than that surely forward one.  The
+// contenders are re-screened (same single-precision values) and decided by
+// the defining rule in double precision.
+__device__ Step step_contenders(const DevMesh &m, int32_t c, float4 oh, float Xo, float f0, float f1, float f2,
+                                float zc32, float ezc, float H, double zc, double xo, double yo, double zo,
+                                double d0, double d1, double d2) {
+    const float zcm = ezc + 4.0f * kU * fabsf(zc32);
+    int32_t best = -1;
+    double qbest = 0.0, zbest = 0.0;
+    const int32_t e1 = m.off[c + 1];
+    for (int32_t e = m.off[c]; e < e1; ++e) {
+        const float4 rec = __ldg(m.nrec + e);
+        const int32_t nb = __float_as_int(rec.w);
+        const float dx = rec.x - oh.x, dy = rec.y - oh.y, dz = rec.z - oh.z;
+        const float S = fabsf(dx) + fabsf(dy) + fabsf(dz);
+        const float XS = fabsf(rec.x) + fabsf(rec.y) + fabsf(rec.z) + Xo;
+        const float z32 = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
+        const float ez = fmaf(3.0f * kU, XS, fmaf(12.0f * kU, S, m.g0));
+        const float diff = z32 - zc32;
+        const float E = ez + zcm + 4.0f * kU * fabsf(diff);
+        if (diff < -E) continue;
+        const float ex = fmaf(-z32, f0, dx), ey = fmaf(-z32, f1, dy), ez2 = fmaf(-z32, f2, dz);
+        const float q = fmaf(ez2, ez2, fmaf(ey, ey, ex * ex));
+        const float eq = fmaf(fmaf(32.0f * kU, XS, 128.0f * kU * S), S, fmaf(32.0f * m.g0, S, 1e-37f));
+        if (q - eq > H) continue;
+        const double ddx = __dsub_rn(__ldg(m.x + nb), xo);
+        const double ddy = __dsub_rn(__ldg(m.y + nb), yo);
+        const double ddz = __dsub_rn(__ldg(m.z + nb), zo);
+        const double zn = __dadd_rn(__dadd_rn(__dmul_rn(ddx, d0), __dmul_rn(ddy, d1)), __dmul_rn(ddz, d2));
+        if (!(zn > zc)) continue;
+        const double qx = __dsub_rn(ddx, __dmul_rn(zn, d0));
+        const double qy = __dsub_rn(ddy, __dmul_rn(zn, d1));
+        const double qz = __dsub_rn(ddz, __dmul_rn(zn, d2));
+        const double qd = __dadd_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(qz, qz));
+        if (best < 0 || qd < qbest || (qd == qbest && nb < best)) {
+            best = nb;
+            qbest = qd;
+            zbest = zn;
+        }
+    }
+    return Step{best, zbest};
+}
+
+// MODE 0: count the points of each half-ray; MODE 1: write their ids;
+// MODE 2: write ids, exact double Z and (optionally) projected velocities.
+// Each thread walks half-rays h = tid, tid + T, ... (T = all threads), which
+// evens out the very different lengths of the rays a warp's lanes trace.
+template <int MODE>
 __global__ void __launch_bounds__(128)
 k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restrict__ lens,
         const int64_t *__restrict__ offs, int64_t base, int32_t *__restrict__ idx_out,
-        double *__restrict__ Z_out, double *__restrict__ delta_out, int *status) {
-    const int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (h >= n_half) return;
-    const int64_t pr = h >> 1;
-    const int32_t o = o_begin + int32_t(pr / R.npairs);
-    const uint32_t ray = R.rays[int64_t(o) * R.npairs + (pr % R.npairs)];
-    const double *r = R.dir + 3 * (level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
-    double d0 = r[0], d1 = r[1], d2 = r[2];
-    if ((h & 1) == 0) {  // backward half: exact negation of the pair direction
-        d0 = -d0;
-        d1 = -d1;
-        d2 = -d2;
-    }
-    const float f0 = __double2float_rn(d0), f1 = __double2float_rn(d1), f2 = __double2float_rn(d2);
-    const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
-    const float4 oh = m.phi[o], ol = m.plo[o];
-    int64_t w = 0;
-    int32_t expect = 0;
-    if (EMIT) {
-        w = offs[h] - base;
-        expect = int32_t(offs[h + 1] - offs[h]);
-    }
-    int32_t c = o, k = 0;
-    double zc = 0.0;
-    for (;;) {
-        const Step s = step_filtered(m, c, oh, ol, xo, yo, zo, d0, d1, d2, f0, f1, f2, zc);
-        if (s.next < 0) break;
-        if (EMIT) {
-            if (k >= expect) {
-                dev_fail(status, kDevTraceMismatch);
-                return;
+        double *__restrict__ Z_out, double *__restrict__ delta_out, int *status,
+        unsigned long long *__restrict__ counters) {
+    const int64_t T = int64_t(gridDim.x) * blockDim.x;
+    unsigned long long n_steps = 0, n_exact = 0;
+    for (int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; h < n_half; h += T) {
+        const int64_t pr = h >> 1;
+        const int32_t o = o_begin + int32_t(pr / R.npairs);
+        const uint32_t ray = R.rays[int64_t(o) * R.npairs + (pr % R.npairs)];
+        const double *r = R.dir + 3 * (level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
+        double d0 = r[0], d1 = r[1], d2 = r[2];
+        if ((h & 1) == 0) {  // backward half: exact negation of the pair direction
+            d0 = -d0;
+            d1 = -d1;
+            d2 = -d2;
+        }
+        const float f0 = __double2float_rn(d0), f1 = __double2float_rn(d1), f2 = __double2float_rn(d2);
+        const float4 oh = m.phi[o];
+        const float Xo = fabsf(oh.x) + fabsf(oh.y) + fabsf(oh.z);
+        int64_t w = 0;
+        int32_t expect = 0;
+        if (MODE > 0) {
+            w = offs[h] - base;
+            expect = int32_t(offs[h + 1] - offs[h]);
+        }
+        int32_t c = o, k = 0;
+        float zc32 = 0.0f, ezc = 0.0f;  // Z of the origin is exactly 0
+        for (;;) {
+            FStep s = step_screen(m, c, oh, Xo, f0, f1, f2, zc32, ezc);
+            ++n_steps;
+            double zexact = 0.0;
+            bool have_exact = false;
+            if (s.next == -2) {  // undecided in single precision: its contenders in double
+                const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
+                const double zc = (c == o) ? 0.0 : exact_Z(m, c, xo, yo, zo, d0, d1, d2);
+                const Step x = step_contenders(m, c, oh, Xo, f0, f1, f2, zc32, ezc, s.z32, zc, xo, yo, zo, d0, d1,
+                                               d2);
+                s.next = x.next;
+                zexact = x.Z;
+                ++n_exact;
+                have_exact = true;
+                s.z32 = __double2float_rn(x.Z);
+                s.ez = 2.0f * kU * fabsf(s.z32);
             }
-            idx_out[w + k] = s.next;
-            Z_out[w + k] = s.Z;
-            if (delta_out) {
-                const double ux = __dsub_rn(m.vx[s.next], m.vx[o]);
-                const double uy = __dsub_rn(m.vy[s.next], m.vy[o]);
-                const double uz = __dsub_rn(m.vz[s.next], m.vz[o]);
-                delta_out[w + k] =
-                    __dadd_rn(__dadd_rn(__dmul_rn(ux, d0), __dmul_rn(uy, d1)), __dmul_rn(uz, d2));
+            if (s.next < 0) break;
+            if (MODE > 0) {
+                if (k >= expect) {
+                    dev_fail(status, kDevTraceMismatch);
+                    return;
+                }
+                idx_out[w + k] = s.next;
+                if (MODE == 2) {
+                    const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
+                    Z_out[w + k] = have_exact ? zexact : exact_Z(m, s.next, xo, yo, zo, d0, d1, d2);
+                    if (delta_out) {
+                        const double ux = __dsub_rn(m.vx[s.next], m.vx[o]);
+                        const double uy = __dsub_rn(m.vy[s.next], m.vy[o]);
+                        const double uz = __dsub_rn(m.vz[s.next], m.vz[o]);
+                        delta_out[w + k] =
+                            __dadd_rn(__dadd_rn(__dmul_rn(ux, d0), __dmul_rn(uy, d1)), __dmul_rn(uz, d2));
+                    }
+                }
+            }
+            ++k;
+            c = s.next;
+            zc32 = s.z32;
+            ezc = s.ez;
+            if (k > m.n) {  // Z increases strictly, so this cannot happen
+                dev_fail(status, kDevTraceGuard);
+                break;
             }
         }
-        ++k;
-        c = s.next;
-        zc = s.Z;
-        if (k > m.n) {  // Z increases strictly, so this cannot happen
-            dev_fail(status, kDevTraceGuard);
-            break;
+        if (MODE > 0) {
+            if (k != expect) dev_fail(status, kDevTraceMismatch);
+        } else {
+            lens[h] = k;
         }
     }
-    if (EMIT) {
-        if (k != expect) dev_fail(status, kDevTraceMismatch);
-    } else {
-        lens[h] = k;
+    if (counters) {
+        atomicAdd(counters + 2, n_steps);
+        atomicAdd(counters + 3, n_exact);
     }
+}
+
+unsigned trace_grid(int64_t n_half) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n_half + 127) / 128;
+    const int64_t cap = int64_t(sms) * 8;  // 8 CTAs of 128 threads per SM
+    return unsigned(want < cap ? want : cap);
 }
 
 }  // namespace
 
 void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
-                        int64_t *lens, int *status, cudaStream_t st) {
+                        int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st) {
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
-    const int tb = 128;
-    k_trace<false><<<unsigned((n_half + tb - 1) / tb), tb, 0, st>>>(m, R, o_begin, n_half, lens, nullptr,
-                                                                    0, nullptr, nullptr, nullptr, status);
+    k_trace<0><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, nullptr, nullptr,
+                                                  nullptr, status, counters);
 }
 
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
@@ -188,9 +263,13 @@ void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int3
                        int *status, cudaStream_t st) {
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
-    const int tb = 128;
-    k_trace<true><<<unsigned((n_half + tb - 1) / tb), tb, 0, st>>>(m, R, o_begin, n_half, nullptr, offs,
-                                                                   base, idx, Z, delta, status);
+    if (Z) {
+        k_trace<2><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, idx, Z, delta,
+                                                      status, nullptr);
+    } else {
+        k_trace<1><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, idx, nullptr,
+                                                      nullptr, status, nullptr);
+    }
 }
 
 }  // namespace mgx

@@ -29,7 +29,7 @@ struct Model {
     double *x = nullptr, *y = nullptr, *z = nullptr, *vx = nullptr, *vy = nullptr, *vz = nullptr;
     float *vxf = nullptr, *vyf = nullptr, *vzf = nullptr;
     int32_t *off = nullptr, *nbr = nullptr;
-    float4 *phi = nullptr, *plo = nullptr;
+    float4 *phi = nullptr, *nrec = nullptr;
     float g0 = 0.0f;
     // lines
     bool has_lines = false;
@@ -65,7 +65,7 @@ struct mgx_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[MGX_K_COUNT];
     int64_t launches[MGX_K_COUNT] = {};
     std::vector<cudaEvent_t> event_pool;
-    unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples
+    unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples, [2] trace steps, [3] redone
     int64_t trace_points = 0, solves = 0;
 };
 
@@ -188,7 +188,7 @@ void reset_profile(mgx_ctx *c) {
     for (auto &l : c->launches) l = 0;
     c->trace_points = 0;
     c->solves = 0;
-    if (c->d_counters) cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (c->d_counters) cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), c->stream);
 }
 
 Model *get_model(mgx_ctx *ctx, int32_t id) {
@@ -205,7 +205,7 @@ DevMesh mesh_view(const Model &m) {
     d.off = m.off;
     d.nbr = m.nbr;
     d.phi = m.phi;
-    d.plo = m.plo;
+    d.nrec = m.nrec;
     d.g0 = m.g0;
     return d;
 }
@@ -294,7 +294,7 @@ void free_model(mgx_ctx *ctx, Model &m) {
     dfree(ctx, m.vx); dfree(ctx, m.vy); dfree(ctx, m.vz);
     dfree(ctx, m.vxf); dfree(ctx, m.vyf); dfree(ctx, m.vzf);
     dfree(ctx, m.off); dfree(ctx, m.nbr);
-    dfree(ctx, m.phi); dfree(ctx, m.plo);
+    dfree(ctx, m.phi); dfree(ctx, m.nrec);
     free_lines(ctx, m);
     dfree(ctx, m.rays);
     m.has_rays = false;
@@ -322,7 +322,8 @@ mgx_status trace_offsets(mgx_ctx *ctx, Model &m, int32_t o0, int32_t o1, int64_t
     CK(cudaMemsetAsync(offs, 0, sizeof(int64_t), ctx->stream));
     {
         Timed t(ctx, MGX_K_TRACE_COUNT);
-        launch_trace_count(mesh_view(m), rays_view(ctx, m), o0, o1, lens, ctx->d_status, ctx->stream);
+        launch_trace_count(mesh_view(m), rays_view(ctx, m), o0, o1, lens, ctx->d_status,
+                           ctx->prof ? ctx->d_counters : nullptr, ctx->stream);
     }
     CK(cudaGetLastError());
     if (n_half > 0) {
@@ -361,8 +362,8 @@ mgx_status mgx_create(int device, void *stream, mgx_ctx **out) {
     CK(cudaMalloc(&c->d_status, sizeof(int)));
     CK(cudaMemset(c->d_status, 0, sizeof(int)));
     CK(cudaMallocHost(&c->h_status, sizeof(int)));
-    CK(cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)));
-    CK(cudaMemset(c->d_counters, 0, 2 * sizeof(unsigned long long)));
+    CK(cudaMalloc(&c->d_counters, 4 * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_counters, 0, 4 * sizeof(unsigned long long)));
     *out = c.release();
     return MGX_OK;
 }
@@ -424,7 +425,7 @@ mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const doubl
     CK(dalloc(ctx, &m.off, size_t(n + 1)));
     CK(dalloc(ctx, &m.nbr, size_t(E)));
     CK(dalloc(ctx, &m.phi, size_t(n)));
-    CK(dalloc(ctx, &m.plo, size_t(n)));
+    CK(dalloc(ctx, &m.nrec, size_t(E)));
     unsigned int *xmax = nullptr;
     CK(dalloc(ctx, &xmax, 1));
     CK(cudaMemsetAsync(xmax, 0, sizeof(unsigned int), ctx->stream));
@@ -436,7 +437,8 @@ mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const doubl
     {
         Timed t(ctx, MGX_K_OTHER);
         launch_ingest_mesh(m.n, pos_d, vel_d, off64, E, m.x, m.y, m.z, m.vx, m.vy, m.vz, m.vxf, m.vyf,
-                           m.vzf, m.off, m.nbr, m.phi, m.plo, xmax, ctx->d_status, ctx->stream);
+                           m.vzf, m.off, m.nbr, m.phi, xmax, ctx->d_status, ctx->stream);
+        launch_pack_neighbours(m.n, m.off, m.nbr, m.phi, m.nrec, ctx->stream);
     }
     CK(cudaGetLastError());
     unsigned int xmax_h = 0;
@@ -651,7 +653,7 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         return s;
     }
     const int64_t total = obound[size_t(n)];
-    const int64_t budget = int64_t(ctx->arena_budget / (sizeof(int32_t) + sizeof(double)));
+    const int64_t budget = int64_t(ctx->arena_budget / sizeof(int32_t));
     std::vector<int32_t> cuts{0};
     int64_t chunk_max = 0;
     while (cuts.back() < n) {
@@ -664,9 +666,7 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
     ctx->trace_points += total;
     ctx->solves += int64_t(n) * np * int64_t(m->L) * m->F;
     int32_t *aidx = nullptr;
-    double *aZ = nullptr;
     CK(dalloc(ctx, &aidx, size_t(chunk_max)));
-    CK(dalloc(ctx, &aZ, size_t(chunk_max)));
     const int64_t NB = int64_t(m->L) * m->F;
     double *J = nullptr;
     if (p->out_on_device) {
@@ -683,7 +683,7 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         const int64_t base = obound[size_t(o0)];
         {
             Timed t(ctx, MGX_K_TRACE_EMIT);
-            launch_trace_emit(dm, dr, o0, o1, offs + h0, base, aidx, aZ, nullptr, ctx->d_status, ctx->stream);
+            launch_trace_emit(dm, dr, o0, o1, offs + h0, base, aidx, nullptr, nullptr, ctx->d_status, ctx->stream);
         }
         CK(cudaGetLastError());
         SolveArgs a;
@@ -696,7 +696,6 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         a.offs = offs + h0;
         a.base = base;
         a.idx = aidx;
-        a.Z = aZ;
         a.J = J;
         a.status = ctx->d_status;
         a.counters = ctx->prof ? ctx->d_counters : nullptr;
@@ -711,7 +710,6 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
     if (!p->out_on_device)
         CK(cudaMemcpyAsync(J_out, J, size_t(n) * size_t(NB) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     dfree(ctx, aidx);
-    dfree(ctx, aZ);
     dfree(ctx, offs);
     if (!p->out_on_device) dfree(ctx, J);
     return sync_status(ctx);
@@ -802,7 +800,7 @@ mgx_status mgx_profile_read(mgx_ctx *ctx, mgx_profile *out) {
     if (!ctx || !out) return MGX_EINVAL;
     ctx->err.clear();
     DeviceGuard g(ctx->device);
-    unsigned long long cnt[2] = {0, 0};
+    unsigned long long cnt[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     std::memset(out, 0, sizeof *out);
@@ -820,6 +818,8 @@ mgx_status mgx_profile_read(mgx_ctx *ctx, mgx_profile *out) {
     out->solves = ctx->solves;
     out->updates = int64_t(cnt[0]);
     out->samples = int64_t(cnt[1]);
+    out->trace_steps = int64_t(cnt[2]);
+    out->trace_exact_steps = int64_t(cnt[3]);
     return MGX_OK;
 }
 

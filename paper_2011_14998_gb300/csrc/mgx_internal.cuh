@@ -41,8 +41,9 @@ struct DevMesh {
     const float *vxf, *vyf, *vzf;
     const int32_t *off;  // [n+1]
     const int32_t *nbr;  // [E]
-    const float4 *phi, *plo;  // positions split as double ~ hi + lo, both float (w unused)
-    float g0;                 // 32 u^2 max_n (|x|+|y|+|z|): split-representation error floor
+    const float4 *phi;        // positions rounded to float (w unused)
+    const float4 *nrec;       // [E] neighbour records: fl32 position of nbr[e], id in w (as int bits)
+    float g0;                 // 32 u^2 max_n (|x|+|y|+|z|) + 1e-37: floor of the screen's error bounds
 };
 
 struct DevLines {
@@ -68,10 +69,10 @@ struct SolveArgs {
     const int64_t *offs;      // [2 npairs (o_end - o_begin) + 1] arena offsets (absolute)
     int64_t base;             // offs[first half-ray of the chunk]
     const int32_t *idx;       // arena point ids (relative to base)
-    const double *Z;          // arena projected distances
     double *J;                // [n][L*F]
     int *status;
-    unsigned long long *counters;  // nullable: [0] elimination updates, [1] optics samples
+    unsigned long long *counters;  // nullable: [0] elimination updates, [1] optics samples,
+                                   // [2] tracer steps, [3] tracer steps redone in double
     double w2[MGX_MAX_LEVEL + 1];  // 2 w_l = 2 / (12 4^l), pair weight of level l (Eq. 4)
 };
 
@@ -84,8 +85,10 @@ inline void fill_pair_weights(SolveArgs &a) {
 void launch_ingest_mesh(int32_t n, const double *pos_aos, const double *vel_aos, const int64_t *off64,
                         int64_t E, double *x, double *y, double *z, double *vx, double *vy,
                         double *vz, float *vxf, float *vyf, float *vzf, int32_t *off32,
-                        const int32_t *nbr, float4 *phi, float4 *plo, unsigned int *xmax_bits,
-                        int *status, cudaStream_t st);
+                        const int32_t *nbr, float4 *phi, unsigned int *xmax_bits, int *status,
+                        cudaStream_t st);
+void launch_pack_neighbours(int32_t n, const int32_t *off, const int32_t *nbr, const float4 *phi,
+                            float4 *nrec, cudaStream_t st);
 void launch_ingest_lines(int32_t n, int32_t L, const double *chi0, const double *eta0,
                          const double *dvw, const double *chic, const double *etac, float *chi0f,
                          float *eta0f, float *dvwf, float *chicf, float *etacf, int *status,
@@ -101,7 +104,8 @@ void launch_rays_adaptive(const DevMesh &m, int32_t lmin, int32_t lmax, int32_t 
 
 // ---- tracing (k_trace.cu)
 void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
-                        int64_t *lens, int *status, cudaStream_t st);
+                        int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st);
+// Z == nullptr: ids only (the solver's arena); otherwise also exact Z (and delta if given)
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
                        const int64_t *offs, int64_t base, int32_t *idx, double *Z, double *delta,
                        int *status, cudaStream_t st);

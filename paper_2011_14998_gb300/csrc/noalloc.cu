@@ -99,16 +99,14 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
         int64_t c = std::min<int64_t>(c_max, m.n - o0);
         int64_t *lens = nullptr, *offs = nullptr;
         int32_t *idx = nullptr;
-        double *Z = nullptr;
         for (;;) {
             const int64_t nh = c * np2;
             lens = reinterpret_cast<int64_t *>(base);
             offs = lens + nh;
             const size_t arena0 = align256(size_t(2 * nh + 1) * sizeof(int64_t));
-            const int64_t cap = int64_t((kNoAllocScratchBytes - arena0) / (sizeof(double) + sizeof(int32_t)));
-            Z = reinterpret_cast<double *>(base + arena0);
-            idx = reinterpret_cast<int32_t *>(base + arena0 + size_t(cap) * sizeof(double));
-            launch_trace_count(m, R, int32_t(o0), int32_t(o0 + c), lens, status, st);
+            const int64_t cap = int64_t((kNoAllocScratchBytes - arena0) / sizeof(int32_t));
+            idx = reinterpret_cast<int32_t *>(base + arena0);
+            launch_trace_count(m, R, int32_t(o0), int32_t(o0 + c), lens, status, nullptr, st);
             k_scan_lengths<<<1, 1024, 0, st>>>(lens, nh, offs);
             int64_t total = 0;
             if ((ce = cudaGetLastError()) != cudaSuccess ||
@@ -126,7 +124,7 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
             }
             c = std::max<int64_t>(1, int64_t(double(c) * double(cap) / double(total) * 0.9));
         }
-        launch_trace_emit(m, R, int32_t(o0), int32_t(o0 + c), offs, 0, idx, Z, nullptr, status, st);
+        launch_trace_emit(m, R, int32_t(o0), int32_t(o0 + c), offs, 0, idx, nullptr, nullptr, status, st);
         SolveArgs a;
         a.dtau_max = dtau_max;
         a.dv_max = dv_max;
@@ -137,7 +135,6 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
         a.offs = offs;
         a.base = 0;
         a.idx = idx;
-        a.Z = Z;
         a.J = J;
         a.status = status;
         a.counters = nullptr;
