@@ -1,15 +1,15 @@
 // k_solve.cu -- formal solution along ray pairs and the mean intensity J
 // (Eqs. 1-3, Sections 2.1.1-2.1.2).
 //
-// One warp per (origin, 32-bin frequency tile); lane = frequency bin.  The warp
-// walks every ray pair of its origin in ascending pair order.  For each half of
-// the pair it starts at the far end of the traced point list and eliminates
-// towards the origin:
+// One warp per (origin, frequency tile); each lane carries BPL frequency bins
+// (bin tile*32*BPL + lane + 32 i, i < BPL).  The warp walks every ray pair of
+// its origin in ascending pair order.  For each half of the pair it starts at
+// the far end of the traced point list and eliminates towards the origin:
 //   * adaptive velocity sampling (Section 2.1.1): between consecutive points
 //     whose projected velocities differ by more than dv_max times the smaller
 //     Doppler width, equally spaced samples with linearly interpolated data;
 //   * line optics: chi = chi_c + sum_l chi0_l exp(-a_l^2), eta likewise, a_l the
-//     Doppler-shifted profile argument of line l at this lane's frequency;
+//     Doppler-shifted profile argument of line l at the bin's frequency;
 //   * adaptive optical-depth increments (Eq. 2): each sample interval is split
 //     into n_inter = ceil(max(chi) ds / dtau_max) equal parts with chi and eta
 //     linear, trapezoidal dtau;
@@ -27,8 +27,14 @@
 // an empty half contributing (zh, D Fh) = (I, 1).  J accumulates 2 w u in
 // double precision with Neumaier's compensated sum.
 //
+// The frequency-independent work of a line point (staging, exact Z, projected
+// velocity, velocity sampling, interpolation, the width's reciprocal) is done
+// once per warp and shared by the lane's BPL bins.
+//
 // Template R selects the arithmetic: double (plain form) or float (the distance
 // increments come from double Z differences; J is summed in double).
+#include <cstdlib>
+
 #include "mgx_internal.cuh"
 
 namespace mgx {
@@ -71,6 +77,7 @@ struct Ar<float> {
     }
 };
 
+// Frequency-independent data of one line sample.
 template <typename R, int NL>
 struct Sample {
     R delta, dv, chic, etac;
@@ -116,22 +123,6 @@ __device__ __forceinline__ void load_sample(const Data<R> &D, int32_t L, int32_t
     }
 }
 
-// Total opacity and emissivity of a sample for this lane's bin.  Lines past
-// the model's count have chi0 = eta0 = 0 and contribute nothing.
-template <typename R, int NL>
-__device__ __forceinline__ void optics(const Sample<R, NL> &s, const R (&A)[NL], const R (&B)[NL], R &chi,
-                                       R &eta) {
-    chi = s.chic;
-    eta = s.etac;
-    const R rdv = Ar<R>::rcp(s.dv);
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        const R g = Ar<R>::gauss((A[l] + B[l] * s.delta) * rdv);
-        chi += s.chi0[l] * g;
-        eta += s.eta0[l] * g;
-    }
-}
-
 template <typename R, int NL>
 __device__ __forceinline__ void shfl_sample(const Sample<R, NL> &s, int j, Sample<R, NL> &o) {
     o.delta = __shfl_sync(0xffffffffu, s.delta, j);
@@ -145,10 +136,31 @@ __device__ __forceinline__ void shfl_sample(const Sample<R, NL> &s, int j, Sampl
     }
 }
 
-// State of the elimination along one half of a pair line.  Starting from
-// (Fh, D, zh, dtp) = (1, 1, I, 0) the interior row below reproduces the
-// second-order boundary row (Fh = 1 + dt/2, zh = D (S dt/2 + I)), and a half
-// without points leaves exactly the empty-half coupling (D Fh, zh) = (1, I).
+// Per-bin constants: the Doppler-shifted profile argument of line l at this
+// bin is (A[l] + B[l] delta) / dv (prescaled for the single-precision ex2).
+template <typename R, int NL>
+struct Bin {
+    R A[NL], B[NL];
+};
+
+// Total opacity and emissivity of a sample for one bin (rdv = 1 / dv).  Lines
+// past the model's count have chi0 = eta0 = 0 and contribute nothing.
+template <typename R, int NL>
+__device__ __forceinline__ void optics(const Sample<R, NL> &s, R rdv, const Bin<R, NL> &f, R &chi, R &eta) {
+    chi = s.chic;
+    eta = s.etac;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+        const R g = Ar<R>::gauss((f.A[l] + f.B[l] * s.delta) * rdv);
+        chi += s.chi0[l] * g;
+        eta += s.eta0[l] * g;
+    }
+}
+
+// State of the elimination of one bin along one half of a pair line.
+// Starting from (Fh, D, zh, dtp) = (1, 1, I, 0) the interior row reproduces
+// the second-order boundary row, and a half without points leaves exactly the
+// empty-half coupling (D Fh, zh) = (1, I).
 template <typename R>
 struct Sweep {
     R Fh, Dm, zh, dtp;  // scaled 1+B quantities of the last eliminated row, its dtau
@@ -169,50 +181,62 @@ __device__ __forceinline__ void row(Sweep<R> &w, R dt) {
     w.dtp = dt;
 }
 
-// One velocity sample q at distance hs beyond the previous one: line optics,
-// Eq. 2 sub-intervals with linear chi and eta, elimination rows.
-template <typename R, int NL>
+// One velocity sample q at distance hs beyond the previous one, for every bin
+// of the lane: line optics, Eq. 2 sub-intervals with linear chi and eta,
+// elimination rows.  When no bin of the warp needs sub-intervals (the common
+// case) the rows run as straight-line code, so the bins' chains interleave.
+template <typename R, int NL, int BPL>
 __device__ __forceinline__ void sample_step(const Sample<R, NL> &q, R hs, R dtau_max, R inv_dtau_max,
-                                            const R (&A)[NL], const R (&B)[NL], Sweep<R> &w, int *status,
-                                            unsigned &n_upd) {
-    R chi_q, eta_q;
-    optics<R, NL>(q, A, B, chi_q, eta_q);
-    const R nr = Ar<R>::ninter(fmax(w.chi_p, chi_q), hs, dtau_max, inv_dtau_max);
-    if (nr <= R(1)) {
-        row(w, hs * (w.chi_p + chi_q) * R(0.5));
-        w.chi_c = chi_q;
-        w.eta_c = eta_q;
-        ++n_upd;
-    } else {
-        int ni = int(fmin(nr, R(kMaxSubdiv)));
-        if (nr > R(kMaxSubdiv)) dev_fail(status, kDevSubdivLimit);
+                                            const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
+                                            int *status, unsigned &n_upd) {
+    const R rdv = Ar<R>::rcp(q.dv);
+    R chi_q[BPL], eta_q[BPL], nr[BPL];
+    bool split = false;
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) {
+        optics<R, NL>(q, rdv, f[i], chi_q[i], eta_q[i]);
+        nr[i] = Ar<R>::ninter(fmax(w[i].chi_p, chi_q[i]), hs, dtau_max, inv_dtau_max);
+        split |= nr[i] > R(1);
+    }
+    if (!__any_sync(0xffffffffu, split)) {
+#pragma unroll
+        for (int i = 0; i < BPL; ++i) {
+            row(w[i], hs * (w[i].chi_p + chi_q[i]) * R(0.5));
+            w[i].chi_c = w[i].chi_p = chi_q[i];
+            w[i].eta_c = w[i].eta_p = eta_q[i];
+            n_upd += act[i] ? 1u : 0u;
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) {
+        int ni = nr[i] <= R(1) ? 1 : int(fmin(nr[i], R(kMaxSubdiv)));
+        if (nr[i] > R(kMaxSubdiv)) dev_fail(status, kDevSubdivLimit);
         const R rni = R(1) / R(ni);
         const R hh = hs * rni * R(0.5);
-        const R dchi = (chi_q - w.chi_p) * rni, deta = (eta_q - w.eta_p) * rni;
-        R cprev = w.chi_p;
-        for (int i = 1; i < ni; ++i) {
-            const R ci = w.chi_p + dchi * R(i);
-            row(w, hh * (cprev + ci));
-            w.chi_c = ci;
-            w.eta_c = w.eta_p + deta * R(i);
-            cprev = ci;
+        const R dchi = (chi_q[i] - w[i].chi_p) * rni, deta = (eta_q[i] - w[i].eta_p) * rni;
+        R cprev = w[i].chi_p;
+        for (int k = 1; k < ni; ++k) {
+            const R ck = w[i].chi_p + dchi * R(k);
+            row(w[i], hh * (cprev + ck));
+            w[i].chi_c = ck;
+            w[i].eta_c = w[i].eta_p + deta * R(k);
+            cprev = ck;
         }
-        row(w, hh * (cprev + chi_q));
-        w.chi_c = chi_q;
-        w.eta_c = eta_q;
-        n_upd += unsigned(ni);
+        row(w[i], hh * (cprev + chi_q[i]));
+        w[i].chi_c = w[i].chi_p = chi_q[i];
+        w[i].eta_c = w[i].eta_p = eta_q[i];
+        n_upd += act[i] ? unsigned(ni) : 0u;
     }
-    w.chi_p = chi_q;
-    w.eta_p = eta_q;
 }
 
 // One interval between consecutive traced points (far -> near): adaptive
 // velocity sampling (Section 2.1.1), then each sample's optics and rows.
-template <typename R, int NL>
+template <typename R, int NL, int BPL>
 __device__ __forceinline__ void interval(const Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds,
                                          const SolveArgs &a, R dtau_max, R inv_dtau_max, R dv_max,
-                                         const R (&A)[NL], const R (&B)[NL], Sweep<R> &w, unsigned &n_upd,
-                                         unsigned &n_smp) {
+                                         const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
+                                         unsigned &n_upd, unsigned &n_smp) {
     int nv = 1;
     if (dv_max > R(0)) {
         const R jump = fabs(nxt.delta - cur.delta);
@@ -229,12 +253,12 @@ __device__ __forceinline__ void interval(const Sample<R, NL> &cur, const Sample<
     }
     n_smp += unsigned(nv);
     if (nv == 1) {
-        sample_step<R, NL>(nxt, ds, dtau_max, inv_dtau_max, A, B, w, a.status, n_upd);
+        sample_step<R, NL, BPL>(nxt, ds, dtau_max, inv_dtau_max, f, act, w, a.status, n_upd);
         return;
     }
     const R rnv = Ar<R>::rcp(R(nv));
     const R hs = ds * rnv;
-    Sample<R, NL> q = cur, st;
+    Sample<R, NL> q, st;
     st.delta = (nxt.delta - cur.delta) * rnv;
     st.dv = (nxt.dv - cur.dv) * rnv;
     st.chic = (nxt.chic - cur.chic) * rnv;
@@ -255,17 +279,11 @@ __device__ __forceinline__ void interval(const Sample<R, NL> &cur, const Sample<
             q.chi0[l] = cur.chi0[l] + st.chi0[l] * t;
             q.eta0[l] = cur.eta0[l] + st.eta0[l] * t;
         }
-        sample_step<R, NL>(q, hs, dtau_max, inv_dtau_max, A, B, w, a.status, n_upd);
+        sample_step<R, NL, BPL>(q, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_upd);
     }
-    sample_step<R, NL>(nxt, hs, dtau_max, inv_dtau_max, A, B, w, a.status, n_upd);
+    sample_step<R, NL, BPL>(nxt, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_upd);
 }
 
-// Eliminate one half of a pair line from its far end up to (excluding) the
-// origin row.  The warp stages 32 traced points at a time: lane j loads entry
-// kb - j (coalesced ids and distances, gathered point data, its projected
-// velocity and its distance to the farther neighbour), then the warp walks the
-// chunk, broadcasting each point with shuffles.  Returns the origin row's
-// coupling (P = D Fh, Q = zh) and the last optical-depth increment.
 // Projected distance Z = (x_n - x_o).d exactly as the tracer and its
 // definition form it (explicitly rounded double operations in fixed order).
 __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t id, double xo, double yo, double zo, double d0,
@@ -281,69 +299,80 @@ __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t id, double x
 // kb - j (coalesced ids, gathered point data), forms its exact Z and projected
 // velocity, and gets the distance to the farther entry from its neighbour lane;
 // then the warp walks the chunk, broadcasting each point with shuffles.
-// Returns the origin row's coupling (P = D Fh, Q = zh) and the last
-// optical-depth increment.
-template <typename R, int NL>
+// Leaves the origin row's coupling (P = D Fh, Q = zh) and the last
+// optical-depth increment in w.
+template <typename R, int NL, int BPL>
 __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &a, int32_t L, int lane,
                            int64_t beg, int32_t cnt, double xo, double yo, double zo, double e0, double e1,
-                           double e2, R vox, R voy, R voz, const Sample<R, NL> &origin, const R (&A)[NL],
-                           const R (&B)[NL], R &P, R &Q, R &dtl, unsigned &n_upd, unsigned &n_smp) {
-    Sweep<R> w;
-    w.Fh = R(1);
-    w.Dm = R(1);
-    w.zh = R(a.I_bdy);
-    w.dtp = R(0);
-    if (cnt > 0) {
-        const R dtau_max = R(a.dtau_max), inv_dtau_max = R(1.0 / a.dtau_max), dv_max = R(a.dv_max);
-        const R d0 = R(e0), d1 = R(e1), d2 = R(e2);
-        Sample<R, NL> cur, nxt, st;
-        double zcarry = 0.0;  // Z of the entry just beyond the current chunk (farther)
-        for (int32_t kb = cnt - 1; kb >= 0; kb -= 32) {
-            const int32_t nch = kb + 1 < 32 ? kb + 1 : 32;
-            double zk = 0.0;
-            if (lane < nch) {
-                const int32_t id = __ldg(a.idx + beg + kb - lane);
-                zk = exact_Z(m, id, xo, yo, zo, e0, e1, e2);
-                load_sample<R, NL>(D, L, id, vox, voy, voz, d0, d1, d2, st);
-            } else {
-                st = origin;
-            }
-            double zf = __shfl_up_sync(0xffffffffu, zk, 1);
-            if (lane == 0) zf = (kb == cnt - 1) ? zk : zcarry;
-            const R sds = R(zf - zk);  // distance increment, differenced in double
-            zcarry = __shfl_sync(0xffffffffu, zk, nch - 1);
-            for (int j = 0; j < nch; ++j) {
-                shfl_sample<R, NL>(st, j, nxt);
-                const R ds = __shfl_sync(0xffffffffu, sds, j);
-                if (kb == cnt - 1 && j == 0) {  // the far end: its row follows with the first increment
-                    cur = nxt;
-                    optics<R, NL>(cur, A, B, w.chi_p, w.eta_p);
-                    w.chi_c = w.chi_p;
-                    w.eta_c = w.eta_p;
-                    continue;
-                }
-                interval<R, NL>(cur, nxt, ds, a, dtau_max, inv_dtau_max, dv_max, A, B, w, n_upd, n_smp);
-                cur = nxt;
-            }
-        }
-        interval<R, NL>(cur, origin, R(zcarry), a, dtau_max, inv_dtau_max, dv_max, A, B, w, n_upd, n_smp);
+                           double e2, R vox, R voy, R voz, int32_t o, const Bin<R, NL> (&f)[BPL],
+                           const bool (&act)[BPL], Sweep<R> (&w)[BPL], unsigned &n_upd, unsigned &n_smp) {
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) {
+        w[i].Fh = R(1);
+        w[i].Dm = R(1);
+        w[i].zh = R(a.I_bdy);
+        w[i].dtp = R(0);
     }
-    P = w.Dm * w.Fh;
-    Q = w.zh;
-    dtl = w.dtp;
+    if (cnt == 0) return;
+    const R dtau_max = R(a.dtau_max), inv_dtau_max = R(1.0 / a.dtau_max), dv_max = R(a.dv_max);
+    const R d0 = R(e0), d1 = R(e1), d2 = R(e2);
+    Sample<R, NL> cur, nxt, st;
+    st.delta = st.dv = st.chic = st.etac = R(0);
+#pragma unroll
+    for (int l = 0; l < NL; ++l) st.chi0[l] = st.eta0[l] = R(0);
+    double zcarry = 0.0;  // Z of the entry just beyond the current chunk (farther)
+    for (int32_t kb = cnt - 1; kb >= 0; kb -= 32) {
+        const int32_t nch = kb + 1 < 32 ? kb + 1 : 32;
+        double zk = 0.0;
+        if (lane < nch) {
+            const int32_t id = __ldg(a.idx + beg + kb - lane);
+            zk = exact_Z(m, id, xo, yo, zo, e0, e1, e2);
+            load_sample<R, NL>(D, L, id, vox, voy, voz, d0, d1, d2, st);
+        }
+        double zf = __shfl_up_sync(0xffffffffu, zk, 1);
+        if (lane == 0) zf = (kb == cnt - 1) ? zk : zcarry;
+        const R sds = R(zf - zk);  // distance increment, differenced in double
+        zcarry = __shfl_sync(0xffffffffu, zk, nch - 1);
+        for (int j = 0; j < nch; ++j) {
+            shfl_sample<R, NL>(st, j, nxt);
+            const R ds = __shfl_sync(0xffffffffu, sds, j);
+            if (kb == cnt - 1 && j == 0) {  // the far end: its row follows with the first increment
+                cur = nxt;
+                const R rdv = Ar<R>::rcp(cur.dv);
+#pragma unroll
+                for (int i = 0; i < BPL; ++i) {
+                    optics<R, NL>(cur, rdv, f[i], w[i].chi_p, w[i].eta_p);
+                    w[i].chi_c = w[i].chi_p;
+                    w[i].eta_c = w[i].eta_p;
+                }
+                continue;
+            }
+            interval<R, NL, BPL>(cur, nxt, ds, a, dtau_max, inv_dtau_max, dv_max, f, act, w, n_upd, n_smp);
+            cur = nxt;
+        }
+    }
+    Sample<R, NL> origin;
+    load_sample<R, NL>(D, L, o, vox, voy, voz, R(0), R(0), R(0), origin);
+    origin.delta = R(0);
+    interval<R, NL, BPL>(cur, origin, R(zcarry), a, dtau_max, inv_dtau_max, dv_max, f, act, w, n_upd, n_smp);
 }
 
-template <typename R>
+// CTAs of 128 threads; the minimum resident CTAs per SM caps the registers
+template <typename R, int BPL>
 struct Occ {
     static constexpr int kMinBlocks = 1;
 };
 template <>
-struct Occ<float> {
-    static constexpr int kMinBlocks = 2;  // 16 warps per SM without spills
+struct Occ<float, 1> {
+    static constexpr int kMinBlocks = 4;  // 16 warps per SM, at most 128 registers
+};
+template <>
+struct Occ<float, 2> {
+    static constexpr int kMinBlocks = 3;  // 12 warps per SM, at most 168 registers
 };
 
-template <typename R, int NL>
-__global__ void __launch_bounds__(256, Occ<R>::kMinBlocks)
+template <typename R, int NL, int BPL>
+__global__ void __launch_bounds__(128, (Occ<R, BPL>::kMinBlocks))
 k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t item = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -353,65 +382,80 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
     const int32_t o = a.o_begin + oc;
     const int32_t tile = int32_t(item % a.n_tiles);
     const int32_t L = Ln.L, F = Ln.F, NB = L * F;
-    const int32_t b = tile * 32 + lane;
-    const bool active = b < NB;
-    const int32_t bb = active ? b : NB - 1;
-    const int32_t l = bb / F, k = bb % F;
-
     const Data<R> D(m, Ln);
-    // frequency of this lane and the profile constants of every line
-    const double x = (F == 1) ? 0.0 : -Ln.x_span + 2.0 * Ln.x_span * double(k) / double(F - 1);
     const double dvo = Ln.dvw[o];
-    const double ub = x * dvo;
-    R A[NL], B[NL];
-#pragma unroll
-    for (int lp = 0; lp < NL; ++lp) {
-        const double r = (lp < L) ? Ln.ratio[l * MGX_MAX_LINES + lp] : 1.0;
-        A[lp] = R((kC * (r - 1.0) + r * ub) * Ar<R>::kArgScale);
-        B[lp] = R(r * (1.0 + ub / kC) * Ar<R>::kArgScale);
-    }
     const R vox = __ldg(D.vx + o), voy = __ldg(D.vy + o), voz = __ldg(D.vz + o);
     const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
     Sample<R, NL> org;
     load_sample<R, NL>(D, L, o, vox, voy, voz, R(0), R(0), R(0), org);
     org.delta = R(0);
-    R chi_o, eta_o;
-    optics<R, NL>(org, A, B, chi_o, eta_o);
-    const R S_o = eta_o / chi_o;
+    const R rdvo = Ar<R>::rcp(org.dv);
 
-    double sum = 0.0, comp = 0.0;
+    // frequency of each bin of this lane and its profile constants
+    Bin<R, NL> f[BPL];
+    int32_t bin[BPL];
+    bool act[BPL];
+    R S_o[BPL];
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) {
+        const int32_t b = tile * 32 * BPL + lane + 32 * i;
+        bin[i] = b;
+        act[i] = b < NB;
+        const int32_t bb = b < NB ? b : NB - 1;
+        const int32_t l = bb / F, k = bb % F;
+        const double x = (F == 1) ? 0.0 : -Ln.x_span + 2.0 * Ln.x_span * double(k) / double(F - 1);
+        const double ub = x * dvo;
+#pragma unroll
+        for (int lp = 0; lp < NL; ++lp) {
+            const double r = (lp < L) ? Ln.ratio[l * MGX_MAX_LINES + lp] : 1.0;
+            f[i].A[lp] = R((kC * (r - 1.0) + r * ub) * Ar<R>::kArgScale);
+            f[i].B[lp] = R(r * (1.0 + ub / kC) * Ar<R>::kArgScale);
+        }
+        R chi_o, eta_o;
+        optics<R, NL>(org, rdvo, f[i], chi_o, eta_o);
+        S_o[i] = eta_o / chi_o;
+    }
+
+    double sum[BPL], comp[BPL];
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) sum[i] = comp[i] = 0.0;
     unsigned n_upd = 0, n_smp = 0;
     const int64_t h0 = int64_t(oc) * Rs.npairs * 2;
+    Sweep<R> wb[BPL], wf[BPL];
     for (int32_t p = 0; p < Rs.npairs; ++p) {
         const uint32_t ray = __ldg(Rs.rays + int64_t(o) * Rs.npairs + p);
         const int lev = int(ray >> 28);
         const double *rv = Rs.dir + 3 * (level_offset(lev) + (ray & 0x0FFFFFFFu));
         const double r0 = rv[0], r1 = rv[1], r2 = rv[2];
-        R P0, Q0, t0, P1, Q1, t1;
         const int64_t hb = h0 + 2 * int64_t(p);
-        {
-            const int64_t beg = a.offs[hb] - a.base;
-            const int32_t cnt = int32_t(a.offs[hb + 1] - a.offs[hb]);
-            half_sweep<R, NL>(m, D, a, L, lane, beg, cnt, xo, yo, zo, -r0, -r1, -r2, vox, voy, voz, org, A, B,
-                              P0, Q0, t0, n_upd, n_smp);
+        half_sweep<R, NL, BPL>(m, D, a, L, lane, a.offs[hb] - a.base, int32_t(a.offs[hb + 1] - a.offs[hb]), xo, yo,
+                               zo, -r0, -r1, -r2, vox, voy, voz, o, f, act, wb, n_upd, n_smp);
+        half_sweep<R, NL, BPL>(m, D, a, L, lane, a.offs[hb + 1] - a.base, int32_t(a.offs[hb + 2] - a.offs[hb + 1]),
+                               xo, yo, zo, r0, r1, r2, vox, voy, voz, o, f, act, wf, n_upd, n_smp);
+        const double w2 = a.w2[lev];
+#pragma unroll
+        for (int i = 0; i < BPL; ++i) {
+            const R dtb = (wb[i].dtp + wf[i].dtp) * R(0.5);
+            const R u = (dtb * S_o[i] + wb[i].zh + wf[i].zh) / (dtb + wb[i].Dm * wb[i].Fh + wf[i].Dm * wf[i].Fh);
+            const double xv = w2 * double(u);
+            const double t = sum[i] + xv;  // Neumaier compensated sum
+            if (fabs(sum[i]) >= fabs(xv)) comp[i] += (sum[i] - t) + xv;
+            else comp[i] += (xv - t) + sum[i];
+            sum[i] = t;
         }
-        {
-            const int64_t beg = a.offs[hb + 1] - a.base;
-            const int32_t cnt = int32_t(a.offs[hb + 2] - a.offs[hb + 1]);
-            half_sweep<R, NL>(m, D, a, L, lane, beg, cnt, xo, yo, zo, r0, r1, r2, vox, voy, voz, org, A, B,
-                              P1, Q1, t1, n_upd, n_smp);
-        }
-        const R dtb = (t0 + t1) * R(0.5);
-        const R u = (dtb * S_o + Q0 + Q1) / (dtb + P0 + P1);
-        const double xv = a.w2[lev] * double(u);
-        const double t = sum + xv;  // Neumaier compensated sum
-        if (fabs(sum) >= fabs(xv)) comp += (sum - t) + xv;
-        else comp += (xv - t) + sum;
-        sum = t;
     }
-    if (active) a.J[int64_t(o) * NB + b] = sum + comp;
+    unsigned n_act = 0;
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) {
+        if (act[i]) {
+            a.J[int64_t(o) * NB + bin[i]] = sum[i] + comp[i];
+            ++n_act;
+        }
+    }
     if (a.counters) {
-        unsigned long long u = active ? n_upd : 0, s = active ? n_smp : 0;
+        // updates are counted per active bin; samples per lane, times its active bins
+        unsigned long long u = n_upd;
+        unsigned long long s = (unsigned long long)n_smp * n_act;
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) {
             u += __shfl_down_sync(0xffffffffu, u, sh);
@@ -424,24 +468,36 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
     }
 }
 
-template <typename R>
-void launch_R(const DevMesh &m, const DevLines &Ln, const DevRays &R_, const SolveArgs &a, cudaStream_t st) {
+template <typename R, int BPL>
+void launch_RB(const DevMesh &m, const DevLines &Ln, const DevRays &R_, const SolveArgs &a, cudaStream_t st) {
     const int64_t n_items = int64_t(a.o_end - a.o_begin) * a.n_tiles;
     if (n_items == 0) return;
-    const int tb = 256;
+    const int tb = 128;
     const unsigned grid = unsigned((n_items * 32 + tb - 1) / tb);
-    if (Ln.L <= 1) k_solve<R, 1><<<grid, tb, 0, st>>>(m, Ln, R_, a);
-    else if (Ln.L <= 2) k_solve<R, 2><<<grid, tb, 0, st>>>(m, Ln, R_, a);
-    else if (Ln.L <= 4) k_solve<R, 4><<<grid, tb, 0, st>>>(m, Ln, R_, a);
-    else k_solve<R, 8><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+    if (Ln.L <= 1) k_solve<R, 1, BPL><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+    else if (Ln.L <= 2) k_solve<R, 2, BPL><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+    else if (Ln.L <= 4) k_solve<R, 4, BPL><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+    else k_solve<R, 8, BPL><<<grid, tb, 0, st>>>(m, Ln, R_, a);
 }
 
 }  // namespace
 
+// Bins per lane of the single-precision kernel: 2 when there are more bins than
+// lanes (the frequency-independent work is then shared by two bins), else 1.
+// MGX_BINS_PER_LANE=1|2 overrides the choice (tuning).
+int solve_bins_per_lane(int precision, int32_t n_bins) {
+    if (precision != MGX_FP32) return 1;
+    const char *env = getenv("MGX_BINS_PER_LANE");
+    if (env && (env[0] == '1' || env[0] == '2') && env[1] == 0) return env[0] - '0';
+    return n_bins > 32 ? 2 : 1;
+}
+
 void launch_solve(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a,
                   int precision, cudaStream_t st) {
-    if (precision == MGX_FP64) launch_R<double>(m, Ln, R, a, st);
-    else launch_R<float>(m, Ln, R, a, st);
+    const int bpl = solve_bins_per_lane(precision, Ln.L * Ln.F);
+    if (precision == MGX_FP64) launch_RB<double, 1>(m, Ln, R, a, st);
+    else if (bpl == 2) launch_RB<float, 2>(m, Ln, R, a, st);
+    else launch_RB<float, 1>(m, Ln, R, a, st);
 }
 
 }  // namespace mgx

@@ -692,7 +692,10 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         a.I_bdy = p->I_bdy;
         a.o_begin = o0;
         a.o_end = o1;
-        a.n_tiles = int32_t((NB + 31) / 32);
+        {
+            const int64_t per = 32 * solve_bins_per_lane(p->precision, int32_t(NB));
+            a.n_tiles = int32_t((NB + per - 1) / per);
+        }
         a.offs = offs + h0;
         a.base = base;
         a.idx = aidx;

@@ -65,7 +65,7 @@ struct DevRays {
 struct SolveArgs {
     double dtau_max, dv_max, I_bdy;
     int32_t o_begin, o_end;   // origins of this chunk
-    int32_t n_tiles;          // frequency tiles of 32 bins per origin
+    int32_t n_tiles;          // frequency tiles per origin (32 x bins-per-lane bins each)
     const int64_t *offs;      // [2 npairs (o_end - o_begin) + 1] arena offsets (absolute)
     int64_t base;             // offs[first half-ray of the chunk]
     const int32_t *idx;       // arena point ids (relative to base)
@@ -111,6 +111,9 @@ void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int3
                        int *status, cudaStream_t st);
 
 // ---- formal solution (k_solve.cu)
+// frequency bins per lane of the solve kernel; a chunk has
+// ceil(n_bins / (32 * bins_per_lane)) tiles per origin
+int solve_bins_per_lane(int precision, int32_t n_bins);
 void launch_solve(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a,
                   int precision, cudaStream_t st);
 

@@ -131,7 +131,10 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
         a.I_bdy = I_bdy;
         a.o_begin = int32_t(o0);
         a.o_end = int32_t(o0 + c);
-        a.n_tiles = int32_t((NB + 31) / 32);
+        {
+            const int64_t per = 32 * solve_bins_per_lane(precision, int32_t(NB));
+            a.n_tiles = int32_t((NB + per - 1) / per);
+        }
         a.offs = offs;
         a.base = 0;
         a.idx = idx;
