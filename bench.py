@@ -345,6 +345,28 @@ def run_mgx(args):
         torch.distributed.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Two FP32 solves of an N-point wind (same generator and settings as the
+    benchmark), for profiler captures of single kernel launches."""
+    import torch
+
+    import paper_2011_14998_gb300 as mgx
+
+    mgx.build()
+    n = args.profile_case
+    m = make_workload(n)
+    ctx = mgx.Context(0)
+    mid = ctx.load(m)
+    out = torch.empty((n, len(m["nu0"]) * int(m["n_freq"])), dtype=torch.float64, device="cuda")
+    prec = mgx.MGX_FP64 if args.profile_fp64 else mgx.MGX_FP32
+    ctx.profile(True)
+    for _ in range(2):
+        ctx.solve_J(mid, precision=prec, dtau_max=0.5, dv_max=1.0 / 3.0, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": n, "counters": ctx.profile_read()}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,8 +376,13 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0,
+                    help="only run two solves of an N-point wind (for profiler captures)")
+    ap.add_argument("--profile-fp64", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_mgx(args)
