@@ -51,8 +51,8 @@ struct Ar<double> {
     static constexpr double kArgScale = 1.0;
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ double gauss(double a) { return exp(-(a * a)); }
-    static __device__ __forceinline__ double ninter(double cm, double hs, double dtau_max, double) {
-        return ceil(cm * hs / dtau_max);
+    static __device__ __forceinline__ double ratio(double cm, double hs, double dtau_max, double) {
+        return cm * hs / dtau_max;
     }
 };
 
@@ -72,8 +72,8 @@ struct Ar<float> {
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(-(a * a)));
         return r;
     }
-    static __device__ __forceinline__ float ninter(float cm, float hs, float, float inv_dtau_max) {
-        return ceilf((cm * hs) * inv_dtau_max);
+    static __device__ __forceinline__ float ratio(float cm, float hs, float, float inv_dtau_max) {
+        return (cm * hs) * inv_dtau_max;
     }
 };
 
@@ -164,20 +164,19 @@ __device__ __forceinline__ void optics(const Sample<R, NL> &s, R rdv, const Bin<
 template <typename R>
 struct Sweep {
     R Fh, Dm, zh, dtp;  // scaled 1+B quantities of the last eliminated row, its dtau
-    R chi_c, eta_c;     // optics of the current (not yet eliminated) sub-point
-    R chi_p, eta_p;     // optics of the current velocity sample
+    R chi, eta;         // optics of the current (not yet eliminated) sample
 };
 
-// Eliminate the row of the current sub-point once the increment dt beyond it
-// is known.  One reciprocal R = 1 / (chi (1 + dt Fh)) gives D = chi R and
-// D S = eta R.
+// Eliminate the row of the current sub-point (optics chi, eta) once the
+// increment dt beyond it is known.  One reciprocal R = 1 / (chi (1 + dt Fh))
+// gives D = chi R and D S = eta R.
 template <typename R>
-__device__ __forceinline__ void row(Sweep<R> &w, R dt) {
+__device__ __forceinline__ void row(Sweep<R> &w, R chi, R eta, R dt) {
     const R dtb = (w.dtp + dt) * R(0.5);
     w.Fh = dtb + w.Dm * w.Fh;
-    const R rr = Ar<R>::rcp(w.chi_c * (R(1) + dt * w.Fh));
-    w.Dm = w.chi_c * rr;
-    w.zh = w.Dm * w.zh + dtb * (w.eta_c * rr);
+    const R rr = Ar<R>::rcp(chi * (R(1) + dt * w.Fh));
+    w.Dm = chi * rr;
+    w.zh = w.Dm * w.zh + dtb * (eta * rr);
     w.dtp = dt;
 }
 
@@ -188,100 +187,102 @@ __device__ __forceinline__ void row(Sweep<R> &w, R dt) {
 template <typename R, int NL, int BPL>
 __device__ __forceinline__ void sample_step(const Sample<R, NL> &q, R hs, R dtau_max, R inv_dtau_max,
                                             const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
-                                            int *status, unsigned &n_upd) {
+                                            int *status, unsigned &n_extra) {
     const R rdv = Ar<R>::rcp(q.dv);
-    R chi_q[BPL], eta_q[BPL], nr[BPL];
+    R chi_q[BPL], eta_q[BPL], x[BPL];
     bool split = false;
 #pragma unroll
     for (int i = 0; i < BPL; ++i) {
         optics<R, NL>(q, rdv, f[i], chi_q[i], eta_q[i]);
-        nr[i] = Ar<R>::ninter(fmax(w[i].chi_p, chi_q[i]), hs, dtau_max, inv_dtau_max);
-        split |= nr[i] > R(1);
+        x[i] = Ar<R>::ratio(fmax(w[i].chi, chi_q[i]), hs, dtau_max, inv_dtau_max);  // Eq. 2 before the ceiling
+        split |= x[i] > R(1);
     }
     if (!__any_sync(0xffffffffu, split)) {
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
-            row(w[i], hs * (w[i].chi_p + chi_q[i]) * R(0.5));
-            w[i].chi_c = w[i].chi_p = chi_q[i];
-            w[i].eta_c = w[i].eta_p = eta_q[i];
-            n_upd += act[i] ? 1u : 0u;
+            row(w[i], w[i].chi, w[i].eta, hs * (w[i].chi + chi_q[i]) * R(0.5));
+            w[i].chi = chi_q[i];
+            w[i].eta = eta_q[i];
         }
         return;
     }
 #pragma unroll
     for (int i = 0; i < BPL; ++i) {
-        int ni = nr[i] <= R(1) ? 1 : int(fmin(nr[i], R(kMaxSubdiv)));
-        if (nr[i] > R(kMaxSubdiv)) dev_fail(status, kDevSubdivLimit);
+        const R nr = ceil(x[i]);
+        int ni = nr <= R(1) ? 1 : int(fmin(nr, R(kMaxSubdiv)));
+        if (nr > R(kMaxSubdiv)) dev_fail(status, kDevSubdivLimit);
         const R rni = R(1) / R(ni);
         const R hh = hs * rni * R(0.5);
-        const R dchi = (chi_q[i] - w[i].chi_p) * rni, deta = (eta_q[i] - w[i].eta_p) * rni;
-        R cprev = w[i].chi_p;
+        const R c0 = w[i].chi, e0 = w[i].eta;
+        const R dchi = (chi_q[i] - c0) * rni, deta = (eta_q[i] - e0) * rni;
+        R cprev = c0, eprev = e0;
         for (int k = 1; k < ni; ++k) {
-            const R ck = w[i].chi_p + dchi * R(k);
-            row(w[i], hh * (cprev + ck));
-            w[i].chi_c = ck;
-            w[i].eta_c = w[i].eta_p + deta * R(k);
+            const R ck = c0 + dchi * R(k);
+            row(w[i], cprev, eprev, hh * (cprev + ck));
             cprev = ck;
+            eprev = e0 + deta * R(k);
         }
-        row(w[i], hh * (cprev + chi_q[i]));
-        w[i].chi_c = w[i].chi_p = chi_q[i];
-        w[i].eta_c = w[i].eta_p = eta_q[i];
-        n_upd += act[i] ? unsigned(ni) : 0u;
+        row(w[i], cprev, eprev, hh * (cprev + chi_q[i]));
+        w[i].chi = chi_q[i];
+        w[i].eta = eta_q[i];
+        n_extra += act[i] ? unsigned(ni - 1) : 0u;
     }
 }
 
-// One interval between consecutive traced points (far -> near): adaptive
-// velocity sampling (Section 2.1.1), then each sample's optics and rows.
+// Velocity samples of the interval between consecutive points a (farther)
+// and b (Section 2.1.1): ceil(|delta_b - delta_a| / (dv_max min(dv_a, dv_b)))
+// when that exceeds one, else 1.
+template <typename R>
+__device__ __forceinline__ int velocity_samples(R da, R wa, R db, R wb, R dv_max, int *status) {
+    if (!(dv_max > R(0))) return 1;
+    const R jump = fabs(db - da);
+    const R lim = dv_max * fmin(wa, wb);
+    if (!(jump > lim)) return 1;
+    const R nvr = ceil(jump / lim);
+    if (nvr > R(kMaxSubdiv)) {
+        dev_fail(status, kDevSubdivLimit);
+        return kMaxSubdiv;
+    }
+    return int(nvr);
+}
+
+// One interval from the current point (cur, modified in place) to nxt with nv
+// velocity samples: interpolated samples, then nxt itself.
 template <typename R, int NL, int BPL>
-__device__ __forceinline__ void interval(const Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds,
-                                         const SolveArgs &a, R dtau_max, R inv_dtau_max, R dv_max,
+__device__ __forceinline__ void interval(Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds, int nv,
+                                         const SolveArgs &a, R dtau_max, R inv_dtau_max,
                                          const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
-                                         unsigned &n_upd, unsigned &n_smp) {
-    int nv = 1;
-    if (dv_max > R(0)) {
-        const R jump = fabs(nxt.delta - cur.delta);
-        const R lim = dv_max * fmin(cur.dv, nxt.dv);
-        if (jump > lim) {
-            const R nvr = ceil(jump / lim);
-            if (nvr > R(kMaxSubdiv)) {
-                dev_fail(a.status, kDevSubdivLimit);
-                nv = kMaxSubdiv;
-            } else {
-                nv = int(nvr);
-            }
-        }
-    }
-    n_smp += unsigned(nv);
-    if (nv == 1) {
-        sample_step<R, NL, BPL>(nxt, ds, dtau_max, inv_dtau_max, f, act, w, a.status, n_upd);
-        return;
-    }
-    const R rnv = Ar<R>::rcp(R(nv));
-    const R hs = ds * rnv;
-    Sample<R, NL> q, st;
-    st.delta = (nxt.delta - cur.delta) * rnv;
-    st.dv = (nxt.dv - cur.dv) * rnv;
-    st.chic = (nxt.chic - cur.chic) * rnv;
-    st.etac = (nxt.etac - cur.etac) * rnv;
-#pragma unroll
-    for (int l = 0; l < NL; ++l) {
-        st.chi0[l] = (nxt.chi0[l] - cur.chi0[l]) * rnv;
-        st.eta0[l] = (nxt.eta0[l] - cur.eta0[l]) * rnv;
-    }
-    for (int j = 1; j < nv; ++j) {
-        const R t = R(j);
-        q.delta = cur.delta + st.delta * t;
-        q.dv = cur.dv + st.dv * t;
-        q.chic = cur.chic + st.chic * t;
-        q.etac = cur.etac + st.etac * t;
+                                         unsigned &n_extra) {
+    if (nv > 1) {
+        const R rnv = Ar<R>::rcp(R(nv));
+        const R hs = ds * rnv;
+        Sample<R, NL> st;
+        st.delta = (nxt.delta - cur.delta) * rnv;
+        st.dv = (nxt.dv - cur.dv) * rnv;
+        st.chic = (nxt.chic - cur.chic) * rnv;
+        st.etac = (nxt.etac - cur.etac) * rnv;
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-            q.chi0[l] = cur.chi0[l] + st.chi0[l] * t;
-            q.eta0[l] = cur.eta0[l] + st.eta0[l] * t;
+            st.chi0[l] = (nxt.chi0[l] - cur.chi0[l]) * rnv;
+            st.eta0[l] = (nxt.eta0[l] - cur.eta0[l]) * rnv;
         }
-        sample_step<R, NL, BPL>(q, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_upd);
+        for (int j = 1; j < nv; ++j) {
+            cur.delta += st.delta;
+            cur.dv += st.dv;
+            cur.chic += st.chic;
+            cur.etac += st.etac;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                cur.chi0[l] += st.chi0[l];
+                cur.eta0[l] += st.eta0[l];
+            }
+            sample_step<R, NL, BPL>(cur, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+        }
+        sample_step<R, NL, BPL>(nxt, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+    } else {
+        sample_step<R, NL, BPL>(nxt, ds, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
     }
-    sample_step<R, NL, BPL>(nxt, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_upd);
+    cur = nxt;
 }
 
 // Projected distance Z = (x_n - x_o).d exactly as the tracer and its
@@ -294,18 +295,28 @@ __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t id, double x
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2));
 }
 
+// Per-warp staging area of 32 line points in shared memory.
+template <typename R, int NL>
+struct Stage {
+    R delta[32], dv[32], chic[32], etac[32], ds[32];
+    R chi0[NL][32], eta0[NL][32];
+    int nv[32];
+};
+
 // Eliminate one half of a pair line from its far end up to (excluding) the
 // origin row.  The warp stages 32 traced points at a time: lane j takes entry
-// kb - j (coalesced ids, gathered point data), forms its exact Z and projected
-// velocity, and gets the distance to the farther entry from its neighbour lane;
-// then the warp walks the chunk, broadcasting each point with shuffles.
+// kb - j (coalesced ids, gathered point data), forms its exact Z, projected
+// velocity, the distance to the farther entry and that interval's number of
+// velocity samples (its neighbour lane holds the farther entry), and writes
+// them to the warp's shared staging area; then the warp walks the chunk.
 // Leaves the origin row's coupling (P = D Fh, Q = zh) and the last
 // optical-depth increment in w.
 template <typename R, int NL, int BPL>
 __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &a, int32_t L, int lane,
-                           int64_t beg, int32_t cnt, double xo, double yo, double zo, double e0, double e1,
-                           double e2, R vox, R voy, R voz, int32_t o, const Bin<R, NL> (&f)[BPL],
-                           const bool (&act)[BPL], Sweep<R> (&w)[BPL], unsigned &n_upd, unsigned &n_smp) {
+                           Stage<R, NL> &sg, int64_t beg, int32_t cnt, double xo, double yo, double zo,
+                           double e0, double e1, double e2, R vox, R voy, R voz, int32_t o,
+                           const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
+                           unsigned &n_extra, unsigned &n_smp) {
 #pragma unroll
     for (int i = 0; i < BPL; ++i) {
         w[i].Fh = R(1);
@@ -316,63 +327,84 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
     if (cnt == 0) return;
     const R dtau_max = R(a.dtau_max), inv_dtau_max = R(1.0 / a.dtau_max), dv_max = R(a.dv_max);
     const R d0 = R(e0), d1 = R(e1), d2 = R(e2);
-    Sample<R, NL> cur, nxt, st;
-    st.delta = st.dv = st.chic = st.etac = R(0);
-#pragma unroll
-    for (int l = 0; l < NL; ++l) st.chi0[l] = st.eta0[l] = R(0);
-    double zcarry = 0.0;  // Z of the entry just beyond the current chunk (farther)
+    Sample<R, NL> cur, nxt;
+    double zcarry = 0.0;          // Z of the entry just beyond the current chunk (farther)
+    R dcarry = R(0), wcarry = R(1);  // its projected velocity and width
     for (int32_t kb = cnt - 1; kb >= 0; kb -= 32) {
         const int32_t nch = kb + 1 < 32 ? kb + 1 : 32;
         double zk = 0.0;
+        Sample<R, NL> st;
+        st.delta = st.dv = R(1);
         if (lane < nch) {
             const int32_t id = __ldg(a.idx + beg + kb - lane);
             zk = exact_Z(m, id, xo, yo, zo, e0, e1, e2);
             load_sample<R, NL>(D, L, id, vox, voy, voz, d0, d1, d2, st);
         }
         double zf = __shfl_up_sync(0xffffffffu, zk, 1);
-        if (lane == 0) zf = (kb == cnt - 1) ? zk : zcarry;
-        const R sds = R(zf - zk);  // distance increment, differenced in double
+        R df = __shfl_up_sync(0xffffffffu, st.delta, 1), wf = __shfl_up_sync(0xffffffffu, st.dv, 1);
+        const bool far_end = kb == cnt - 1 && lane == 0;
+        if (lane == 0) {
+            zf = far_end ? zk : zcarry;
+            df = far_end ? st.delta : dcarry;
+            wf = far_end ? st.dv : wcarry;
+        }
         zcarry = __shfl_sync(0xffffffffu, zk, nch - 1);
+        dcarry = __shfl_sync(0xffffffffu, st.delta, nch - 1);
+        wcarry = __shfl_sync(0xffffffffu, st.dv, nch - 1);
+        __syncwarp();
+        if (lane < nch) {
+            sg.delta[lane] = st.delta;
+            sg.dv[lane] = st.dv;
+            sg.chic[lane] = st.chic;
+            sg.etac[lane] = st.etac;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                sg.chi0[l][lane] = st.chi0[l];
+                sg.eta0[l][lane] = st.eta0[l];
+            }
+            sg.ds[lane] = R(zf - zk);  // distance increment, differenced in double
+            sg.nv[lane] = far_end ? 0 : velocity_samples<R>(df, wf, st.delta, st.dv, dv_max, a.status);
+        }
+        __syncwarp();
         for (int j = 0; j < nch; ++j) {
-            shfl_sample<R, NL>(st, j, nxt);
-            const R ds = __shfl_sync(0xffffffffu, sds, j);
-            if (kb == cnt - 1 && j == 0) {  // the far end: its row follows with the first increment
+            nxt.delta = sg.delta[j];
+            nxt.dv = sg.dv[j];
+            nxt.chic = sg.chic[j];
+            nxt.etac = sg.etac[j];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                nxt.chi0[l] = sg.chi0[l][j];
+                nxt.eta0[l] = sg.eta0[l][j];
+            }
+            const int nv = sg.nv[j];
+            if (nv == 0) {  // the far end: its row follows with the first increment
                 cur = nxt;
                 const R rdv = Ar<R>::rcp(cur.dv);
 #pragma unroll
-                for (int i = 0; i < BPL; ++i) {
-                    optics<R, NL>(cur, rdv, f[i], w[i].chi_p, w[i].eta_p);
-                    w[i].chi_c = w[i].chi_p;
-                    w[i].eta_c = w[i].eta_p;
-                }
+                for (int i = 0; i < BPL; ++i) optics<R, NL>(cur, rdv, f[i], w[i].chi, w[i].eta);
                 continue;
             }
-            interval<R, NL, BPL>(cur, nxt, ds, a, dtau_max, inv_dtau_max, dv_max, f, act, w, n_upd, n_smp);
-            cur = nxt;
+            n_smp += unsigned(nv);
+            interval<R, NL, BPL>(cur, nxt, sg.ds[j], nv, a, dtau_max, inv_dtau_max, f, act, w, n_extra);
         }
     }
     Sample<R, NL> origin;
     load_sample<R, NL>(D, L, o, vox, voy, voz, R(0), R(0), R(0), origin);
     origin.delta = R(0);
-    interval<R, NL, BPL>(cur, origin, R(zcarry), a, dtau_max, inv_dtau_max, dv_max, f, act, w, n_upd, n_smp);
+    const int nv = velocity_samples<R>(cur.delta, cur.dv, origin.delta, origin.dv, dv_max, a.status);
+    n_smp += unsigned(nv);
+    interval<R, NL, BPL>(cur, origin, R(zcarry), nv, a, dtau_max, inv_dtau_max, f, act, w, n_extra);
 }
 
 // CTAs of 128 threads; the minimum resident CTAs per SM caps the registers
-template <typename R, int BPL>
+// (4 CTAs: 128 registers, 3 CTAs: 168) at the largest occupancy without spills.
+template <typename R, int NL, int BPL>
 struct Occ {
-    static constexpr int kMinBlocks = 1;
-};
-template <>
-struct Occ<float, 1> {
-    static constexpr int kMinBlocks = 4;  // 16 warps per SM, at most 128 registers
-};
-template <>
-struct Occ<float, 2> {
-    static constexpr int kMinBlocks = 3;  // 12 warps per SM, at most 168 registers
+    static constexpr int kMinBlocks = (sizeof(R) == 4 && (NL == 1 || BPL == 1)) ? 4 : (sizeof(R) == 4 ? 3 : 1);
 };
 
 template <typename R, int NL, int BPL>
-__global__ void __launch_bounds__(128, (Occ<R, BPL>::kMinBlocks))
+__global__ void __launch_bounds__(128, (Occ<R, NL, BPL>::kMinBlocks))
 k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t item = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -389,6 +421,7 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
     Sample<R, NL> org;
     load_sample<R, NL>(D, L, o, vox, voy, voz, R(0), R(0), R(0), org);
     org.delta = R(0);
+    (void)sizeof(org);
     const R rdvo = Ar<R>::rcp(org.dv);
 
     // frequency of each bin of this lane and its profile constants
@@ -416,10 +449,12 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
         S_o[i] = eta_o / chi_o;
     }
 
+    __shared__ Stage<R, NL> stage[4];  // one per warp of the 128-thread CTA
+    Stage<R, NL> &sg = stage[threadIdx.x >> 5];
     double sum[BPL], comp[BPL];
 #pragma unroll
     for (int i = 0; i < BPL; ++i) sum[i] = comp[i] = 0.0;
-    unsigned n_upd = 0, n_smp = 0;
+    unsigned n_extra = 0, n_smp = 0;
     const int64_t h0 = int64_t(oc) * Rs.npairs * 2;
     Sweep<R> wb[BPL], wf[BPL];
     for (int32_t p = 0; p < Rs.npairs; ++p) {
@@ -428,10 +463,11 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
         const double *rv = Rs.dir + 3 * (level_offset(lev) + (ray & 0x0FFFFFFFu));
         const double r0 = rv[0], r1 = rv[1], r2 = rv[2];
         const int64_t hb = h0 + 2 * int64_t(p);
-        half_sweep<R, NL, BPL>(m, D, a, L, lane, a.offs[hb] - a.base, int32_t(a.offs[hb + 1] - a.offs[hb]), xo, yo,
-                               zo, -r0, -r1, -r2, vox, voy, voz, o, f, act, wb, n_upd, n_smp);
-        half_sweep<R, NL, BPL>(m, D, a, L, lane, a.offs[hb + 1] - a.base, int32_t(a.offs[hb + 2] - a.offs[hb + 1]),
-                               xo, yo, zo, r0, r1, r2, vox, voy, voz, o, f, act, wf, n_upd, n_smp);
+        half_sweep<R, NL, BPL>(m, D, a, L, lane, sg, a.offs[hb] - a.base, int32_t(a.offs[hb + 1] - a.offs[hb]),
+                               xo, yo, zo, -r0, -r1, -r2, vox, voy, voz, o, f, act, wb, n_extra, n_smp);
+        half_sweep<R, NL, BPL>(m, D, a, L, lane, sg, a.offs[hb + 1] - a.base,
+                               int32_t(a.offs[hb + 2] - a.offs[hb + 1]), xo, yo, zo, r0, r1, r2, vox, voy, voz, o, f,
+                               act, wf, n_extra, n_smp);
         const double w2 = a.w2[lev];
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
@@ -453,8 +489,8 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
         }
     }
     if (a.counters) {
-        // updates are counted per active bin; samples per lane, times its active bins
-        unsigned long long u = n_upd;
+        // [0]: sub-intervals beyond one per sample (active bins); [1]: samples x active bins
+        unsigned long long u = n_extra;
         unsigned long long s = (unsigned long long)n_smp * n_act;
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) {

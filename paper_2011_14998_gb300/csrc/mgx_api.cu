@@ -819,7 +819,7 @@ mgx_status mgx_profile_read(mgx_ctx *ctx, mgx_profile *out) {
     }
     out->trace_points = ctx->trace_points;
     out->solves = ctx->solves;
-    out->updates = int64_t(cnt[0]);
+    out->updates = int64_t(cnt[1] + cnt[0]);  // one row per sample and bin, plus the extra sub-intervals
     out->samples = int64_t(cnt[1]);
     out->trace_steps = int64_t(cnt[2]);
     out->trace_exact_steps = int64_t(cnt[3]);
