@@ -177,6 +177,32 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
                            double f_large, double G_thres, uint64_t seed, double *Gf, double *L,
                            double *ell, uint8_t *keep, int64_t *n_kept);
 
+/* Flags of mgx_solve_J_batch. */
+enum {
+    MGX_BATCH_GRAPH = 1, /* capture the step in a CUDA graph and replay it on later calls */
+    MGX_BATCH_RAYS = 2   /* rebuild every model's ray set first (its last levels and sample) */
+};
+
+/* Mean intensity of several models in one launch (the batched form of
+ * mgx_solve_J, same results).  All models' half-rays are traced and prefix-
+ * summed together; each (model, origin, frequency tile) item's cost is the
+ * number of points on its traced lines, items are binned by log2 of that cost
+ * and laid out longest bin first, and one persistent kernel (one warp per item,
+ * items taken from a global counter) solves them all, so very uneven ray
+ * lengths and model sizes share the GPU without a long tail.
+ *   models  [n_models] distinct model handles (1..65535), lines and rays set
+ *   J_out   [n_models] device pointers, J_out[k] of size [n_k][n_lines_k*n_freq_k]
+ *   flags   MGX_BATCH_RAYS: the step starts by rebuilding the ray sets;
+ *           MGX_BATCH_GRAPH: the first call plans the arena (one host
+ *           synchronisation), runs the step and captures it as a CUDA graph;
+ *           later calls with the same models, parameters, outputs and flags
+ *           replay the graph without host work.  A replay whose traced lists
+ *           no longer fit the planned arena fails with MGX_ERANGE and drops the
+ *           plan.  Freeing a model drops the plan.
+ * The call synchronises the stream before returning. */
+mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_models, const mgx_solve_params *params,
+                             double *const *J_out, int32_t flags);
+
 /* Allocation-free variant of mgx_solve_J, for callers that must not allocate
  * device memory during their step: code running while a framework owns every
  * device byte and forbids third-party allocations, or code that may not enqueue

@@ -26,7 +26,8 @@ MGX_MAX_LINES = 8
 ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs", "mgx_load_mesh",
                "mgx_free_model", "mgx_set_lines", "mgx_set_rays", "mgx_get_rays", "mgx_trace",
                "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read",
-               "mgx_solve_J_noalloc")
+               "mgx_solve_J_noalloc", "mgx_solve_J_batch")
+MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
 
 
@@ -79,6 +80,7 @@ def load_library(path: str = LIB_PATH):
         "mgx_solve_J": (i32, [vp, i32, C.POINTER(SolveParams), vp]),
         "mgx_reduce_mesh": (i32, [vp, i32, vp, dbl, dbl, dbl, u64, vp, vp, vp, vp, C.POINTER(i64)]),
         "mgx_solve_J_noalloc": (i32, [vp, i32, C.POINTER(SolveParams), vp]),
+        "mgx_solve_J_batch": (i32, [vp, vp, i32, C.POINTER(SolveParams), vp, i32]),
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
     }
@@ -189,6 +191,13 @@ def mgx_solve_J_noalloc(ctx, model, params: SolveParams, J_out) -> None:
     _check(ctx, load_library().mgx_solve_J_noalloc(ctx, int(model), C.byref(params), _ptr(J_out)))
 
 
+def mgx_solve_J_batch(ctx, models, params: SolveParams, J_outs, flags: int = 0) -> None:
+    """Batched solve of several models into CUDA float64 tensors J_outs[k] (see include/mgx.h)."""
+    ids = np.ascontiguousarray(models, np.int32)
+    ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
+    _check(ctx, load_library().mgx_solve_J_batch(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags)))
+
+
 def mgx_reduce_mesh(ctx, model, f, f_small, f_large, G_thres, seed):
     f = _arr(f, np.float64)
     n = len(f)
@@ -278,6 +287,17 @@ class Context:
         J = np.empty((i["n"], i["L"] * i["F"]), np.float64)
         mgx_solve_J(self.ptr, mid, solve_params(dtau_max, dv_max, I_bdy, precision, False), J)
         return J
+
+    def solve_J_batch(self, mids, precision=MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, outs=None,
+                      flags=0):
+        """J of several models in one persistent launch; returns CUDA float64 tensors."""
+        import torch
+
+        if outs is None:
+            outs = [torch.empty((self.models[m]["n"], self.models[m]["L"] * self.models[m]["F"]),
+                                dtype=torch.float64, device=f"cuda:{self.device}") for m in mids]
+        mgx_solve_J_batch(self.ptr, list(mids), solve_params(dtau_max, dv_max, I_bdy, precision, True), outs, flags)
+        return outs
 
     def reduce_mesh(self, mid, f, f_small, f_large, G_thres, seed):
         return mgx_reduce_mesh(self.ptr, mid, f, f_small, f_large, G_thres, seed)

@@ -403,16 +403,12 @@ struct Occ {
     static constexpr int kMinBlocks = (sizeof(R) == 4 && (NL == 1 || BPL == 1)) ? 4 : (sizeof(R) == 4 ? 3 : 1);
 };
 
+// J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
 template <typename R, int NL, int BPL>
-__global__ void __launch_bounds__(128, (Occ<R, NL, BPL>::kMinBlocks))
-k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t item = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
-    const int64_t n_items = int64_t(a.o_end - a.o_begin) * a.n_tiles;
-    if (item >= n_items) return;
-    const int32_t oc = int32_t(item / a.n_tiles);
+__device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln, const DevRays &Rs,
+                                           const SolveArgs &a, int32_t oc, int32_t tile, Stage<R, NL> &sg,
+                                           int lane) {
     const int32_t o = a.o_begin + oc;
-    const int32_t tile = int32_t(item % a.n_tiles);
     const int32_t L = Ln.L, F = Ln.F, NB = L * F;
     const Data<R> D(m, Ln);
     const double dvo = Ln.dvw[o];
@@ -449,8 +445,6 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
         S_o[i] = eta_o / chi_o;
     }
 
-    __shared__ Stage<R, NL> stage[4];  // one per warp of the 128-thread CTA
-    Stage<R, NL> &sg = stage[threadIdx.x >> 5];
     double sum[BPL], comp[BPL];
 #pragma unroll
     for (int i = 0; i < BPL; ++i) sum[i] = comp[i] = 0.0;
@@ -504,6 +498,41 @@ k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
     }
 }
 
+// Grid-mapped launch: warp w of the grid solves item w = oc * n_tiles + tile.
+template <typename R, int NL, int BPL>
+__global__ void __launch_bounds__(128, (Occ<R, NL, BPL>::kMinBlocks))
+k_solve(DevMesh m, DevLines Ln, DevRays Rs, SolveArgs a) {
+    __shared__ Stage<R, NL> stage[4];  // one per warp of the 128-thread CTA
+    const int lane = threadIdx.x & 31;
+    const int64_t item = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+    const int64_t n_items = int64_t(a.o_end - a.o_begin) * a.n_tiles;
+    if (item >= n_items) return;
+    solve_item<R, NL, BPL>(m, Ln, Rs, a, int32_t(item / a.n_tiles), int32_t(item % a.n_tiles),
+                           stage[threadIdx.x >> 5], lane);
+}
+
+// Persistent launch over a work list of (model, origin, tile) items of many
+// models, sorted by decreasing traced length: each warp takes the next item
+// from a global counter until the list is exhausted, so the longest lines
+// start first and the tail is short.
+template <typename R, int NL, int BPL>
+__global__ void __launch_bounds__(128, (Occ<R, NL, BPL>::kMinBlocks))
+k_solve_queue(const BatchSlot *__restrict__ slots, const uint2 *__restrict__ work, int64_t n_work,
+              unsigned long long *__restrict__ next) {
+    __shared__ Stage<R, NL> stage[4];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        unsigned long long it = 0;
+        if (lane == 0) it = atomicAdd(next, 1ull);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= (unsigned long long)n_work) return;
+        const uint2 w = work[it];  // x = model << 16 | tile, y = origin
+        const BatchSlot &s = slots[w.x >> 16];
+        solve_item<R, NL, BPL>(s.m, s.Ln, s.R, s.a, int32_t(w.y), int32_t(w.x & 0xffffu), stage[threadIdx.x >> 5],
+                               lane);
+    }
+}
+
 template <typename R, int BPL>
 void launch_RB(const DevMesh &m, const DevLines &Ln, const DevRays &R_, const SolveArgs &a, cudaStream_t st) {
     const int64_t n_items = int64_t(a.o_end - a.o_begin) * a.n_tiles;
@@ -528,12 +557,44 @@ int solve_bins_per_lane(int precision, int32_t n_bins) {
     return n_bins > 32 ? 2 : 1;
 }
 
+template <typename R, int BPL, int NL>
+void launch_queue_NL(const BatchSlot *slots, const uint2 *work, int64_t n_work, unsigned long long *next,
+                     cudaStream_t st) {
+    int dev = 0, sms = 152, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_queue<R, NL, BPL>, 128, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = int64_t(sms) * per_sm;
+    const int64_t need = (n_work + 3) / 4;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    k_solve_queue<R, NL, BPL><<<unsigned(grid), 128, 0, st>>>(slots, work, n_work, next);
+}
+
+template <typename R, int BPL>
+void launch_queue_RB(int max_lines, const BatchSlot *slots, const uint2 *work, int64_t n_work,
+                     unsigned long long *next, cudaStream_t st) {
+    if (max_lines <= 1) launch_queue_NL<R, BPL, 1>(slots, work, n_work, next, st);
+    else if (max_lines <= 2) launch_queue_NL<R, BPL, 2>(slots, work, n_work, next, st);
+    else if (max_lines <= 4) launch_queue_NL<R, BPL, 4>(slots, work, n_work, next, st);
+    else launch_queue_NL<R, BPL, 8>(slots, work, n_work, next, st);
+}
+
 void launch_solve(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a,
                   int precision, cudaStream_t st) {
     const int bpl = solve_bins_per_lane(precision, Ln.L * Ln.F);
     if (precision == MGX_FP64) launch_RB<double, 1>(m, Ln, R, a, st);
     else if (bpl == 2) launch_RB<float, 2>(m, Ln, R, a, st);
     else launch_RB<float, 1>(m, Ln, R, a, st);
+}
+
+void launch_solve_queue(int precision, int bins_per_lane, int max_lines, const BatchSlot *slots, const uint2 *work,
+                        int64_t n_work, unsigned long long *next, cudaStream_t st) {
+    if (n_work == 0) return;
+    if (precision == MGX_FP64) launch_queue_RB<double, 1>(max_lines, slots, work, n_work, next, st);
+    else if (bins_per_lane == 2) launch_queue_RB<float, 2>(max_lines, slots, work, n_work, next, st);
+    else launch_queue_RB<float, 1>(max_lines, slots, work, n_work, next, st);
 }
 
 }  // namespace mgx

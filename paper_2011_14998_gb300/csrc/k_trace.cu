@@ -156,7 +156,7 @@ __device__ Step step_contenders(const DevMesh &m, int32_t c, float4 oh, float Xo
 template <int MODE>
 __global__ void __launch_bounds__(128)
 k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restrict__ lens,
-        const int64_t *__restrict__ offs, int64_t base, int32_t *__restrict__ idx_out,
+        const int64_t *__restrict__ offs, int64_t base, int64_t cap, int32_t *__restrict__ idx_out,
         double *__restrict__ Z_out, double *__restrict__ delta_out, int *status,
         unsigned long long *__restrict__ counters) {
     const int64_t T = int64_t(gridDim.x) * blockDim.x;
@@ -180,6 +180,10 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         if (MODE > 0) {
             w = offs[h] - base;
             expect = int32_t(offs[h + 1] - offs[h]);
+            if (w < 0 || offs[h + 1] - base > cap) {
+                dev_fail(status, kDevArenaOverflow);
+                continue;
+            }
         }
         int32_t c = o, k = 0;
         float zc32 = 0.0f, ezc = 0.0f;  // Z of the origin is exactly 0
@@ -254,21 +258,21 @@ void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int
                         int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st) {
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
-    k_trace<0><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, nullptr, nullptr,
+    k_trace<0><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, nullptr, nullptr,
                                                   nullptr, status, counters);
 }
 
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
-                       const int64_t *offs, int64_t base, int32_t *idx, double *Z, double *delta,
+                       const int64_t *offs, int64_t base, int64_t cap, int32_t *idx, double *Z, double *delta,
                        int *status, cudaStream_t st) {
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
     if (Z) {
-        k_trace<2><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, idx, Z, delta,
-                                                      status, nullptr);
+        k_trace<2><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx, Z,
+                                                      delta, status, nullptr);
     } else {
-        k_trace<1><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, idx, nullptr,
-                                                      nullptr, status, nullptr);
+        k_trace<1><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx,
+                                                      nullptr, nullptr, status, nullptr);
     }
 }
 

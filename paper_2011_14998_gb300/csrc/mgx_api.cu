@@ -42,6 +42,30 @@ struct Model {
     bool has_rays = false;
     int32_t lmin = 0, lmax = 0, npairs = 0;
     uint32_t *rays = nullptr;
+    int32_t *sample = nullptr;  // device copy of the ray-set sample (adaptive sets)
+    int64_t n_sample = 0;
+};
+
+// A batched solve kept for replay: its buffers and, in graph mode, the
+// instantiated CUDA graph of the whole step.
+struct BatchPlan {
+    bool valid = false;
+    std::vector<int32_t> models;
+    std::vector<double *> J;
+    mgx_solve_params p{};
+    int32_t flags = 0;
+    int64_t total_half = 0, n_origins = 0, n_work = 0, arena_cap = 0;
+    int bpl = 1, max_lines = 1;
+    int64_t *lens = nullptr, *offs = nullptr, *obase = nullptr;
+    int32_t *arena = nullptr;
+    BatchGeom *geo = nullptr;
+    BatchSlot *slots = nullptr;
+    uint2 *work = nullptr;
+    unsigned long long *scratch = nullptr;  // 64 work-list counters + the queue counter
+    void *cub_tmp = nullptr;
+    size_t cub_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
 
 }  // namespace
@@ -67,6 +91,8 @@ struct mgx_ctx {
     std::vector<cudaEvent_t> event_pool;
     unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples, [2] trace steps, [3] redone
     int64_t trace_points = 0, solves = 0;
+    BatchPlan plan;
+    cudaStream_t capture_stream = nullptr;  // graphs are captured here (the caller's may be the legacy stream)
 };
 
 namespace {
@@ -123,6 +149,7 @@ const char *dev_err_text(int code) {
         case kDevTraceMismatch: return "trace emit pass disagrees with count pass";
         case kDevSubdivLimit: return "more than 2^20 optical-depth sub-intervals in one step (dtau_max too small?)";
         case kDevBadInput: return "line data out of range (chi0, eta0 >= 0; dvw, chi_c > 0; eta_c >= 0; finite)";
+        case kDevArenaOverflow: return "traced point lists longer than planned (mesh or rays changed since the plan?)";
         default: return "unknown device error";
     }
 }
@@ -133,7 +160,7 @@ mgx_status sync_status(mgx_ctx *ctx) {
     CK(cudaStreamSynchronize(ctx->stream));
     const int code = *ctx->h_status;
     if (code != 0) {
-        const mgx_status s = (code == kDevSubdivLimit || code == kDevTraceGuard) ? MGX_ERANGE : MGX_EINVAL;
+        const mgx_status s = (code == kDevSubdivLimit || code == kDevTraceGuard || code == kDevArenaOverflow) ? MGX_ERANGE : MGX_EINVAL;
         cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->stream);
         cudaStreamSynchronize(ctx->stream);
         return fail(ctx, s, "device check failed: %s", dev_err_text(code));
@@ -297,6 +324,7 @@ void free_model(mgx_ctx *ctx, Model &m) {
     dfree(ctx, m.phi); dfree(ctx, m.nrec);
     free_lines(ctx, m);
     dfree(ctx, m.rays);
+    dfree(ctx, m.sample);
     m.has_rays = false;
     m.live = false;
 }
@@ -336,6 +364,89 @@ mgx_status trace_offsets(mgx_ctx *ctx, Model &m, int32_t o0, int32_t o1, int64_t
     return MGX_OK;
 }
 
+
+void free_plan(mgx_ctx *ctx, BatchPlan &pl) {
+    if (pl.exec) cudaGraphExecDestroy(pl.exec);
+    if (pl.graph) cudaGraphDestroy(pl.graph);
+    pl.exec = nullptr;
+    pl.graph = nullptr;
+    dfree(ctx, pl.lens);
+    dfree(ctx, pl.offs);
+    dfree(ctx, pl.obase);
+    dfree(ctx, pl.arena);
+    dfree(ctx, pl.geo);
+    dfree(ctx, pl.slots);
+    dfree(ctx, pl.work);
+    dfree(ctx, pl.scratch);
+    if (pl.cub_tmp) cudaFreeAsync(pl.cub_tmp, ctx->stream);
+    pl.cub_tmp = nullptr;
+    pl.valid = false;
+}
+
+// Rebuild the ray set of a model with its current levels and sample (enqueue only).
+void enqueue_rays(mgx_ctx *ctx, Model &m) {
+    Timed t(ctx, MGX_K_RAYS);
+    if (m.lmin == m.lmax) {
+        launch_rays_fixed(m.n, m.lmin, m.npairs, ctx->pair_lists_dev[size_t(m.lmin)], m.rays, ctx->stream);
+    } else {
+        launch_rays_adaptive(mesh_view(m), m.lmin, m.lmax, m.npairs, m.n_sample, m.sample, ctx->anti,
+                             ctx->pair_lists_dev[size_t(m.lmin)], int32_t(ctx->pair_lists[size_t(m.lmin)].size()),
+                             m.rays, ctx->d_status, ctx->stream);
+    }
+}
+
+// Enqueue the tracing passes' first half: (ray sets,) counts and offsets.
+mgx_status enqueue_batch_count(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
+    if (pl.flags & MGX_BATCH_RAYS)
+        for (Model *m : ms) enqueue_rays(ctx, *m);
+    int64_t hb = 0;
+    for (Model *m : ms) {
+        Timed t(ctx, MGX_K_TRACE_COUNT);
+        launch_trace_count(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.lens + hb, ctx->d_status,
+                           ctx->prof ? ctx->d_counters : nullptr, ctx->stream);
+        hb += int64_t(m->n) * m->npairs * 2;
+    }
+    CK(cudaMemsetAsync(pl.offs, 0, sizeof(int64_t), ctx->stream));
+    {
+        Timed t(ctx, MGX_K_SCAN);
+        CK(cub::DeviceScan::InclusiveSum(pl.cub_tmp, pl.cub_bytes, pl.lens, pl.offs + 1, pl.total_half, ctx->stream));
+    }
+    return MGX_OK;
+}
+
+// Enqueue the second half: point lists, work list, persistent solve.
+mgx_status enqueue_batch_solve(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
+    int64_t hb = 0;
+    for (Model *m : ms) {
+        Timed t(ctx, MGX_K_TRACE_EMIT);
+        launch_trace_emit(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.offs + hb, 0, pl.arena_cap, pl.arena,
+                          nullptr, nullptr, ctx->d_status, ctx->stream);
+        hb += int64_t(m->n) * m->npairs * 2;
+    }
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_batch_worklist(pl.geo, pl.obase, int32_t(ms.size()), pl.n_origins, pl.offs, pl.scratch, pl.work,
+                              ctx->stream);
+    }
+    CK(cudaMemsetAsync(pl.scratch + 64, 0, sizeof(unsigned long long), ctx->stream));
+    {
+        Timed t(ctx, MGX_K_SOLVE);
+        launch_solve_queue(pl.p.precision, pl.bpl, pl.max_lines, pl.slots, pl.work, pl.n_work, pl.scratch + 64,
+                           ctx->stream);
+    }
+    CK(cudaGetLastError());
+    return MGX_OK;
+}
+
+bool plan_matches(const BatchPlan &pl, const int32_t *models, int32_t n, const mgx_solve_params *p,
+                  double *const *J, int32_t flags) {
+    if (!pl.valid || int32_t(pl.models.size()) != n || pl.flags != flags) return false;
+    for (int32_t k = 0; k < n; ++k)
+        if (pl.models[size_t(k)] != models[k] || pl.J[size_t(k)] != J[k]) return false;
+    return pl.p.dtau_max == p->dtau_max && pl.p.dv_max == p->dv_max && pl.p.I_bdy == p->I_bdy &&
+           pl.p.precision == p->precision;
+}
+
 }  // namespace
 
 extern "C" {
@@ -372,6 +483,7 @@ void mgx_destroy(mgx_ctx *ctx) {
     if (!ctx) return;
     {
         DeviceGuard g(ctx->device);
+        free_plan(ctx, ctx->plan);
         for (auto &m : ctx->models)
             if (m.live) free_model(ctx, m);
         dfree(ctx, ctx->dir);
@@ -379,6 +491,8 @@ void mgx_destroy(mgx_ctx *ctx) {
         for (auto *p : ctx->pair_lists_dev) dfree(ctx, p);
         reset_profile(ctx);  // before the counters are freed: it clears them on the stream
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+        ctx->capture_stream = nullptr;
         for (auto e : ctx->event_pool) cudaEventDestroy(e);
         ctx->event_pool.clear();
         cudaFree(ctx->d_status);
@@ -469,6 +583,7 @@ mgx_status mgx_free_model(mgx_ctx *ctx, int32_t model) {
     Model *m = get_model(ctx, model);
     if (!m) return fail(ctx, MGX_EINVAL, "free_model: no model %d", model);
     DeviceGuard g(ctx->device);
+    free_plan(ctx, ctx->plan);
     free_model(ctx, *m);
     return MGX_OK;
 }
@@ -547,16 +662,17 @@ mgx_status mgx_set_rays(mgx_ctx *ctx, int32_t model, int32_t l_min, int32_t l_ma
         launch_rays_fixed(m->n, l_min, m->npairs, ctx->pair_lists_dev[size_t(l_min)], m->rays, ctx->stream);
         CK(cudaGetLastError());
     } else {
-        int32_t *smp = nullptr;
-        CK(dalloc(ctx, &smp, size_t(n_sample)));
+        dfree(ctx, m->sample);
+        CK(dalloc(ctx, &m->sample, size_t(n_sample)));
+        m->n_sample = n_sample;
         if (n_sample > 0)
-            CK(cudaMemcpyAsync(smp, sample, size_t(n_sample) * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(m->sample, sample, size_t(n_sample) * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               ctx->stream));
         Timed t(ctx, MGX_K_RAYS);
-        launch_rays_adaptive(mesh_view(*m), l_min, l_max, m->npairs, n_sample, smp, ctx->anti,
+        launch_rays_adaptive(mesh_view(*m), l_min, l_max, m->npairs, n_sample, m->sample, ctx->anti,
                              ctx->pair_lists_dev[size_t(l_min)], int32_t(ctx->pair_lists[size_t(l_min)].size()),
                              m->rays, ctx->d_status, ctx->stream);
         CK(cudaGetLastError());
-        dfree(ctx, smp);
     }
     s = sync_status(ctx);
     m->has_rays = (s == MGX_OK);
@@ -608,8 +724,8 @@ mgx_status mgx_trace(mgx_ctx *ctx, int32_t model, int64_t o_begin, int64_t o_end
     if (delta_out) CK(dalloc(ctx, &de, size_t(total)));
     {
         Timed t(ctx, MGX_K_TRACE_EMIT);
-        launch_trace_emit(mesh_view(*m), rays_view(ctx, *m), int32_t(o_begin), int32_t(o_end), offs, 0, idx, Z,
-                          de, ctx->d_status, ctx->stream);
+        launch_trace_emit(mesh_view(*m), rays_view(ctx, *m), int32_t(o_begin), int32_t(o_end), offs, 0, total, idx,
+                          Z, de, ctx->d_status, ctx->stream);
     }
     CK(cudaGetLastError());
     if (total > 0) {
@@ -683,7 +799,8 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         const int64_t base = obound[size_t(o0)];
         {
             Timed t(ctx, MGX_K_TRACE_EMIT);
-            launch_trace_emit(dm, dr, o0, o1, offs + h0, base, aidx, nullptr, nullptr, ctx->d_status, ctx->stream);
+            launch_trace_emit(dm, dr, o0, o1, offs + h0, base, chunk_max, aidx, nullptr, nullptr, ctx->d_status,
+                              ctx->stream);
         }
         CK(cudaGetLastError());
         SolveArgs a;
@@ -787,6 +904,160 @@ mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_para
         return fail(ctx, rc, "solve_J_noalloc: %s", msg);
     }
     return sync_status(ctx);
+}
+
+
+mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_models, const mgx_solve_params *p,
+                             double *const *J_out, int32_t flags) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!models || !p || !J_out || n_models < 1 || n_models > 65535)
+        return fail(ctx, MGX_EINVAL, "solve_J_batch: bad model list, params or outputs");
+    if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0)) return fail(ctx, MGX_EINVAL, "solve_J_batch: dtau_max must be > 0");
+    if (!std::isfinite(p->dv_max) || !std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J_batch: dv_max, I_bdy must be finite");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J_batch: unknown precision");
+    if (flags & ~(MGX_BATCH_GRAPH | MGX_BATCH_RAYS)) return fail(ctx, MGX_EINVAL, "solve_J_batch: unknown flags");
+    std::vector<Model *> ms;
+    for (int32_t k = 0; k < n_models; ++k) {
+        Model *m = get_model(ctx, models[k]);
+        if (!m) return fail(ctx, MGX_EINVAL, "solve_J_batch: no model %d", models[k]);
+        if (!m->has_lines || !m->has_rays) return fail(ctx, MGX_ESTATE, "solve_J_batch: model %d lacks lines or rays", models[k]);
+        for (int32_t j = 0; j < k; ++j)
+            if (models[j] == models[k]) return fail(ctx, MGX_EINVAL, "solve_J_batch: model %d listed twice", models[k]);
+        cudaPointerAttributes attr;
+        if (!J_out[k] || cudaPointerGetAttributes(&attr, J_out[k]) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+            cudaGetLastError();
+            return fail(ctx, MGX_EINVAL, "solve_J_batch: J_out[%d] must be device memory", k);
+        }
+        ms.push_back(m);
+    }
+    DeviceGuard g(ctx->device);
+    BatchPlan &pl = ctx->plan;
+    const bool graph = (flags & MGX_BATCH_GRAPH) != 0;
+    if (graph && plan_matches(pl, models, n_models, p, J_out, flags) && pl.exec) {
+        CK(cudaGraphLaunch(pl.exec, ctx->stream));
+        ctx->launches[MGX_K_SOLVE] += 1;
+        const mgx_status s = sync_status(ctx);
+        if (s != MGX_OK) free_plan(ctx, pl);
+        return s;
+    }
+    free_plan(ctx, pl);
+    pl.models.assign(models, models + n_models);
+    pl.J.assign(J_out, J_out + n_models);
+    pl.p = *p;
+    pl.flags = flags;
+    int64_t max_nb = 1;
+    pl.max_lines = 1;
+    for (Model *m : ms) {
+        max_nb = std::max<int64_t>(max_nb, int64_t(m->L) * m->F);
+        pl.max_lines = std::max(pl.max_lines, int(m->L));
+    }
+    pl.bpl = solve_bins_per_lane(p->precision, int32_t(max_nb));
+    std::vector<BatchGeom> geo(static_cast<size_t>(n_models));
+    std::vector<int64_t> obase(static_cast<size_t>(n_models));
+    pl.total_half = pl.n_origins = pl.n_work = 0;
+    for (int32_t k = 0; k < n_models; ++k) {
+        const Model &m = *ms[size_t(k)];
+        const int64_t nb = int64_t(m.L) * m.F;
+        geo[size_t(k)].half_base = pl.total_half;
+        geo[size_t(k)].npairs2 = 2 * m.npairs;
+        geo[size_t(k)].n_tiles = int32_t((nb + 32 * pl.bpl - 1) / (32 * pl.bpl));
+        obase[size_t(k)] = pl.n_origins;
+        pl.total_half += int64_t(m.n) * m.npairs * 2;
+        pl.n_origins += m.n;
+        pl.n_work += int64_t(m.n) * geo[size_t(k)].n_tiles;
+        if (geo[size_t(k)].n_tiles > 65535) return fail(ctx, MGX_ERANGE, "solve_J_batch: too many frequency tiles");
+    }
+    CK(dalloc(ctx, &pl.lens, size_t(pl.total_half)));
+    CK(dalloc(ctx, &pl.offs, size_t(pl.total_half + 1)));
+    CK(dalloc(ctx, &pl.obase, size_t(n_models)));
+    CK(dalloc(ctx, &pl.geo, size_t(n_models)));
+    CK(dalloc(ctx, &pl.slots, size_t(n_models)));
+    CK(dalloc(ctx, &pl.work, size_t(pl.n_work)));
+    CK(dalloc(ctx, &pl.scratch, 65));
+    CK(cub::DeviceScan::InclusiveSum(nullptr, pl.cub_bytes, pl.lens, pl.offs + 1, pl.total_half, ctx->stream));
+    CK(cudaMallocAsync(&pl.cub_tmp, pl.cub_bytes ? pl.cub_bytes : 1, ctx->stream));
+    CK(cudaMemcpyAsync(pl.geo, geo.data(), geo.size() * sizeof(BatchGeom), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(pl.obase, obase.data(), obase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    // plan the arena: counts, offsets, total (the only host synchronisation)
+    mgx_status s = enqueue_batch_count(ctx, pl, ms);
+    if (s != MGX_OK) return s;
+    int64_t total = 0;
+    CK(cudaMemcpyAsync(&total, pl.offs + pl.total_half, sizeof total, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_status(ctx);
+    if (s != MGX_OK) {
+        free_plan(ctx, pl);
+        return s;
+    }
+    pl.arena_cap = total;
+    CK(dalloc(ctx, &pl.arena, size_t(total)));
+    std::vector<BatchSlot> slots(static_cast<size_t>(n_models));
+    for (int32_t k = 0; k < n_models; ++k) {
+        Model &m = *ms[size_t(k)];
+        BatchSlot &b = slots[size_t(k)];
+        b.m = mesh_view(m);
+        b.Ln = lines_view(m);
+        b.R = rays_view(ctx, m);
+        SolveArgs &a = b.a;
+        a.dtau_max = p->dtau_max;
+        a.dv_max = p->dv_max;
+        a.I_bdy = p->I_bdy;
+        a.o_begin = 0;
+        a.o_end = m.n;
+        a.n_tiles = geo[size_t(k)].n_tiles;
+        a.offs = pl.offs + geo[size_t(k)].half_base;
+        a.base = 0;
+        a.idx = pl.arena;
+        a.J = J_out[k];
+        a.status = ctx->d_status;
+        a.counters = ctx->prof ? ctx->d_counters : nullptr;
+        fill_pair_weights(a);
+        ctx->solves += int64_t(m.n) * m.npairs * int64_t(m.L) * m.F;
+    }
+    ctx->trace_points += total;
+    CK(cudaMemcpyAsync(pl.slots, slots.data(), slots.size() * sizeof(BatchSlot), cudaMemcpyHostToDevice, ctx->stream));
+    s = enqueue_batch_solve(ctx, pl, ms);
+    if (s != MGX_OK) {
+        free_plan(ctx, pl);
+        return s;
+    }
+    s = sync_status(ctx);
+    if (s != MGX_OK) {
+        free_plan(ctx, pl);
+        return s;
+    }
+    pl.valid = true;
+    if (graph) {
+        // capture the whole step for replay; kernels only, no profiling events
+        const bool prof = ctx->prof;
+        ctx->prof = false;
+        for (auto &sl : slots) sl.a.counters = nullptr;
+        CK(cudaMemcpyAsync(pl.slots, slots.data(), slots.size() * sizeof(BatchSlot), cudaMemcpyHostToDevice,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        if (!ctx->capture_stream) CK(cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+        cudaStream_t user = ctx->stream;
+        ctx->stream = ctx->capture_stream;
+        cudaError_t ce = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+        mgx_status s2 = MGX_ECUDA;
+        cudaGraph_t gr = nullptr;
+        if (ce == cudaSuccess) {
+            const mgx_status s1 = enqueue_batch_count(ctx, pl, ms);
+            s2 = s1 == MGX_OK ? enqueue_batch_solve(ctx, pl, ms) : s1;
+            ce = cudaStreamEndCapture(ctx->stream, &gr);
+        }
+        ctx->stream = user;
+        ctx->prof = prof;
+        if (s2 != MGX_OK || ce != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            free_plan(ctx, pl);
+            return s2 != MGX_OK ? s2 : fail(ctx, MGX_ECUDA, "solve_J_batch: graph capture failed: %s", cudaGetErrorString(ce));
+        }
+        pl.graph = gr;
+        CK(cudaGraphInstantiate(&pl.exec, gr, 0));
+    }
+    return MGX_OK;
 }
 
 mgx_status mgx_profile_enable(mgx_ctx *ctx, int32_t enable) {

@@ -20,6 +20,7 @@ enum DevErr : int {
     kDevTraceMismatch = 4, // emit pass disagrees with the count pass
     kDevSubdivLimit = 5,   // more than kMaxSubdiv optical-depth sub-intervals in one step
     kDevBadInput = 6,      // value outside its documented range
+    kDevArenaOverflow = 7, // traced lists longer than the arena planned for them
 };
 
 constexpr int kMaxSubdiv = 1 << 20;
@@ -105,10 +106,31 @@ void launch_rays_adaptive(const DevMesh &m, int32_t lmin, int32_t lmax, int32_t 
 // ---- tracing (k_trace.cu)
 void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
                         int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st);
-// Z == nullptr: ids only (the solver's arena); otherwise also exact Z (and delta if given)
+// Z == nullptr: ids only (the solver's arena); otherwise also exact Z (and delta if given).
+// Entries beyond cap (relative to base) are refused with kDevArenaOverflow.
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
-                       const int64_t *offs, int64_t base, int32_t *idx, double *Z, double *delta,
+                       const int64_t *offs, int64_t base, int64_t cap, int32_t *idx, double *Z, double *delta,
                        int *status, cudaStream_t st);
+
+// One model of a batched solve (device-resident descriptor).
+struct BatchSlot {
+    DevMesh m;
+    DevLines Ln;
+    DevRays R;
+    SolveArgs a;  // o_begin = 0, o_end = n; offsets into the batch's shared arena
+};
+
+// Geometry of one model of a batch: its half-rays start at half_base in the
+// batch's offset array, 2 npairs per origin, n_tiles frequency tiles.
+struct BatchGeom {
+    int64_t half_base;
+    int32_t npairs2;
+    int32_t n_tiles;
+};
+
+// ---- batched work list (k_batch.cu); scratch64 holds 64 counters
+void launch_batch_worklist(const BatchGeom *geo, const int64_t *origin_base, int32_t n_models, int64_t n_origins,
+                           const int64_t *offs, unsigned long long *scratch64, uint2 *work, cudaStream_t st);
 
 // ---- formal solution (k_solve.cu)
 // frequency bins per lane of the solve kernel; a chunk has
@@ -116,6 +138,9 @@ void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int3
 int solve_bins_per_lane(int precision, int32_t n_bins);
 void launch_solve(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a,
                   int precision, cudaStream_t st);
+// persistent launch over a work list (x = model << 16 | tile, y = origin); next: zeroed counter
+void launch_solve_queue(int precision, int bins_per_lane, int max_lines, const BatchSlot *slots, const uint2 *work,
+                        int64_t n_work, unsigned long long *next, cudaStream_t st);
 
 // ---- reduction criterion (k_reduce.cu)
 void launch_reduce(const DevMesh &m, const double *f, double f_small, double f_large,

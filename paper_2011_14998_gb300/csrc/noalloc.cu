@@ -99,6 +99,7 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
         int64_t c = std::min<int64_t>(c_max, m.n - o0);
         int64_t *lens = nullptr, *offs = nullptr;
         int32_t *idx = nullptr;
+        int64_t cap_used = 0;
         for (;;) {
             const int64_t nh = c * np2;
             lens = reinterpret_cast<int64_t *>(base);
@@ -106,6 +107,7 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
             const size_t arena0 = align256(size_t(2 * nh + 1) * sizeof(int64_t));
             const int64_t cap = int64_t((kNoAllocScratchBytes - arena0) / sizeof(int32_t));
             idx = reinterpret_cast<int32_t *>(base + arena0);
+            cap_used = cap;
             launch_trace_count(m, R, int32_t(o0), int32_t(o0 + c), lens, status, nullptr, st);
             k_scan_lengths<<<1, 1024, 0, st>>>(lens, nh, offs);
             int64_t total = 0;
@@ -124,7 +126,7 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
             }
             c = std::max<int64_t>(1, int64_t(double(c) * double(cap) / double(total) * 0.9));
         }
-        launch_trace_emit(m, R, int32_t(o0), int32_t(o0 + c), offs, 0, idx, nullptr, nullptr, status, st);
+        launch_trace_emit(m, R, int32_t(o0), int32_t(o0 + c), offs, 0, cap_used, idx, nullptr, nullptr, status, st);
         SolveArgs a;
         a.dtau_max = dtau_max;
         a.dv_max = dv_max;

@@ -1,0 +1,76 @@
+"""Batched, length-binned persistent solve (mgx_solve_J_batch) and its CUDA-graph
+replay: same J as the per-model solve and as the oracle, for models of different
+sizes, line counts, bin counts and ray sets in one launch."""
+import numpy as np
+import pytest
+
+from helpers import j_rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    import synth
+
+    import paper_2011_14998_gb300 as mgx
+
+    mgx.build()
+    ctx = mgx.Context(0)
+    models = [
+        synth.wind_model(900, seed=31, n_freq=50, level=2),
+        synth.random_cloud(150, seed=5, n_lines=3, n_freq=13, x_span=3.5, l_min=0, l_max=2, v_rms=1.5),
+        synth.grid_model(6, n_freq=9),
+        synth.wind_model(600, seed=32, n_freq=20, level=1, l_min=0),
+    ]
+    mids = [ctx.load(m) for m in models]
+    yield ctx, models, mids
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(1, 1e-5), (0, 1e-13)])
+def test_batch_matches_single_model_solves(setup, prec, tol):
+    ctx, models, mids = setup
+    singles = [ctx.solve_J(m, precision=prec) for m in mids]
+    outs = ctx.solve_J_batch(mids, precision=prec)
+    for J1, Jb in zip(singles, outs):
+        assert Jb.shape == J1.shape
+        assert j_rel_err(Jb.cpu().numpy(), J1)[0] <= tol
+
+
+def test_batch_against_oracle(setup, orc):
+    ctx, models, mids = setup
+    outs = ctx.solve_J_batch(mids, precision=0, dtau_max=0.4, I_bdy=0.05)
+    for m, mid, Jb in zip(models, mids, outs):
+        om = orc.OracleModel(m, rays=ctx.rays(mid))
+        origins = np.arange(0, len(m["pos"]), 7)
+        Jo = om.solve_J(orc.params(dtau_max=0.4, I_bdy=0.05), origins=origins)
+        assert j_rel_err(Jb.cpu().numpy()[origins], Jo)[0] < 1e-10
+
+
+def test_graph_replay_with_ray_rebuild(setup):
+    import paper_2011_14998_gb300 as mgx
+
+    ctx, models, mids = setup
+    ref = ctx.solve_J_batch(mids, precision=1)
+    outs = ctx.solve_J_batch(mids, precision=1, flags=mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS)
+    first = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(float("nan"))
+    ctx.solve_J_batch(mids, precision=1, outs=outs, flags=mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS)  # replay
+    for a, b, r in zip(first, outs, ref):
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+        assert np.array_equal(a.cpu().numpy(), r.cpu().numpy())
+
+
+def test_batch_rejects_bad_arguments(setup):
+    import torch
+
+    import paper_2011_14998_gb300 as mgx
+
+    ctx, models, mids = setup
+    out = torch.empty((900, 50), dtype=torch.float64, device="cuda")
+    with pytest.raises(mgx.MgxError):  # a model twice
+        mgx.mgx_solve_J_batch(ctx.ptr, [mids[0], mids[0]], mgx.solve_params(), [out, out])
+    with pytest.raises(mgx.MgxError):  # host output
+        mgx.mgx_solve_J_batch(ctx.ptr, [mids[0]], mgx.solve_params(), [torch.empty((900, 50), dtype=torch.float64)])
