@@ -201,46 +201,65 @@ def run_mgx(args):
     out64 = torch.empty((n, NB), dtype=torch.float64, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def step(precision, out):
-        ctx.set_rays(mid, 2, 2)
-        ctx.solve_J(mid, precision=precision, dtau_max=0.5, dv_max=1.0 / 3.0, out=out)
+    batched = mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS
 
-    def timed(precision, out, k, warm):
+    def step32():
+        # the FP32 batched form: ray sets, tracing, length-binned work list and the
+        # persistent solve, replayed as one CUDA graph
+        ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32],
+                          flags=batched)
+
+    def step32_profiled():
+        ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32],
+                          flags=mgx.MGX_BATCH_RAYS)
+
+    def step64():
+        # the FP64 plain form: grid-mapped solve, one warp per origin and 32-bin tile
+        ctx.set_rays(mid, 2, 2)
+        ctx.solve_J(mid, precision=mgx.MGX_FP64, dtau_max=0.5, dv_max=1.0 / 3.0, out=out64)
+
+    def timed(stepfn, k, warm, profile):
         for _ in range(warm):
-            step(precision, out)
+            stepfn()
         torch.cuda.synchronize()
         ev = []
-        ctx.profile(True)
+        if profile:
+            ctx.profile(True)
         for _ in range(k):
             with torch.cuda.stream(stream):
                 flush.zero_()  # evict the mesh from L2 between timed steps
                 a = torch.cuda.Event(enable_timing=True)
                 b = torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-            step(precision, out)
+            stepfn()
             with torch.cuda.stream(stream):
                 b.record(stream)
             ev.append((a, b))
         torch.cuda.synchronize()
-        prof = ctx.profile_read()
-        ctx.profile(False)
+        prof = None
+        if profile:
+            prof = ctx.profile_read()
+            ctx.profile(False)
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3, prof
 
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(gpu_physical_index(local)) as clk:
-        t32, prof32 = timed(mgx.MGX_FP32, out32, args.steps, args.warmup)
+        t32, _ = timed(step32, args.steps, args.warmup, False)
     if ws > 1:
         tt = torch.tensor([t32], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t32 = float(tt.item())
         torch.distributed.barrier()
     value = ws * solves_per_step * args.steps / t32
+    # per-kernel CUDA-event breakdown of the same step, launched without the graph
+    kb = max(1, min(args.steps, 3))
+    tb, prof32 = timed(step32_profiled, kb, 1, True)
 
     # FP64 plain form on the same inputs (fewer steps: it is much slower on GB300)
     k64 = max(1, args.fp64_steps)
-    t64, prof64 = timed(mgx.MGX_FP64, out64, k64, 1)
+    t64, prof64 = timed(step64, k64, 1, True)
     value64 = solves_per_step * k64 / t64
     J32 = out32.cpu().numpy()
     J64 = out64.cpu().numpy()
@@ -253,12 +272,17 @@ def run_mgx(args):
     h2d = sum(t.numel() * t.element_size() for t in host.values())
     d2h = Jh.numel() * Jh.element_size()
 
+    Jd = torch.empty((n, NB), dtype=torch.float64, device="cuda")
+
     def e2e_step():
         mm = mgx.mgx_load_mesh(ctx.ptr, host["pos"], host["vel"], host["nbr_off"], host["nbr_idx"])
         mgx.mgx_set_lines(ctx.ptr, mm, host["nu0"], host["chi0"], host["eta0"], host["dvw"], host["chi_c"],
                           host["eta_c"], m["n_freq"], m["x_span"])
         mgx.mgx_set_rays(ctx.ptr, mm, 2, 2, None)
-        mgx.mgx_solve_J(ctx.ptr, mm, mgx.solve_params(0.5, 1.0 / 3.0, 0.0, mgx.MGX_FP32, False), Jh)
+        mgx.mgx_solve_J_batch(ctx.ptr, [mm], mgx.solve_params(0.5, 1.0 / 3.0, 0.0, mgx.MGX_FP32, True), [Jd], 0)
+        with torch.cuda.stream(stream):
+            Jh.copy_(Jd, non_blocking=True)
+        stream.synchronize()
         mgx.mgx_free_model(ctx.ptr, mm)
 
     e2e_step()
@@ -312,24 +336,27 @@ def run_mgx(args):
     achieved = flops_per_launch / (ms_solve * 1e-3) / 1e12
     arena_bytes = prof32["trace_points"] * 12 * ((NB + 31) // 32) + n * NB * 8  # point lists per tile + J
     hbm_gbs = arena_bytes / max(1, prof32["launches"]["solve"]) / (ms_solve * 1e-3) / 1e9
-    step_ms = {k: v / args.steps for k, v in prof32["ms"].items()}
-    launches = sum(v for k, v in prof32["launches"].items() if k != "scan")
+    step_ms = {k: v / kb for k, v in prof32["ms"].items()}
+    launches = args.steps * sum(v for k, v in prof32["launches"].items() if k != "scan") // kb
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t32 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(WORKLOAD, parallelism=f"replicas x{ws}", l2="flushed between timed steps (256 MiB write)"),
+        "config": dict(WORKLOAD, parallelism=f"replicas x{ws}", l2="flushed between timed steps (256 MiB write)",
+                       step="one CUDA-graph replay: ray sets, trace count, scan, work list, trace emit, "
+                            "persistent length-binned solve"),
         "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
                        "speedup_fp32_over_fp64": value / ws / value64},
         "accuracy": {"fp32_vs_fp64_max_rel": float(rel32_64.max()),
                      "fp32_vs_fp64_p99_rel": float(np.quantile(rel32_64, 0.99)),
                      "oracle_sample": acc_oracle},
         "kernel_ms_per_step": step_ms,
-        "work_per_step": {"solves": solves_per_step, "trace_points": prof32["trace_points"] // args.steps,
-                          "updates": prof32["updates"] // args.steps, "samples": prof32["samples"] // args.steps,
-                          "trace_steps": prof32["trace_steps"] // args.steps,
-                          "trace_steps_redone_fp64": prof32["trace_exact_steps"] // args.steps},
-        "roofline": {"kernel": "k_solve<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+        "kernel_breakdown_step_ms": 1e3 * tb / kb,
+        "work_per_step": {"solves": solves_per_step, "trace_points": prof32["trace_points"] // kb,
+                          "updates": prof32["updates"] // kb, "samples": prof32["samples"] // kb,
+                          "trace_steps": prof32["trace_steps"] // kb,
+                          "trace_steps_redone_fp64": prof32["trace_exact_steps"] // kb},
+        "roofline": {"kernel": "k_solve_queue<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
                      "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",
                      "hbm_algorithmic_gbs": hbm_gbs},
