@@ -222,6 +222,47 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
 mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params,
                                double *J_out);
 
+/* Learned mesh reduction (a learned companion to the criterion of Section
+ * 2.2.2; the paper has no network).  A small MLP, 8 -> 64 -> 64 -> 1 with ReLU,
+ * predicts from eight per-point features how much J error dropping a point
+ * causes; mgx_reduce_mesh_learned keeps the points with the largest
+ * prediction.  Parameters are one FP32 vector of MGX_MLP_NPARAM values:
+ * W1 [8][64], b1 [64], W2 [64][64], b2 [64], W3 [64], b3 [1]
+ * (h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), y = h2 . W3 + b3).
+ * The kernels compute the two hidden products on the tensor cores in bfloat16
+ * (inputs, W1, W2, h1 and the back-propagated hidden gradients rounded to
+ * bfloat16) with FP32 accumulation; everything else is FP32.  The loss is the
+ * mean squared error; training uses Adam (beta1 0.9, beta2 0.999, eps 1e-8)
+ * on the FP32 master parameters. */
+#define MGX_MLP_NPARAM 4801
+
+/* Set the parameters (host [MGX_MLP_NPARAM]); resets the optimiser state. */
+mgx_status mgx_mlp_set_params(mgx_ctx *ctx, const float *theta);
+/* Copy the current parameters to the host. */
+mgx_status mgx_mlp_get_params(mgx_ctx *ctx, float *theta);
+/* y [n] = network(X [n][8]) (host arrays). */
+mgx_status mgx_mlp_forward(mgx_ctx *ctx, const float *X, int64_t n, float *y);
+/* Gradient of the mean squared error over all n rows (one batch), host
+ * [MGX_MLP_NPARAM]; *loss (may be NULL) receives the loss.  No update. */
+mgx_status mgx_mlp_grad(mgx_ctx *ctx, const float *X, const float *t, int64_t n, float *grad, float *loss);
+/* Adam training for `epochs` passes in shuffled mini-batches of `batch` rows
+ * (shuffles from SplitMix64 seeded with `seed`); loss_per_epoch [epochs]
+ * (may be NULL) receives each epoch's mean loss. */
+mgx_status mgx_mlp_train(mgx_ctx *ctx, const float *X, const float *t, int64_t n, int32_t epochs, int32_t batch,
+                         float lr, uint64_t seed, float *loss_per_epoch);
+/* Per-point features X [n][8] (host output) of a model with lines set, from
+ * its density rho [n] and temperature T [n] (host, > 0): log rho, the largest
+ * |log rho contrast| to a neighbour, the largest neighbour velocity difference
+ * in local Doppler widths, log T, log of the mean neighbour distance L (Eq. 8),
+ * neighbour count, log distance from the coordinate origin, and log of the
+ * first line's centre opacity times L. */
+mgx_status mgx_mlp_features(mgx_ctx *ctx, int32_t model, const double *rho, const double *T, float *X);
+/* Keep the round(keep_fraction * n) points with the largest network output
+ * for standardised features X [n][8] (host): keep [n] (host) receives 1/0,
+ * *n_kept the count.  Ties go to the smaller index. */
+mgx_status mgx_reduce_mesh_learned(mgx_ctx *ctx, int32_t model, const float *X, double keep_fraction, uint8_t *keep,
+                                   int64_t *n_kept);
+
 /* Kernel-level profiling.  While enabled, every kernel launch of the context is
  * bracketed by CUDA events on the context's stream and the work counters below
  * are accumulated on the device; mgx_profile_read synchronises the stream and

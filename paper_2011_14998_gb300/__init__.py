@@ -26,7 +26,9 @@ MGX_MAX_LINES = 8
 ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs", "mgx_load_mesh",
                "mgx_free_model", "mgx_set_lines", "mgx_set_rays", "mgx_get_rays", "mgx_trace",
                "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read",
-               "mgx_solve_J_noalloc", "mgx_solve_J_batch")
+               "mgx_solve_J_noalloc", "mgx_solve_J_batch", "mgx_mlp_set_params", "mgx_mlp_get_params",
+               "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned")
+MGX_MLP_NPARAM = 4801
 MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
 
@@ -81,6 +83,13 @@ def load_library(path: str = LIB_PATH):
         "mgx_reduce_mesh": (i32, [vp, i32, vp, dbl, dbl, dbl, u64, vp, vp, vp, vp, C.POINTER(i64)]),
         "mgx_solve_J_noalloc": (i32, [vp, i32, C.POINTER(SolveParams), vp]),
         "mgx_solve_J_batch": (i32, [vp, vp, i32, C.POINTER(SolveParams), vp, i32]),
+        "mgx_mlp_set_params": (i32, [vp, vp]),
+        "mgx_mlp_get_params": (i32, [vp, vp]),
+        "mgx_mlp_forward": (i32, [vp, vp, i64, vp]),
+        "mgx_mlp_grad": (i32, [vp, vp, vp, i64, vp, vp]),
+        "mgx_mlp_train": (i32, [vp, vp, vp, i64, i32, i32, C.c_float, u64, vp]),
+        "mgx_mlp_features": (i32, [vp, i32, vp, vp, vp]),
+        "mgx_reduce_mesh_learned": (i32, [vp, i32, vp, dbl, vp, C.POINTER(i64)]),
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
     }
@@ -196,6 +205,60 @@ def mgx_solve_J_batch(ctx, models, params: SolveParams, J_outs, flags: int = 0) 
     ids = np.ascontiguousarray(models, np.int32)
     ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
     _check(ctx, load_library().mgx_solve_J_batch(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags)))
+
+
+def mgx_mlp_set_params(ctx, theta) -> None:
+    theta = np.ascontiguousarray(theta, np.float32)
+    assert theta.size == MGX_MLP_NPARAM
+    _check(ctx, load_library().mgx_mlp_set_params(ctx, _ptr(theta)))
+
+
+def mgx_mlp_get_params(ctx) -> np.ndarray:
+    out = np.empty(MGX_MLP_NPARAM, np.float32)
+    _check(ctx, load_library().mgx_mlp_get_params(ctx, _ptr(out)))
+    return out
+
+
+def mgx_mlp_forward(ctx, X) -> np.ndarray:
+    X = np.ascontiguousarray(X, np.float32)
+    y = np.empty(len(X), np.float32)
+    _check(ctx, load_library().mgx_mlp_forward(ctx, _ptr(X), len(X), _ptr(y)))
+    return y
+
+
+def mgx_mlp_grad(ctx, X, t):
+    X = np.ascontiguousarray(X, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    g = np.empty(MGX_MLP_NPARAM, np.float32)
+    loss = C.c_float(0.0)
+    _check(ctx, load_library().mgx_mlp_grad(ctx, _ptr(X), _ptr(t), len(X), _ptr(g), C.byref(loss)))
+    return g, float(loss.value)
+
+
+def mgx_mlp_train(ctx, X, t, epochs, batch, lr, seed) -> np.ndarray:
+    X = np.ascontiguousarray(X, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    losses = np.empty(epochs, np.float32)
+    _check(ctx, load_library().mgx_mlp_train(ctx, _ptr(X), _ptr(t), len(X), int(epochs), int(batch), float(lr),
+                                             C.c_uint64(int(seed) & (2**64 - 1)), _ptr(losses)))
+    return losses
+
+
+def mgx_mlp_features(ctx, model, rho, T) -> np.ndarray:
+    rho = np.ascontiguousarray(rho, np.float64)
+    T = np.ascontiguousarray(T, np.float64)
+    X = np.empty((len(rho), 8), np.float32)
+    _check(ctx, load_library().mgx_mlp_features(ctx, int(model), _ptr(rho), _ptr(T), _ptr(X)))
+    return X
+
+
+def mgx_reduce_mesh_learned(ctx, model, X, keep_fraction):
+    X = np.ascontiguousarray(X, np.float32)
+    keep = np.empty(len(X), np.uint8)
+    nk = C.c_int64(0)
+    _check(ctx, load_library().mgx_reduce_mesh_learned(ctx, int(model), _ptr(X), float(keep_fraction), _ptr(keep),
+                                                       C.byref(nk)))
+    return keep, int(nk.value)
 
 
 def mgx_reduce_mesh(ctx, model, f, f_small, f_large, G_thres, seed):

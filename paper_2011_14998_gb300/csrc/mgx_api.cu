@@ -92,7 +92,12 @@ struct mgx_ctx {
     unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples, [2] trace steps, [3] redone
     int64_t trace_points = 0, solves = 0;
     BatchPlan plan;
-    cudaStream_t capture_stream = nullptr;  // graphs are captured here (the caller's may be the legacy stream)
+    cudaStream_t capture_stream = nullptr;
+    // learned reduction network: FP32 master parameters, Adam moments, gradient
+    // accumulator, loss accumulator, bf16 copies of W1 (padded) and W2
+    float *mlp_theta = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_grad = nullptr, *mlp_loss = nullptr;
+    void *mlp_W1b = nullptr, *mlp_W2b = nullptr;
+    int64_t mlp_step = 0;  // graphs are captured here (the caller's may be the legacy stream)
 };
 
 namespace {
@@ -484,6 +489,10 @@ void mgx_destroy(mgx_ctx *ctx) {
     {
         DeviceGuard g(ctx->device);
         free_plan(ctx, ctx->plan);
+        dfree(ctx, ctx->mlp_theta); dfree(ctx, ctx->mlp_m); dfree(ctx, ctx->mlp_v);
+        dfree(ctx, ctx->mlp_grad); dfree(ctx, ctx->mlp_loss);
+        if (ctx->mlp_W1b) cudaFreeAsync(ctx->mlp_W1b, ctx->stream);
+        if (ctx->mlp_W2b) cudaFreeAsync(ctx->mlp_W2b, ctx->stream);
         for (auto &m : ctx->models)
             if (m.live) free_model(ctx, m);
         dfree(ctx, ctx->dir);
@@ -1058,6 +1067,224 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         CK(cudaGraphInstantiate(&pl.exec, gr, 0));
     }
     return MGX_OK;
+}
+
+
+mgx_status mgx_mlp_set_params(mgx_ctx *ctx, const float *theta) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!theta) return fail(ctx, MGX_EINVAL, "mlp_set_params: null parameters");
+    for (int i = 0; i < kMlpN; ++i)
+        if (!std::isfinite(theta[i])) return fail(ctx, MGX_EINVAL, "mlp_set_params: non-finite parameter %d", i);
+    DeviceGuard g(ctx->device);
+    if (!ctx->mlp_theta) {
+        CK(dalloc(ctx, &ctx->mlp_theta, kMlpN));
+        CK(dalloc(ctx, &ctx->mlp_m, kMlpN));
+        CK(dalloc(ctx, &ctx->mlp_v, kMlpN));
+        CK(dalloc(ctx, &ctx->mlp_grad, kMlpN));
+        CK(dalloc(ctx, &ctx->mlp_loss, 1));
+        CK(cudaMallocAsync(&ctx->mlp_W1b, 16 * 64 * 2, ctx->stream));
+        CK(cudaMallocAsync(&ctx->mlp_W2b, 64 * 64 * 2, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(ctx->mlp_theta, theta, kMlpN * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlp_m, 0, kMlpN * sizeof(float), ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlp_v, 0, kMlpN * sizeof(float), ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlp_grad, 0, kMlpN * sizeof(float), ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_mlp_convert(ctx->mlp_theta, ctx->mlp_W1b, ctx->mlp_W2b, ctx->stream);
+    }
+    ctx->mlp_step = 0;
+    return sync_status(ctx);
+}
+
+mgx_status mgx_mlp_get_params(mgx_ctx *ctx, float *theta) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!theta) return fail(ctx, MGX_EINVAL, "mlp_get_params: null output");
+    if (!ctx->mlp_theta) return fail(ctx, MGX_ESTATE, "mlp_get_params: mgx_mlp_set_params not called");
+    DeviceGuard g(ctx->device);
+    CK(cudaMemcpyAsync(theta, ctx->mlp_theta, kMlpN * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MGX_OK;
+}
+
+mgx_status mgx_mlp_forward(mgx_ctx *ctx, const float *X, int64_t n, float *y) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!X || !y || n < 1 || n >= (int64_t(1) << 31)) return fail(ctx, MGX_EINVAL, "mlp_forward: bad arguments");
+    if (!ctx->mlp_theta) return fail(ctx, MGX_ESTATE, "mlp_forward: mgx_mlp_set_params not called");
+    DeviceGuard g(ctx->device);
+    float *Xd = nullptr, *yd = nullptr;
+    CK(dalloc(ctx, &Xd, size_t(n) * 8));
+    CK(dalloc(ctx, &yd, size_t(n)));
+    CK(cudaMemcpyAsync(Xd, X, size_t(n) * 8 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_mlp(false, Xd, nullptr, nullptr, n, ctx->mlp_W1b, ctx->mlp_W2b, ctx->mlp_theta, yd, nullptr, nullptr,
+                   0.0f, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(y, yd, size_t(n) * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, Xd);
+    dfree(ctx, yd);
+    return sync_status(ctx);
+}
+
+mgx_status mgx_mlp_grad(mgx_ctx *ctx, const float *X, const float *t, int64_t n, float *grad, float *loss) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!X || !t || !grad || n < 1 || n >= (int64_t(1) << 31)) return fail(ctx, MGX_EINVAL, "mlp_grad: bad arguments");
+    if (!ctx->mlp_theta) return fail(ctx, MGX_ESTATE, "mlp_grad: mgx_mlp_set_params not called");
+    DeviceGuard g(ctx->device);
+    float *Xd = nullptr, *td = nullptr;
+    CK(dalloc(ctx, &Xd, size_t(n) * 8));
+    CK(dalloc(ctx, &td, size_t(n)));
+    CK(cudaMemcpyAsync(Xd, X, size_t(n) * 8 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(td, t, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlp_grad, 0, kMlpN * sizeof(float), ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(float), ctx->stream));
+    {
+        Timed tm(ctx, MGX_K_OTHER);
+        launch_mlp(true, Xd, td, nullptr, n, ctx->mlp_W1b, ctx->mlp_W2b, ctx->mlp_theta, nullptr, ctx->mlp_grad,
+                   ctx->mlp_loss, float(2.0 / double(n)), ctx->stream);
+    }
+    CK(cudaGetLastError());
+    float lsum = 0.0f;
+    CK(cudaMemcpyAsync(grad, ctx->mlp_grad, kMlpN * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&lsum, ctx->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemsetAsync(ctx->mlp_grad, 0, kMlpN * sizeof(float), ctx->stream));
+    dfree(ctx, Xd);
+    dfree(ctx, td);
+    const mgx_status s = sync_status(ctx);
+    if (loss) *loss = lsum / float(n);
+    return s;
+}
+
+mgx_status mgx_mlp_train(mgx_ctx *ctx, const float *X, const float *t, int64_t n, int32_t epochs, int32_t batch,
+                         float lr, uint64_t seed, float *loss_per_epoch) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!X || !t || n < 1 || n >= (int64_t(1) << 31) || epochs < 1 || batch < 1 || !(lr > 0.0f) || !std::isfinite(lr))
+        return fail(ctx, MGX_EINVAL, "mlp_train: bad arguments");
+    if (!ctx->mlp_theta) return fail(ctx, MGX_ESTATE, "mlp_train: mgx_mlp_set_params not called");
+    DeviceGuard g(ctx->device);
+    float *Xd = nullptr, *td = nullptr;
+    int32_t *perm = nullptr;
+    CK(dalloc(ctx, &Xd, size_t(n) * 8));
+    CK(dalloc(ctx, &td, size_t(n)));
+    CK(dalloc(ctx, &perm, size_t(n)));
+    CK(cudaMemcpyAsync(Xd, X, size_t(n) * 8 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(td, t, size_t(n) * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    std::vector<int32_t> order(static_cast<size_t>(n));
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    uint64_t state = seed;
+    auto next_u64 = [&state]() {  // SplitMix64 (Steele, Lea & Flood 2014) for the shuffles
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    for (int32_t ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = 0; i < n; ++i) order[size_t(i)] = int32_t(i);
+        for (int64_t i = n - 1; i > 0; --i) std::swap(order[size_t(i)], order[size_t(next_u64() % uint64_t(i + 1))]);
+        CK(cudaMemcpyAsync(perm, order.data(), size_t(n) * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemsetAsync(ctx->mlp_loss, 0, sizeof(float), ctx->stream));
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int64_t rows = std::min<int64_t>(batch, n - b0);
+            {
+                Timed tm(ctx, MGX_K_OTHER);
+                launch_mlp(true, Xd, td, perm + b0, rows, ctx->mlp_W1b, ctx->mlp_W2b, ctx->mlp_theta, nullptr,
+                           ctx->mlp_grad, ctx->mlp_loss, float(2.0 / double(rows)), ctx->stream);
+            }
+            ctx->mlp_step += 1;
+            const float c1 = float(1.0 / (1.0 - std::pow(double(b1), double(ctx->mlp_step))));
+            const float c2 = float(1.0 / (1.0 - std::pow(double(b2), double(ctx->mlp_step))));
+            {
+                Timed tm(ctx, MGX_K_OTHER);
+                launch_mlp_adam(ctx->mlp_theta, ctx->mlp_m, ctx->mlp_v, ctx->mlp_grad, lr, b1, b2, eps, c1, c2,
+                                ctx->mlp_W1b, ctx->mlp_W2b, ctx->stream);
+            }
+        }
+        CK(cudaGetLastError());
+        if (loss_per_epoch) {
+            float lsum = 0.0f;
+            CK(cudaMemcpyAsync(&lsum, ctx->mlp_loss, sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            loss_per_epoch[ep] = lsum / float(n);
+        }
+    }
+    dfree(ctx, Xd);
+    dfree(ctx, td);
+    dfree(ctx, perm);
+    return sync_status(ctx);
+}
+
+mgx_status mgx_mlp_features(mgx_ctx *ctx, int32_t model, const double *rho, const double *T, float *X) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "mlp_features: no model %d", model);
+    if (!m->has_lines) return fail(ctx, MGX_ESTATE, "mlp_features: set_lines not called");
+    if (!rho || !T || !X) return fail(ctx, MGX_EINVAL, "mlp_features: null pointer");
+    for (int64_t i = 0; i < m->n; ++i)
+        if (!(rho[i] > 0.0) || !(T[i] > 0.0) || !std::isfinite(rho[i]) || !std::isfinite(T[i]))
+            return fail(ctx, MGX_EINVAL, "mlp_features: rho and T must be positive and finite (point %lld)", (long long)i);
+    DeviceGuard g(ctx->device);
+    const size_t n = size_t(m->n);
+    double *rd = nullptr, *Td = nullptr;
+    float *Xd = nullptr;
+    CK(dalloc(ctx, &rd, n));
+    CK(dalloc(ctx, &Td, n));
+    CK(dalloc(ctx, &Xd, n * 8));
+    CK(cudaMemcpyAsync(rd, rho, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(Td, T, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_mlp_features(mesh_view(*m), m->chi0f, m->L, m->dvwf, rd, Td, Xd, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(X, Xd, n * 8 * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, rd);
+    dfree(ctx, Td);
+    dfree(ctx, Xd);
+    return sync_status(ctx);
+}
+
+mgx_status mgx_reduce_mesh_learned(mgx_ctx *ctx, int32_t model, const float *X, double keep_fraction, uint8_t *keep,
+                                   int64_t *n_kept) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "reduce_mesh_learned: no model %d", model);
+    if (!X || !keep || !(keep_fraction >= 0.0) || !(keep_fraction <= 1.0))
+        return fail(ctx, MGX_EINVAL, "reduce_mesh_learned: bad arguments");
+    if (!ctx->mlp_theta) return fail(ctx, MGX_ESTATE, "reduce_mesh_learned: mgx_mlp_set_params not called");
+    DeviceGuard g(ctx->device);
+    const int64_t n = m->n;
+    const int64_t k = std::llround(keep_fraction * double(n));
+    float *Xd = nullptr, *yd = nullptr, *ys = nullptr;
+    int32_t *ids = nullptr, *ids_s = nullptr;
+    uint8_t *kd = nullptr;
+    CK(dalloc(ctx, &Xd, size_t(n) * 8));
+    CK(dalloc(ctx, &yd, size_t(n)));
+    CK(dalloc(ctx, &ys, size_t(n)));
+    CK(dalloc(ctx, &ids, size_t(n)));
+    CK(dalloc(ctx, &ids_s, size_t(n)));
+    CK(dalloc(ctx, &kd, size_t(n)));
+    CK(cudaMemcpyAsync(Xd, X, size_t(n) * 8 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_mlp(false, Xd, nullptr, nullptr, n, ctx->mlp_W1b, ctx->mlp_W2b, ctx->mlp_theta, yd, nullptr, nullptr,
+                   0.0f, ctx->stream);
+        launch_select_top(yd, n, k, ids, ys, ids_s, kd, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(keep, kd, size_t(n), cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, Xd); dfree(ctx, yd); dfree(ctx, ys); dfree(ctx, ids); dfree(ctx, ids_s); dfree(ctx, kd);
+    const mgx_status s = sync_status(ctx);
+    if (n_kept) *n_kept = k;
+    return s;
 }
 
 mgx_status mgx_profile_enable(mgx_ctx *ctx, int32_t enable) {

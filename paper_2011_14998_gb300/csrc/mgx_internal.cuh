@@ -152,6 +152,22 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
                   double dv_max, double I_bdy, int precision, double *J, int *status, cudaStream_t st,
                   char *err, size_t errlen);
 
+// ---- learned reduction network (k_mlp.cu); parameter offsets in theta
+constexpr int kMlpW1 = 0, kMlpB1 = 512, kMlpW2 = 576, kMlpB2 = 4672, kMlpW3 = 4736, kMlpB3 = 4800, kMlpN = 4801;
+size_t mlp_smem_bytes();
+void launch_mlp_convert(const float *theta, void *W1b, void *W2b, cudaStream_t st);
+// train == false: y[r] = network(X[perm[r]]); train == true: adds the gradient of
+// sum_r (y - t)^2 * inv_batch / 2 ... scaled so that inv_batch = 2 / B gives the MSE gradient
+void launch_mlp(bool train, const float *X, const float *t, const int32_t *perm, int64_t rows, const void *W1b,
+                const void *W2b, const float *theta, float *y, float *grad, float *loss, float inv_batch,
+                cudaStream_t st);
+void launch_mlp_adam(float *theta, float *m, float *v, float *grad, float lr, float b1, float b2, float eps, float c1,
+                     float c2, void *W1b, void *W2b, cudaStream_t st);
+void launch_mlp_features(const DevMesh &m, const float *chi0, int32_t L, const float *dvw, const double *rho,
+                         const double *T, float *X, cudaStream_t st);
+void launch_select_top(const float *score, int64_t n, int64_t k, int32_t *ids, float *score_sorted,
+                       int32_t *ids_sorted, uint8_t *keep, cudaStream_t st);
+
 // ---- host HEALPix tables (hpx_host.cpp)
 int64_t hpx_npix(int l);
 void hpx_pix2vec(int l, int64_t p, double v[3]);
