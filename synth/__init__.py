@@ -147,3 +147,51 @@ def random_cloud(n: int = 40, seed: int = 0, n_lines: int = 1, n_freq: int = 7,
         eta0=chi0 * S, dvw=doppler_width(T), chi_c=chi_c, eta_c=chi_c * S[:, 0],
         n_freq=n_freq, x_span=x_span, l_min=l_min, l_max=l_max,
         sample=sample_indices(n), rho=rng.uniform(0.1, 1.0, n), T=T)
+
+
+def spiral_model(n: int = 1_000_000, seed: int = 4, n_freq: int = 100, x_span: float = 4.0, level: int = 2,
+                 l_min: int | None = None, box: float = 1200.0, arm_spacing: float = 50.0,
+                 contrast: float = 10.0, tau_radial: float = 10.0, cont_frac: float = 1e-4):
+    """Binary-wind Archimedean spiral as an SPH-like particle cloud: density
+    rho ~ r^-2 (1 + (contrast - 1) g), g a Gaussian arm profile around the
+    spiral r = r0 + arm_spacing phi / 2 pi in the orbital plane (arm half-width
+    8 AU, scale height 30 AU), in a box of `box` AU; equal-mass particles
+    (positions drawn with probability ~ rho), Delaunay neighbours, a 15 km/s
+    radial wind with 1 km/s noise, T = 2000 K (r / 10 AU)^-0.7."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5B]))
+    r_in, r_out = 10.0, box / 2.0
+
+    def arm(x):
+        r = np.sqrt(x[:, 0] ** 2 + x[:, 1] ** 2)
+        ph = np.arctan2(x[:, 1], x[:, 0]) % (2 * np.pi)
+        r0 = r_in + arm_spacing * ph / (2 * np.pi)
+        d = np.abs(((r - r0 + 0.5 * arm_spacing) % arm_spacing) - 0.5 * arm_spacing)
+        return np.exp(-(d / 8.0) ** 2) * np.exp(-(x[:, 2] / 30.0) ** 2)
+
+    pts = []
+    need = n
+    while need > 0:
+        m = int(need * 2.5) + 1000
+        r = rng.uniform(r_in, r_out, m)  # mass ~ rho r^2 dr is uniform in r for rho ~ r^-2
+        mu = rng.uniform(-1.0, 1.0, m)
+        ph = rng.uniform(0.0, 2 * np.pi, m)
+        st = np.sqrt(1 - mu * mu)
+        x = np.stack([st * np.cos(ph), st * np.sin(ph), mu], 1) * r[:, None]
+        acc = rng.uniform(0.0, 1.0, m) < (1 + (contrast - 1) * arm(x)) / contrast
+        pts.append(x[acc][:need])
+        need -= len(pts[-1])
+    pos = np.concatenate(pts)[:n]
+    off, nbr = delaunay_csr(pos)
+    r = np.sqrt((pos ** 2).sum(1))
+    rhat = pos / r[:, None]
+    vel = 15.0 * rhat + rng.normal(0.0, 1.0, (n, 3))
+    rho = (r / r_in) ** -2.0 * (1 + (contrast - 1) * arm(pos))
+    T = 2000.0 * (r / r_in) ** -0.7
+    k = tau_radial / (r_in * (1 - r_in / r_out))  # radial line-centre depth of the smooth r^-2 part
+    chi0 = (k * rho)[:, None]
+    S = T / 2000.0
+    chi_c = cont_frac * chi0[:, 0]
+    return dict(
+        name=f"spiral{n}", pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr, nu0=np.array([NU_CO10]), chi0=chi0,
+        eta0=chi0 * S[:, None], dvw=doppler_width(T), chi_c=chi_c, eta_c=chi_c * S, n_freq=n_freq, x_span=x_span,
+        l_min=level if l_min is None else l_min, l_max=level, sample=sample_indices(n, 10000, seed), rho=rho, T=T)

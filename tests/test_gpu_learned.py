@@ -1,0 +1,61 @@
+"""The learned reduction against the plain criterion (Section 2.2.2) on a held-out
+spiral model: the network is trained on the GPU from J errors that plain
+reductions of other seeds produce, then both methods keep the same number of
+points of the test model and the J error after re-meshing and barycentric
+interpolation back to the full mesh is compared."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SOLVE = dict(dtau_max=0.5, dv_max=1.0 / 3.0)
+SPH = (1.0, 2.15, 0.21)  # Table 1, SPH row
+
+
+def test_learned_reduction_beats_plain_criterion():
+    import synth
+
+    import paper_2011_14998_gb300 as mgx
+    from paper_2011_14998_gb300 import learned
+
+    mgx.build()
+    ctx = mgx.Context(0)
+    try:
+        n, kw = 8000, dict(n_freq=16, level=1)
+        Xs, ys = [], []
+        for seed in (100, 101, 102, 103):
+            m = synth.spiral_model(n, seed=seed, **kw)
+            reds = [(SPH[0], fl, SPH[2], 1000 + seed * 10 + j) for j, fl in enumerate((1.7, 2.15, 2.6))]
+            X, y = learned.training_samples(ctx, m, reds, **SOLVE)
+            Xs.append(X)
+            ys.append(y)
+        X, y = np.concatenate(Xs), np.concatenate(ys)
+        std, losses, _ = learned.train_network(ctx, X, y, epochs=60, seed=1)
+        assert losses[-1] < losses[0]
+
+        test = synth.spiral_model(n, seed=4, **kw)
+        mid = ctx.load(test)
+        J_full = ctx.solve_J(mid, precision=mgx.MGX_FP32, **SOLVE)
+        keep_plain = ctx.reduce_mesh(mid, test["rho"], *SPH, seed=77)[3]
+        frac = keep_plain.mean()
+        keep_mlp = learned.reduce_learned(ctx, mid, test, std, frac)
+        ctx.free(mid)
+        assert keep_mlp.sum() == round(frac * n)
+        e_plain = learned.reduction_error(ctx, test, J_full, keep_plain, **SOLVE)
+        e_mlp = learned.reduction_error(ctx, test, J_full, keep_mlp, **SOLVE)
+        res = dict(n_points=n, kept_fraction=float(frac), reduction_factor=float(1 / frac),
+                   mean_rel_err_plain=float(e_plain.mean()), mean_rel_err_learned=float(e_mlp.mean()),
+                   p90_plain=float(np.quantile(e_plain, 0.9)), p90_learned=float(np.quantile(e_mlp, 0.9)),
+                   gain=float(e_plain.mean() / e_mlp.mean()), train_samples=int(len(y)),
+                   loss_first=float(losses[0]), loss_last=float(losses[-1]))
+        print(json.dumps(res))
+        out = os.environ.get("MGX_LEARNED_REPORT")
+        if out:
+            with open(out, "w") as f:
+                json.dump(res, f)
+        assert e_mlp.mean() <= e_plain.mean()
+    finally:
+        ctx.close()
