@@ -195,3 +195,167 @@ def spiral_model(n: int = 1_000_000, seed: int = 4, n_freq: int = 100, x_span: f
         name=f"spiral{n}", pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr, nu0=np.array([NU_CO10]), chi0=chi0,
         eta0=chi0 * S[:, None], dvw=doppler_width(T), chi_c=chi_c, eta_c=chi_c * S, n_freq=n_freq, x_span=x_span,
         l_min=level if l_min is None else l_min, l_max=level, sample=sample_indices(n, 10000, seed), rho=rho, T=T)
+
+
+def _clump_params(rng, n_clumps: int, box: float):
+    centres = rng.uniform(-0.3 * box, 0.3 * box, (n_clumps, 3))
+    sigmas = rng.uniform(30.0, 80.0, n_clumps)
+    return centres, sigmas
+
+
+def _clump_density(x, centres, sigmas, contrast):
+    rho = np.ones(len(x))
+    for c, s in zip(centres, sigmas):
+        rho += (contrast - 1.0) * np.exp(-((x - c) ** 2).sum(1) / (2 * s * s))
+    return rho
+
+
+def _refine(box, lo_level, hi_level, centres, sigmas, contrast, thr, q):
+    """Leaves (level, i, j, k) of an octree over [-box/2, box/2]^3: every cell
+    down to lo_level, then a cell of level l is split while the largest density
+    inside it (the clump profiles evaluated at each clump's nearest point of the
+    cell) exceeds thr * q^(l - lo_level)."""
+    n0 = 2 ** lo_level
+    ijk = np.stack(np.meshgrid(*([np.arange(n0)] * 3), indexing="ij"), -1).reshape(-1, 3)
+    leaves = []
+    for l in range(lo_level, hi_level + 1):
+        h = box / 2 ** l
+        lo = -box / 2 + ijk * h
+        rho_max = np.ones(len(ijk))
+        for c, s in zip(centres, sigmas):
+            near = np.clip(c, lo, lo + h)
+            rho_max += (contrast - 1.0) * np.exp(-((near - c) ** 2).sum(1) / (2 * s * s))
+        split = rho_max > thr * q ** (l - lo_level) if l < hi_level else np.zeros(len(ijk), bool)
+        leaves.append(np.concatenate([np.full((int((~split).sum()), 1), l), ijk[~split]], 1))
+        kids = ijk[split]
+        d = np.stack(np.meshgrid([0, 1], [0, 1], [0, 1], indexing="ij"), -1).reshape(-1, 3)
+        ijk = (2 * kids[:, None, :] + d[None]).reshape(-1, 3)
+    return np.concatenate(leaves)
+
+
+def octree_leaf_csr(leaves: np.ndarray, hi_level: int):
+    """Neighbour CSR of octree leaves: two leaves are neighbours when their closed
+    cubes touch (share a face, an edge or a corner). Every leaf is rasterised
+    on the finest grid; two leaves touch iff two of their fine voxels are
+    26-adjacent."""
+    g = 2 ** hi_level
+    grid = np.empty((g, g, g), np.int32)
+    for l in np.unique(leaves[:, 0]):
+        sel = np.where(leaves[:, 0] == l)[0]
+        s = 2 ** (hi_level - l)
+        v = grid.reshape(g // s, s, g // s, s, g // s, s)
+        i, j, k = leaves[sel, 1], leaves[sel, 2], leaves[sel, 3]
+        v[i, :, j, :, k, :] = sel.astype(np.int32)[:, None, None, None]
+    a_all, b_all = [], []
+    offs = [(dx, dy, dz) for dx in (-1, 0, 1) for dy in (-1, 0, 1) for dz in (-1, 0, 1) if (dx, dy, dz) > (0, 0, 0)]
+    for dx, dy, dz in offs:
+        sa = tuple(slice(max(0, -d), g - max(0, d)) for d in (dx, dy, dz))
+        sb = tuple(slice(max(0, d), g - max(0, -d)) for d in (dx, dy, dz))
+        A, B = grid[sa].ravel(), grid[sb].ravel()
+        diff = A != B
+        key = np.unique(np.minimum(A[diff], B[diff]).astype(np.int64) * len(leaves) + np.maximum(A[diff], B[diff]))
+        a_all.append(key // len(leaves))
+        b_all.append(key % len(leaves))
+    return csr_from_pairs(len(leaves), np.concatenate(a_all), np.concatenate(b_all))
+
+
+def _fourier_velocity(pos, rng, n_modes: int, rms: float, box: float):
+    """Smooth random velocity field: a sum of n_modes seeded Fourier modes with
+    wavelengths between box/8 and box, each component scaled to the given rms
+    over the points."""
+    kdir = rng.normal(size=(n_modes, 3))
+    kdir /= np.linalg.norm(kdir, axis=1, keepdims=True)
+    lam = box * np.exp(rng.uniform(np.log(1 / 8), 0.0, n_modes))
+    kvec = kdir * (2 * np.pi / lam)[:, None]
+    amp = rng.normal(size=(n_modes, 3)) * (lam / box)[:, None]
+    phase = rng.uniform(0.0, 2 * np.pi, n_modes)
+    v = np.cos(pos @ kvec.T + phase) @ amp
+    v -= v.mean(0)
+    return v * (rms / v.std(0))
+
+
+def multi_line(nu0: float, n_lines: int, spacing: float = 1e-3):
+    """Line centres spaced by `spacing` in relative frequency (300 km/s for 1e-3),
+    several hundred thermal widths apart."""
+    return nu0 * (1.0 + spacing * np.arange(n_lines))
+
+
+def octree_model(n_leaves: int = 300_000, seed: int = 3, n_lines: int = 2, n_freq: int = 64, x_span: float = 4.0,
+                 l_min: int = 0, l_max: int = 3, box: float = 1000.0, lo_level: int = 3, hi_level: int = 8,
+                 contrast: float = 1e3, v_rms: float = 2.0, n_modes: int = 64, tau_box: float = 1.0,
+                 line_ratio: float = 0.1, cont_frac: float = 1e-4, velocity: str = "fourier"):
+    """Octree AMR-like mesh of leaf-cell centres: a box of `box` AU refined from
+    lo_level to hi_level around three seeded Gaussian clumps (sigma 30-80 AU,
+    peak/background density contrast `contrast`), with the split threshold tuned
+    by bisection so that the leaf count is close to n_leaves. Neighbours are the
+    leaves whose closed cubes touch. Velocity: a smooth field of n_modes Fourier
+    modes (or i.i.d. Gaussian per leaf with velocity='iid'), v_rms per component.
+    n_lines lines with line-centre opacity ratio 1 : line_ratio : line_ratio^2 ...,
+    opacity ~ density with a line-centre optical depth tau_box across the box
+    at background density, T = 1000 K rho^-0.2, S = T / 1000 K."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x0C]))
+    centres, sigmas = _clump_params(rng, 3, box)
+    lo, hi = 1.0, contrast
+    best = None
+    for _ in range(40):  # bisection on log threshold; leaf count decreases with it
+        thr = np.sqrt(lo * hi)
+        leaves = _refine(box, lo_level, hi_level, centres, sigmas, contrast, thr, 2.0)
+        if best is None or abs(len(leaves) - n_leaves) < abs(len(best) - n_leaves):
+            best = leaves
+        if len(leaves) > n_leaves:
+            lo = thr
+        else:
+            hi = thr
+        if hi / lo < 1.0 + 1e-4 or abs(len(leaves) - n_leaves) <= 0.01 * n_leaves:
+            break
+    leaves = best
+    n = len(leaves)
+    h = box / 2.0 ** leaves[:, 0]
+    pos = -box / 2 + (leaves[:, 1:] + 0.5) * h[:, None]
+    off, nbr = octree_leaf_csr(leaves, hi_level)
+    if velocity == "iid":
+        vel = rng.normal(0.0, v_rms, (n, 3))
+    else:
+        vel = _fourier_velocity(pos, rng, n_modes, v_rms, box)
+    rho = _clump_density(pos, centres, sigmas, contrast)
+    T = 1000.0 * rho ** -0.2
+    S = T / 1000.0
+    chi0 = (tau_box / box) * rho[:, None] * line_ratio ** np.arange(n_lines)[None, :]
+    chi_c = cont_frac * chi0[:, 0]
+    return dict(
+        name=f"octree{n}", pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr, nu0=multi_line(NU_CO10, n_lines), chi0=chi0,
+        eta0=chi0 * S[:, None], dvw=doppler_width(T), chi_c=chi_c, eta_c=chi_c * S, n_freq=n_freq, x_span=x_span,
+        l_min=l_min, l_max=l_max, sample=sample_indices(n, 10000, seed), rho=rho, T=T, level=leaves[:, 0])
+
+
+def with_lines(m: dict, n_lines: int, n_freq: int, line_ratio: float = 0.5) -> dict:
+    """The model with its first line's opacity and source function repeated over
+    n_lines separated lines (opacity ratio 1 : line_ratio : ...)."""
+    out = dict(m)
+    S = m["eta0"][:, :1] / m["chi0"][:, :1]
+    chi0 = m["chi0"][:, :1] * line_ratio ** np.arange(n_lines)[None, :]
+    out.update(nu0=multi_line(m["nu0"][0], n_lines), chi0=chi0, eta0=chi0 * S, n_freq=n_freq)
+    return out
+
+
+def batch_models(n_models: int = 64, seed: int = 5, n_min: int = 10_000, n_max: int = 200_000, n_lines: int = 4,
+                 n_freq: int = 100, l_min: int = 0, l_max: int = 3):
+    """Independent models with seeded sizes log-uniform in [n_min, n_max], the
+    generators taken in turn (Cartesian grid, stellar wind, clump octree), each
+    with n_lines separated lines of n_freq bins and adaptive rays l_min..l_max."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA]))
+    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_models)).astype(np.int64)
+    out = []
+    for k, n in enumerate(sizes):
+        s = seed * 1000 + k
+        kind = k % 3
+        if kind == 0:
+            m = grid_model(max(3, int(round(n ** (1 / 3)))), n_freq=n_freq)
+            m = with_lines(m, n_lines, n_freq)
+        elif kind == 1:
+            m = with_lines(wind_model(int(n), seed=s, n_freq=n_freq), n_lines, n_freq)
+        else:
+            m = octree_model(int(n), seed=s, n_lines=n_lines, n_freq=n_freq, hi_level=max(5, min(8, int(np.log2(n) / 3) + 3)))
+        m.update(l_min=l_min, l_max=l_max, name=f"{m['name']}_b{k}")
+        out.append(m)
+    return out

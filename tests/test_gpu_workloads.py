@@ -1,0 +1,113 @@
+"""Parity on the shapes of the remaining workloads, through the C-ABI:
+
+* a clump octree (leaf-cell centres, levels 3-6, two lines x 64 bins, adaptive
+  rays l 0-3, smooth Fourier velocity field) -- FP64 within 1e-10 and FP32 within
+  1e-4 of the oracle on sampled origins, for the per-model and the batched form;
+* a batch of mixed models (grid, wind, octree in turn; four lines x 100 bins;
+  adaptive rays l 0-3) in one persistent launch replayed from a CUDA graph --
+  four of them against the oracle;
+* the 50,000-point wind at full size in the launch configuration that the
+  benchmark times (batched FP32, ray sets rebuilt inside the graph) -- sampled
+  origins against the oracle, and the traced lists bit-exact."""
+import numpy as np
+import pytest
+
+from helpers import j_rel_err
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2011_14998_gb300 as mgx
+
+    mgx.build()
+    c = mgx.Context(0)
+    yield c
+    c.close()
+
+
+def _sample(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False))
+
+
+def test_octree_adaptive_two_lines(ctx, orc):
+    import synth
+
+    import paper_2011_14998_gb300 as mgx
+
+    m = synth.octree_model(6000, seed=13, hi_level=6)
+    mid = ctx.load(m)
+    rays = ctx.rays(mid)
+    assert rays.shape == (len(m["pos"]), 69)
+    J64 = ctx.solve_J(mid, precision=mgx.MGX_FP64)
+    J32 = ctx.solve_J(mid, precision=mgx.MGX_FP32)
+    Jb32 = ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, flags=mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS)[0]
+    ctx.free(mid)
+    assert J64.shape == (len(m["pos"]), 128)
+    origins = _sample(len(m["pos"]), 300, 1)
+    om = orc.OracleModel(m, rays=rays)
+    Jo = om.solve_J(orc.params(), origins=origins)
+    Jo32 = om.solve_J(orc.params(decide32=True), origins=origins)
+    assert j_rel_err(J64[origins], Jo)[0] < FP64_TOL
+    assert j_rel_err(J32[origins], Jo32)[0] < FP32_TOL
+    assert j_rel_err(Jb32.cpu().numpy()[origins], Jo32)[0] < FP32_TOL
+
+
+def test_mixed_batch_four_lines(ctx, orc):
+    import synth
+
+    import paper_2011_14998_gb300 as mgx
+
+    models = synth.batch_models(n_models=6, seed=21, n_min=800, n_max=4000, n_lines=4, n_freq=100)
+    mids = [ctx.load(m) for m in models]
+    out32 = ctx.solve_J_batch(mids, precision=mgx.MGX_FP32, flags=mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS)
+    out64 = ctx.solve_J_batch(mids, precision=mgx.MGX_FP64)
+    rays = [ctx.rays(k) for k in mids]
+    for k in mids:
+        ctx.free(k)
+    for j in range(4):
+        m = models[j]
+        assert out32[j].shape == (len(m["pos"]), 400)
+        origins = _sample(len(m["pos"]), 60, 2 + j)
+        om = orc.OracleModel(m, rays=rays[j])
+        Jo = om.solve_J(orc.params(), origins=origins)
+        Jo32 = om.solve_J(orc.params(decide32=True), origins=origins)
+        assert j_rel_err(out64[j].cpu().numpy()[origins], Jo)[0] < FP64_TOL, m["name"]
+        assert j_rel_err(out32[j].cpu().numpy()[origins], Jo32)[0] < FP32_TOL, m["name"]
+
+
+def test_wind_full_size_bench_configuration(ctx, orc):
+    import synth
+
+    import paper_2011_14998_gb300 as mgx
+
+    m = synth.wind_model()  # 50,000 points, 1 line x 50 bins, l = 2
+    mid = ctx.load(m)
+    flags = mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS
+    out = ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, flags=flags)[0]
+    ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, outs=[out], flags=flags)  # graph replay
+    J32 = out.cpu().numpy()
+    rays = ctx.rays(mid)
+    origins = _sample(len(m["pos"]), 200, 3)
+    o64 = origins[:40]
+    J64 = ctx.solve_J(mid, precision=mgx.MGX_FP64)
+    # traced lists of sampled origins, bit-exact against the oracle tracer
+    traced = {int(o): ctx.trace(mid, int(o), int(o) + 1) for o in origins[:8]}
+    ctx.free(mid)
+    om = orc.OracleModel(m, rays=rays)
+    for o, (off, idx, Z, _) in traced.items():
+        for h in range(len(off) - 1):
+            ray = rays[o, h // 2]
+            d = orc.pix2vec(int(ray >> 28), int(ray & 0x0FFFFFFF)) * (-1.0 if h % 2 == 0 else 1.0)
+            ri, rz = om.trace_half(o, d)
+            assert np.array_equal(idx[off[h]:off[h + 1]], ri)
+            assert np.array_equal(Z[off[h]:off[h + 1]], rz)
+    assert np.all(np.isfinite(J32)) and J32.min() >= 0
+    Jo32 = om.solve_J(orc.params(decide32=True), origins=origins)
+    assert j_rel_err(J32[origins], Jo32)[0] < FP32_TOL
+    Jo = om.solve_J(orc.params(), origins=o64)
+    assert j_rel_err(J64[o64], Jo)[0] < FP64_TOL
