@@ -373,8 +373,10 @@ def run_mgx(args):
 
 
 def run_profile_case(args):
-    """Two FP32 solves of an N-point wind (same generator and settings as the
-    benchmark), for profiler captures of single kernel launches."""
+    """Two solves of an N-point wind (same generator and settings as the
+    benchmark) through the batched entry point without graph capture, so that
+    each kernel of the timed step (ray sets, both trace passes, scan, work
+    list, persistent solve) is a separate launch a profiler can select."""
     import torch
 
     import paper_2011_14998_gb300 as mgx
@@ -384,11 +386,12 @@ def run_profile_case(args):
     m = make_workload(n)
     ctx = mgx.Context(0)
     mid = ctx.load(m)
-    out = torch.empty((n, len(m["nu0"]) * int(m["n_freq"])), dtype=torch.float64, device="cuda")
     prec = mgx.MGX_FP64 if args.profile_fp64 else mgx.MGX_FP32
     ctx.profile(True)
+    outs = None
     for _ in range(2):
-        ctx.solve_J(mid, precision=prec, dtau_max=0.5, dv_max=1.0 / 3.0, out=out)
+        outs = ctx.solve_J_batch([mid], precision=prec, dtau_max=0.5, dv_max=1.0 / 3.0, outs=outs,
+                                 flags=mgx.MGX_BATCH_RAYS)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": n, "counters": ctx.profile_read()}))
     ctx.close()

@@ -163,21 +163,23 @@ __device__ __forceinline__ void optics(const Sample<R, NL> &s, R rdv, const Bin<
 // empty-half coupling (D Fh, zh) = (1, I).
 template <typename R>
 struct Sweep {
-    R Fh, Dm, zh, dtp;  // scaled 1+B quantities of the last eliminated row, its dtau
+    R Fh, Dm, zh, dtp;  // scaled 1+B quantities of the last eliminated row, half its dtau
     R chi, eta;         // optics of the current (not yet eliminated) sample
 };
 
 // Eliminate the row of the current sub-point (optics chi, eta) once the
 // increment dt beyond it is known.  One reciprocal R = 1 / (chi (1 + dt Fh))
-// gives D = chi R and D S = eta R.
+// gives D = chi R and D S = eta R.  The state carries half the previous
+// increment, so dtbar = (dt_prev + dt) / 2 is one fused operation (the
+// halvings are exact, so the rounding is that of the plain expression).
 template <typename R>
 __device__ __forceinline__ void row(Sweep<R> &w, R chi, R eta, R dt) {
-    const R dtb = (w.dtp + dt) * R(0.5);
+    const R dtb = fma(dt, R(0.5), w.dtp);
     w.Fh = dtb + w.Dm * w.Fh;
     const R rr = Ar<R>::rcp(chi * (R(1) + dt * w.Fh));
     w.Dm = chi * rr;
     w.zh = w.Dm * w.zh + dtb * (eta * rr);
-    w.dtp = dt;
+    w.dtp = dt * R(0.5);
 }
 
 // One velocity sample q at distance hs beyond the previous one, for every bin
@@ -198,9 +200,10 @@ __device__ __forceinline__ void sample_step(const Sample<R, NL> &q, R hs, R dtau
         split |= x[i] > R(1);
     }
     if (!__any_sync(0xffffffffu, split)) {
+        const R hh = hs * R(0.5);
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
-            row(w[i], w[i].chi, w[i].eta, hs * (w[i].chi + chi_q[i]) * R(0.5));
+            row(w[i], w[i].chi, w[i].eta, hh * (w[i].chi + chi_q[i]));
             w[i].chi = chi_q[i];
             w[i].eta = eta_q[i];
         }
@@ -247,7 +250,10 @@ __device__ __forceinline__ int velocity_samples(R da, R wa, R db, R wb, R dv_max
 }
 
 // One interval from the current point (cur, modified in place) to nxt with nv
-// velocity samples: interpolated samples, then nxt itself.
+// velocity samples: interpolated samples, then nxt itself.  (Inlining the
+// sample step at its three sites measured faster than one call site in a
+// loop with a select: the interpolation increments stay out of the common
+// one-sample path.)
 template <typename R, int NL, int BPL>
 __device__ __forceinline__ void interval(Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds, int nv,
                                          const SolveArgs &a, R dtau_max, R inv_dtau_max,
@@ -295,6 +301,32 @@ __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t id, double x
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2));
 }
 
+// Where the ids of one half-ray are: entries k < n_main at main[k], the rest
+// at tail[tail_off + k] (padded layout); cnt entries in all.
+struct HalfList {
+    const int32_t *main;
+    const int32_t *tail;
+    int64_t tail_off;
+    int32_t n_main, cnt;
+};
+
+__device__ __forceinline__ HalfList half_list(const SolveArgs &a, int64_t h) {
+    HalfList l;
+    if (a.pad == 0) {
+        l.main = a.idx + (a.offs[h] - a.base);
+        l.cnt = l.n_main = int32_t(a.offs[h + 1] - a.offs[h]);
+        l.tail = a.idx;
+        l.tail_off = 0;
+    } else {
+        l.cnt = int32_t(a.lens[h]);
+        l.main = a.idx + h * a.pad;
+        l.n_main = l.cnt < a.pad ? l.cnt : a.pad;
+        l.tail = a.tail;
+        l.tail_off = a.offs[h] - a.base - a.pad;
+    }
+    return l;
+}
+
 // Per-warp staging area of 32 line points in shared memory.
 template <typename R, int NL>
 struct Stage {
@@ -313,7 +345,7 @@ struct Stage {
 // optical-depth increment in w.
 template <typename R, int NL, int BPL>
 __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &a, int32_t L, int lane,
-                           Stage<R, NL> &sg, int64_t beg, int32_t cnt, double xo, double yo, double zo,
+                           Stage<R, NL> &sg, const HalfList &hl, double xo, double yo, double zo,
                            double e0, double e1, double e2, R vox, R voy, R voz, int32_t o,
                            const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
                            unsigned &n_extra, unsigned &n_smp) {
@@ -324,6 +356,7 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
         w[i].zh = R(a.I_bdy);
         w[i].dtp = R(0);
     }
+    const int32_t cnt = hl.cnt;
     if (cnt == 0) return;
     const R dtau_max = R(a.dtau_max), inv_dtau_max = R(1.0 / a.dtau_max), dv_max = R(a.dv_max);
     const R d0 = R(e0), d1 = R(e1), d2 = R(e2);
@@ -336,7 +369,8 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
         Sample<R, NL> st;
         st.delta = st.dv = R(1);
         if (lane < nch) {
-            const int32_t id = __ldg(a.idx + beg + kb - lane);
+            const int32_t k = kb - lane;
+            const int32_t id = k < hl.n_main ? __ldg(hl.main + k) : __ldg(hl.tail + (hl.tail_off + k));
             zk = exact_Z(m, id, xo, yo, zo, e0, e1, e2);
             load_sample<R, NL>(D, L, id, vox, voy, voz, d0, d1, d2, st);
         }
@@ -457,15 +491,14 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
         const double *rv = Rs.dir + 3 * (level_offset(lev) + (ray & 0x0FFFFFFFu));
         const double r0 = rv[0], r1 = rv[1], r2 = rv[2];
         const int64_t hb = h0 + 2 * int64_t(p);
-        half_sweep<R, NL, BPL>(m, D, a, L, lane, sg, a.offs[hb] - a.base, int32_t(a.offs[hb + 1] - a.offs[hb]),
-                               xo, yo, zo, -r0, -r1, -r2, vox, voy, voz, o, f, act, wb, n_extra, n_smp);
-        half_sweep<R, NL, BPL>(m, D, a, L, lane, sg, a.offs[hb + 1] - a.base,
-                               int32_t(a.offs[hb + 2] - a.offs[hb + 1]), xo, yo, zo, r0, r1, r2, vox, voy, voz, o, f,
-                               act, wf, n_extra, n_smp);
+        half_sweep<R, NL, BPL>(m, D, a, L, lane, sg, half_list(a, hb), xo, yo, zo, -r0, -r1, -r2, vox, voy, voz, o,
+                               f, act, wb, n_extra, n_smp);
+        half_sweep<R, NL, BPL>(m, D, a, L, lane, sg, half_list(a, hb + 1), xo, yo, zo, r0, r1, r2, vox, voy, voz, o,
+                               f, act, wf, n_extra, n_smp);
         const double w2 = a.w2[lev];
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
-            const R dtb = (wb[i].dtp + wf[i].dtp) * R(0.5);
+            const R dtb = wb[i].dtp + wf[i].dtp;  // the halves of the two last increments
             const R u = (dtb * S_o[i] + wb[i].zh + wf[i].zh) / (dtb + wb[i].Dm * wb[i].Fh + wf[i].Dm * wf[i].Fh);
             const double xv = w2 * double(u);
             const double t = sum[i] + xv;  // Neumaier compensated sum

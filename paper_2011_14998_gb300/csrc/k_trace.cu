@@ -26,9 +26,18 @@
 // operation at all; the exact Z is formed only on undecided steps (and for
 // the inspection output of mgx_trace).
 //
-// Two passes share the walk: the count pass stores the half-ray lengths, which
-// are prefix-summed into arena offsets; the emit pass writes the point ids at
-// those offsets (the solver re-forms each point's exact Z from its position).
+// The walk serves three layouts of the traced lists (the solver re-forms each
+// point's exact Z from its position, so only point ids are stored):
+//   * packed: a count pass stores the half-ray lengths, which are prefix-summed
+//     into arena offsets, and an emit pass writes the ids at those offsets;
+//   * padded (batched solves): one pass writes the first `pad` ids of each
+//     half-ray into a fixed-width row h * pad, stores the full length and its
+//     excess over the row, and for a half-ray longer than the row the walk's
+//     state after its pad-th point; a tail pass resumes those walks from
+//     their states and writes the remaining ids into a packed overflow arena
+//     at the prefix sums of the excesses.  Every step is walked once by the
+//     padded pass and the tail steps once more, so the lists cost about one
+//     walk instead of two.
 #include "mgx_internal.cuh"
 
 namespace mgx {
@@ -150,7 +159,11 @@ __device__ Step step_contenders(const DevMesh &m, int32_t c, float4 oh, float Xo
 }
 
 // MODE 0: count the points of each half-ray; MODE 1: write their ids;
-// MODE 2: write ids, exact double Z and (optionally) projected velocities.
+// MODE 2: write ids, exact double Z and (optionally) projected velocities;
+// MODE 3: padded pass (ids k < pad to row h, length to lens[h], excess over
+// the row to excess[h], the walk state after entry pad - 1 to resume[h] when
+// the half-ray is longer); MODE 4: tail pass (ids k >= pad of the half-rays
+// longer than the row, at offs[h] - base + k - pad, resumed from resume[h]).
 // Each thread walks half-rays h = tid, tid + T, ... (T = all threads), which
 // evens out the very different lengths of the rays a warp's lanes trace.
 template <int MODE>
@@ -158,10 +171,16 @@ __global__ void __launch_bounds__(128)
 k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restrict__ lens,
         const int64_t *__restrict__ offs, int64_t base, int64_t cap, int32_t *__restrict__ idx_out,
         double *__restrict__ Z_out, double *__restrict__ delta_out, int *status,
-        unsigned long long *__restrict__ counters) {
+        unsigned long long *__restrict__ counters, int32_t pad, int64_t *__restrict__ excess,
+        int4 *__restrict__ resume) {
     const int64_t T = int64_t(gridDim.x) * blockDim.x;
     unsigned long long n_steps = 0, n_exact = 0;
     for (int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; h < n_half; h += T) {
+        int64_t expect_len = 0;
+        if (MODE == 4) {  // only the half-rays longer than their row
+            expect_len = lens[h];
+            if (expect_len <= pad) continue;
+        }
         const int64_t pr = h >> 1;
         const int32_t o = o_begin + int32_t(pr / R.npairs);
         const uint32_t ray = R.rays[int64_t(o) * R.npairs + (pr % R.npairs)];
@@ -177,16 +196,36 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         const float Xo = fabsf(oh.x) + fabsf(oh.y) + fabsf(oh.z);
         int64_t w = 0;
         int32_t expect = 0;
-        if (MODE > 0) {
+        if (MODE == 1 || MODE == 2) {
             w = offs[h] - base;
             expect = int32_t(offs[h + 1] - offs[h]);
             if (w < 0 || offs[h + 1] - base > cap) {
                 dev_fail(status, kDevArenaOverflow);
                 continue;
             }
+        } else if (MODE == 3) {
+            w = h * int64_t(pad);
+        } else if (MODE == 4) {
+            w = offs[h] - base - pad;  // entry k >= pad goes to w + k
+            expect = int32_t(expect_len);
+            if (offs[h] - base < 0 || offs[h + 1] - base > cap || offs[h + 1] - offs[h] != expect_len - pad) {
+                dev_fail(status, kDevArenaOverflow);
+                continue;
+            }
         }
         int32_t c = o, k = 0;
         float zc32 = 0.0f, ezc = 0.0f;  // Z of the origin is exactly 0
+        if (MODE == 4) {  // resume after the row's last entry
+            const int4 r = resume[h];
+            c = r.x;
+            zc32 = __int_as_float(r.y);
+            ezc = __int_as_float(r.z);
+            k = pad;
+            if (c < 0 || c >= m.n) {
+                dev_fail(status, kDevTraceMismatch);
+                continue;
+            }
+        }
         for (;;) {
             FStep s = step_screen(m, c, oh, Xo, f0, f1, f2, zc32, ezc);
             ++n_steps;
@@ -205,7 +244,15 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
                 s.ez = 2.0f * kU * fabsf(s.z32);
             }
             if (s.next < 0) break;
-            if (MODE > 0) {
+            if (MODE == 3) {
+                if (k < pad) idx_out[w + k] = s.next;
+            } else if (MODE == 4) {
+                if (k >= expect) {
+                    dev_fail(status, kDevTraceMismatch);
+                    return;
+                }
+                if (k >= pad) idx_out[w + k] = s.next;
+            } else if (MODE > 0) {
                 if (k >= expect) {
                     dev_fail(status, kDevTraceMismatch);
                     return;
@@ -227,15 +274,19 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
             c = s.next;
             zc32 = s.z32;
             ezc = s.ez;
+            if (MODE == 3 && k == pad) resume[h] = make_int4(c, __float_as_int(zc32), __float_as_int(ezc), 0);
             if (k > m.n) {  // Z increases strictly, so this cannot happen
                 dev_fail(status, kDevTraceGuard);
                 break;
             }
         }
-        if (MODE > 0) {
-            if (k != expect) dev_fail(status, kDevTraceMismatch);
-        } else {
+        if (MODE == 0) {
             lens[h] = k;
+        } else if (MODE == 3) {
+            lens[h] = k;
+            excess[h] = k > pad ? k - pad : 0;
+        } else if (k != expect) {
+            dev_fail(status, kDevTraceMismatch);
         }
     }
     if (counters) {
@@ -259,7 +310,7 @@ void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
     k_trace<0><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, nullptr, nullptr,
-                                                  nullptr, status, counters);
+                                                  nullptr, status, counters, 0, nullptr, nullptr);
 }
 
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
@@ -269,11 +320,30 @@ void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int3
     if (n_half == 0) return;
     if (Z) {
         k_trace<2><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx, Z,
-                                                      delta, status, nullptr);
+                                                      delta, status, nullptr, 0, nullptr, nullptr);
     } else {
         k_trace<1><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx,
-                                                      nullptr, nullptr, status, nullptr);
+                                                      nullptr, nullptr, status, nullptr, 0, nullptr, nullptr);
     }
+}
+
+void launch_trace_pad(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
+                      int64_t *lens, int64_t *excess, int4 *resume, int32_t *rows, int *status,
+                      unsigned long long *counters, cudaStream_t st) {
+    const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
+    if (n_half == 0) return;
+    k_trace<3><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, rows, nullptr,
+                                                  nullptr, status, counters, pad, excess, resume);
+}
+
+void launch_trace_tail(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
+                       const int64_t *lens, const int4 *resume, const int64_t *offs, int64_t base, int64_t cap,
+                       int32_t *tail, int *status, cudaStream_t st) {
+    const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
+    if (n_half == 0) return;
+    k_trace<4><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, const_cast<int64_t *>(lens), offs, base,
+                                                  cap, tail, nullptr, nullptr, status, nullptr, pad, nullptr,
+                                                  const_cast<int4 *>(resume));
 }
 
 }  // namespace mgx

@@ -47,21 +47,25 @@ struct Model {
 };
 
 // A batched solve kept for replay: its buffers and, in graph mode, the
-// instantiated CUDA graph of the whole step.
+// instantiated CUDA graph of the whole step.  Traced lists use the padded
+// layout (k_trace.cu): rows of `pad` ids per half-ray plus a tail arena for
+// the entries beyond the row, at the prefix sums (offs) of the excesses.
 struct BatchPlan {
     bool valid = false;
     std::vector<int32_t> models;
     std::vector<double *> J;
     mgx_solve_params p{};
     int32_t flags = 0;
-    int64_t total_half = 0, n_origins = 0, n_work = 0, arena_cap = 0;
+    int64_t total_half = 0, n_origins = 0, n_work = 0, tail_cap = 0, total_points = 0;
+    int32_t pad = 0;
     int bpl = 1, max_lines = 1;
-    int64_t *lens = nullptr, *offs = nullptr, *obase = nullptr;
-    int32_t *arena = nullptr;
+    int64_t *lens = nullptr, *excess = nullptr, *offs = nullptr, *obase = nullptr;
+    int32_t *rows = nullptr, *tail = nullptr;
+    int4 *resume = nullptr;
     BatchGeom *geo = nullptr;
     BatchSlot *slots = nullptr;
     uint2 *work = nullptr;
-    unsigned long long *scratch = nullptr;  // 64 work-list counters + the queue counter
+    unsigned long long *scratch = nullptr;  // 64 work-list counters, the queue counter, row-width totals
     void *cub_tmp = nullptr;
     size_t cub_bytes = 0;
     cudaGraph_t graph = nullptr;
@@ -376,9 +380,12 @@ void free_plan(mgx_ctx *ctx, BatchPlan &pl) {
     pl.exec = nullptr;
     pl.graph = nullptr;
     dfree(ctx, pl.lens);
+    dfree(ctx, pl.excess);
     dfree(ctx, pl.offs);
+    dfree(ctx, pl.rows);
+    dfree(ctx, pl.tail);
+    dfree(ctx, pl.resume);
     dfree(ctx, pl.obase);
-    dfree(ctx, pl.arena);
     dfree(ctx, pl.geo);
     dfree(ctx, pl.slots);
     dfree(ctx, pl.work);
@@ -400,47 +407,65 @@ void enqueue_rays(mgx_ctx *ctx, Model &m) {
     }
 }
 
-// Enqueue the tracing passes' first half: (ray sets,) counts and offsets.
-mgx_status enqueue_batch_count(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
+constexpr int kScratchQueue = 64;   // the persistent solve's work counter
+constexpr int kScratchTotals = 72;  // kPadCandidates + 1 row-width totals
+constexpr int kScratchSize = kScratchTotals + kPadCandidates + 1;
+
+// One step of a batched solve: (ray sets,) padded trace, tail offsets, tail
+// trace, work list, persistent solve.
+mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
     if (pl.flags & MGX_BATCH_RAYS)
         for (Model *m : ms) enqueue_rays(ctx, *m);
     int64_t hb = 0;
     for (Model *m : ms) {
         Timed t(ctx, MGX_K_TRACE_COUNT);
-        launch_trace_count(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.lens + hb, ctx->d_status,
-                           ctx->prof ? ctx->d_counters : nullptr, ctx->stream);
+        launch_trace_pad(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.pad, pl.lens + hb, pl.excess + hb,
+                         pl.resume + hb, pl.rows + hb * pl.pad, ctx->d_status,
+                         ctx->prof ? ctx->d_counters : nullptr, ctx->stream);
         hb += int64_t(m->n) * m->npairs * 2;
     }
     CK(cudaMemsetAsync(pl.offs, 0, sizeof(int64_t), ctx->stream));
     {
         Timed t(ctx, MGX_K_SCAN);
-        CK(cub::DeviceScan::InclusiveSum(pl.cub_tmp, pl.cub_bytes, pl.lens, pl.offs + 1, pl.total_half, ctx->stream));
+        CK(cub::DeviceScan::InclusiveSum(pl.cub_tmp, pl.cub_bytes, pl.excess, pl.offs + 1, pl.total_half,
+                                         ctx->stream));
     }
-    return MGX_OK;
-}
-
-// Enqueue the second half: point lists, work list, persistent solve.
-mgx_status enqueue_batch_solve(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
-    int64_t hb = 0;
-    for (Model *m : ms) {
-        Timed t(ctx, MGX_K_TRACE_EMIT);
-        launch_trace_emit(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.offs + hb, 0, pl.arena_cap, pl.arena,
-                          nullptr, nullptr, ctx->d_status, ctx->stream);
-        hb += int64_t(m->n) * m->npairs * 2;
+    if (pl.tail_cap > 0) {
+        hb = 0;
+        for (Model *m : ms) {
+            Timed t(ctx, MGX_K_TRACE_EMIT);
+            launch_trace_tail(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.pad, pl.lens + hb, pl.resume + hb,
+                              pl.offs + hb, 0, pl.tail_cap, pl.tail, ctx->d_status, ctx->stream);
+            hb += int64_t(m->n) * m->npairs * 2;
+        }
     }
     {
         Timed t(ctx, MGX_K_OTHER);
-        launch_batch_worklist(pl.geo, pl.obase, int32_t(ms.size()), pl.n_origins, pl.offs, pl.scratch, pl.work,
+        launch_batch_worklist(pl.geo, pl.obase, int32_t(ms.size()), pl.n_origins, pl.lens, pl.scratch, pl.work,
                               ctx->stream);
     }
-    CK(cudaMemsetAsync(pl.scratch + 64, 0, sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(pl.scratch + kScratchQueue, 0, sizeof(unsigned long long), ctx->stream));
     {
         Timed t(ctx, MGX_K_SOLVE);
-        launch_solve_queue(pl.p.precision, pl.bpl, pl.max_lines, pl.slots, pl.work, pl.n_work, pl.scratch + 64,
-                           ctx->stream);
+        launch_solve_queue(pl.p.precision, pl.bpl, pl.max_lines, pl.slots, pl.work, pl.n_work,
+                           pl.scratch + kScratchQueue, ctx->stream);
     }
     CK(cudaGetLastError());
     return MGX_OK;
+}
+
+// Row width of the padded layout: the narrowest power of two that leaves at
+// most 2 % of the traced points to the tail pass, within the memory budget
+// for the rows (else the widest that fits).
+int32_t choose_pad(const unsigned long long *tot, int64_t total_half, size_t budget_bytes) {
+    const unsigned long long all = tot[kPadCandidates];
+    int best = -1;
+    for (int j = 0; j < kPadCandidates; ++j) {
+        if (size_t(total_half) * (size_t(1) << j) * sizeof(int32_t) > budget_bytes) break;
+        best = j;
+        if (double(tot[j]) <= 0.02 * double(all)) break;
+    }
+    return best < 0 ? 1 : int32_t(1) << best;
 }
 
 bool plan_matches(const BatchPlan &pl, const int32_t *models, int32_t n, const mgx_solve_params *p,
@@ -978,28 +1003,46 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         if (geo[size_t(k)].n_tiles > 65535) return fail(ctx, MGX_ERANGE, "solve_J_batch: too many frequency tiles");
     }
     CK(dalloc(ctx, &pl.lens, size_t(pl.total_half)));
+    CK(dalloc(ctx, &pl.excess, size_t(pl.total_half)));
+    CK(dalloc(ctx, &pl.resume, size_t(pl.total_half)));
     CK(dalloc(ctx, &pl.offs, size_t(pl.total_half + 1)));
     CK(dalloc(ctx, &pl.obase, size_t(n_models)));
     CK(dalloc(ctx, &pl.geo, size_t(n_models)));
     CK(dalloc(ctx, &pl.slots, size_t(n_models)));
     CK(dalloc(ctx, &pl.work, size_t(pl.n_work)));
-    CK(dalloc(ctx, &pl.scratch, 65));
-    CK(cub::DeviceScan::InclusiveSum(nullptr, pl.cub_bytes, pl.lens, pl.offs + 1, pl.total_half, ctx->stream));
+    CK(dalloc(ctx, &pl.scratch, kScratchSize));
+    CK(cub::DeviceScan::InclusiveSum(nullptr, pl.cub_bytes, pl.excess, pl.offs + 1, pl.total_half, ctx->stream));
     CK(cudaMallocAsync(&pl.cub_tmp, pl.cub_bytes ? pl.cub_bytes : 1, ctx->stream));
     CK(cudaMemcpyAsync(pl.geo, geo.data(), geo.size() * sizeof(BatchGeom), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(pl.obase, obase.data(), obase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-    // plan the arena: counts, offsets, total (the only host synchronisation)
-    mgx_status s = enqueue_batch_count(ctx, pl, ms);
-    if (s != MGX_OK) return s;
-    int64_t total = 0;
-    CK(cudaMemcpyAsync(&total, pl.offs + pl.total_half, sizeof total, cudaMemcpyDeviceToHost, ctx->stream));
-    s = sync_status(ctx);
+    // plan the layout from the half-ray lengths (the only host synchronisation)
+    if (flags & MGX_BATCH_RAYS)
+        for (Model *m : ms) enqueue_rays(ctx, *m);
+    {
+        int64_t hb = 0;
+        for (Model *m : ms) {
+            launch_trace_count(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.lens + hb, ctx->d_status, nullptr,
+                               ctx->stream);
+            hb += int64_t(m->n) * m->npairs * 2;
+        }
+    }
+    launch_excess_totals(pl.lens, pl.total_half, pl.scratch + kScratchTotals, ctx->stream);
+    unsigned long long tot[kPadCandidates + 1] = {};
+    CK(cudaMemcpyAsync(tot, pl.scratch + kScratchTotals, sizeof tot, cudaMemcpyDeviceToHost, ctx->stream));
+    mgx_status s = sync_status(ctx);
     if (s != MGX_OK) {
         free_plan(ctx, pl);
         return s;
     }
-    pl.arena_cap = total;
-    CK(dalloc(ctx, &pl.arena, size_t(total)));
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    pl.pad = choose_pad(tot, pl.total_half, std::min(ctx->arena_budget, free_b / 3));
+    int j = 0;
+    while ((int32_t(1) << j) < pl.pad) ++j;
+    pl.tail_cap = int64_t(tot[j]);
+    pl.total_points = int64_t(tot[kPadCandidates]);
+    CK(dalloc(ctx, &pl.rows, size_t(pl.total_half) * size_t(pl.pad)));
+    CK(dalloc(ctx, &pl.tail, size_t(std::max<int64_t>(pl.tail_cap, 1))));
     std::vector<BatchSlot> slots(static_cast<size_t>(n_models));
     for (int32_t k = 0; k < n_models; ++k) {
         Model &m = *ms[size_t(k)];
@@ -1016,16 +1059,19 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         a.n_tiles = geo[size_t(k)].n_tiles;
         a.offs = pl.offs + geo[size_t(k)].half_base;
         a.base = 0;
-        a.idx = pl.arena;
+        a.idx = pl.rows + geo[size_t(k)].half_base * pl.pad;
+        a.pad = pl.pad;
+        a.lens = pl.lens + geo[size_t(k)].half_base;
+        a.tail = pl.tail;
         a.J = J_out[k];
         a.status = ctx->d_status;
         a.counters = ctx->prof ? ctx->d_counters : nullptr;
         fill_pair_weights(a);
         ctx->solves += int64_t(m.n) * m.npairs * int64_t(m.L) * m.F;
     }
-    ctx->trace_points += total;
+    ctx->trace_points += pl.total_points;
     CK(cudaMemcpyAsync(pl.slots, slots.data(), slots.size() * sizeof(BatchSlot), cudaMemcpyHostToDevice, ctx->stream));
-    s = enqueue_batch_solve(ctx, pl, ms);
+    s = enqueue_batch_step(ctx, pl, ms);
     if (s != MGX_OK) {
         free_plan(ctx, pl);
         return s;
@@ -1051,8 +1097,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         mgx_status s2 = MGX_ECUDA;
         cudaGraph_t gr = nullptr;
         if (ce == cudaSuccess) {
-            const mgx_status s1 = enqueue_batch_count(ctx, pl, ms);
-            s2 = s1 == MGX_OK ? enqueue_batch_solve(ctx, pl, ms) : s1;
+            s2 = enqueue_batch_step(ctx, pl, ms);
             ce = cudaStreamEndCapture(ctx->stream, &gr);
         }
         ctx->stream = user;

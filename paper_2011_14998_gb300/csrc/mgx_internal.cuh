@@ -67,9 +67,16 @@ struct SolveArgs {
     double dtau_max, dv_max, I_bdy;
     int32_t o_begin, o_end;   // origins of this chunk
     int32_t n_tiles;          // frequency tiles per origin (32 x bins-per-lane bins each)
-    const int64_t *offs;      // [2 npairs (o_end - o_begin) + 1] arena offsets (absolute)
+    // Traced lists.  Packed (pad == 0): the ids of half-ray h are
+    // idx[offs[h] - base .. offs[h+1] - base).  Padded (pad > 0): its length is
+    // lens[h], entries k < pad are idx[h pad + k] and entries k >= pad are
+    // tail[offs[h] - base + k - pad].
+    const int64_t *offs;      // [2 npairs (o_end - o_begin) + 1] arena (or tail) offsets (absolute)
     int64_t base;             // offs[first half-ray of the chunk]
-    const int32_t *idx;       // arena point ids (relative to base)
+    const int32_t *idx;       // arena point ids (relative to base), or the padded rows
+    int32_t pad = 0;
+    const int64_t *lens = nullptr;  // padded: half-ray lengths
+    const int32_t *tail = nullptr;  // padded: entries beyond the row
     double *J;                // [n][L*F]
     int *status;
     unsigned long long *counters;  // nullable: [0] elimination updates, [1] optics samples,
@@ -111,6 +118,14 @@ void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
                        const int64_t *offs, int64_t base, int64_t cap, int32_t *idx, double *Z, double *delta,
                        int *status, cudaStream_t st);
+// padded layout (see k_trace.cu): rows [n_half][pad], lengths, excess over
+// pad, walk state after the row for the half-rays longer than it
+void launch_trace_pad(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
+                      int64_t *lens, int64_t *excess, int4 *resume, int32_t *rows, int *status,
+                      unsigned long long *counters, cudaStream_t st);
+void launch_trace_tail(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
+                       const int64_t *lens, const int4 *resume, const int64_t *offs, int64_t base, int64_t cap,
+                       int32_t *tail, int *status, cudaStream_t st);
 
 // One model of a batched solve (device-resident descriptor).
 struct BatchSlot {
@@ -129,8 +144,13 @@ struct BatchGeom {
 };
 
 // ---- batched work list (k_batch.cu); scratch64 holds 64 counters
+// Work list from the half-ray lengths lens (all models' half-rays, in order).
 void launch_batch_worklist(const BatchGeom *geo, const int64_t *origin_base, int32_t n_models, int64_t n_origins,
-                           const int64_t *offs, unsigned long long *scratch64, uint2 *work, cudaStream_t st);
+                           const int64_t *lens, unsigned long long *scratch64, uint2 *work, cudaStream_t st);
+// Row widths 2^j (j < kPadCandidates) considered for the padded layout:
+// out[j] = sum over half-rays of max(0, len - 2^j), out[kPadCandidates] = sum of len.
+constexpr int kPadCandidates = 11;
+void launch_excess_totals(const int64_t *lens, int64_t n, unsigned long long *out, cudaStream_t st);
 
 // ---- formal solution (k_solve.cu)
 // frequency bins per lane of the solve kernel; a chunk has
