@@ -303,7 +303,8 @@ typedef struct {
     int32_t decide32; /* take the two integer decisions in single precision, as
                          the single-precision form of the solver does: the
                          velocity-sample count as ceil(|d delta| / limit) and
-                         Eq. 2's n_inter as ceil((chi_max ds) fl32(1/dtau_max));
+                         Eq. 2's n_inter as 1 unless chi_max > dtau_max / ds,
+                         else ceil((chi_max ds) fl32(1/dtau_max));
                          everything else stays double */
 } orc_params;
 
@@ -532,8 +533,16 @@ int64_t orc_subdivide(int64_t mv, const double *s, const double *chi, const doub
     for (int64_t i = 0; i + 1 < mv; ++i) {
         const double ds = s[i + 1] - s[i];
         const double cmax = fmax(chi[i], chi[i + 1]);
-        int64_t ni = decide32 ? (int64_t)ceilf(((float)cmax * (float)ds) * (float)(1.0 / dtau_max))
-                              : (int64_t)ceil(cmax * ds / dtau_max);
+        /* Eq. 2.  In single precision the test "more than one part" is the
+         * equivalent inequality chi_max > dtau_max / ds, and the count is
+         * formed only when it holds. */
+        int64_t ni = 1;
+        if (decide32) {
+            const float cm = (float)cmax, dsf = (float)ds, dtm = (float)dtau_max;
+            if (cm > dtm / dsf) ni = (int64_t)ceilf((cm * dsf) * (float)(1.0 / dtau_max));
+        } else {
+            ni = (int64_t)ceil(cmax * ds / dtau_max);
+        }
         if (ni < 1) ni = 1;
         if (M + ni > max_pts) return -1;
         const double h = ds / (double)ni;

@@ -186,18 +186,31 @@ __device__ __forceinline__ void row(Sweep<R> &w, R chi, R eta, R dt) {
 // of the lane: line optics, Eq. 2 sub-intervals with linear chi and eta,
 // elimination rows.  When no bin of the warp needs sub-intervals (the common
 // case) the rows run as straight-line code, so the bins' chains interleave.
+//
+// Single precision decides "more than one sub-interval" as chi_max > thr with
+// thr = fl32(dtau_max / hs) (the same inequality as Eq. 2's ceiling exceeding
+// one), on the lane's running maximum of chi over its bins (cmax: the previous
+// sample's, updated here), and only then forms the ceiling; double precision
+// evaluates Eq. 2 as written.
 template <typename R, int NL, int BPL>
-__device__ __forceinline__ void sample_step(const Sample<R, NL> &q, R hs, R dtau_max, R inv_dtau_max,
-                                            const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
-                                            int *status, unsigned &n_extra) {
+__device__ __forceinline__ void sample_step(const Sample<R, NL> &q, R hs, R thr, R &cmax, R dtau_max,
+                                            R inv_dtau_max, const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL],
+                                            Sweep<R> (&w)[BPL], int *status, unsigned &n_extra) {
     const R rdv = Ar<R>::rcp(q.dv);
-    R chi_q[BPL], eta_q[BPL], x[BPL];
-    bool split = false;
+    R chi_q[BPL], eta_q[BPL];
 #pragma unroll
-    for (int i = 0; i < BPL; ++i) {
-        optics<R, NL>(q, rdv, f[i], chi_q[i], eta_q[i]);
-        x[i] = Ar<R>::ratio(fmax(w[i].chi, chi_q[i]), hs, dtau_max, inv_dtau_max);  // Eq. 2 before the ceiling
-        split |= x[i] > R(1);
+    for (int i = 0; i < BPL; ++i) optics<R, NL>(q, rdv, f[i], chi_q[i], eta_q[i]);
+    bool split = false;
+    if constexpr (sizeof(R) == 4) {
+        R cq = chi_q[0];
+#pragma unroll
+        for (int i = 1; i < BPL; ++i) cq = fmax(cq, chi_q[i]);
+        split = fmax(cmax, cq) > thr;
+        cmax = cq;
+    } else {
+#pragma unroll
+        for (int i = 0; i < BPL; ++i)
+            split |= Ar<R>::ratio(fmax(w[i].chi, chi_q[i]), hs, dtau_max, inv_dtau_max) > R(1);
     }
     if (!__any_sync(0xffffffffu, split)) {
         const R hh = hs * R(0.5);
@@ -211,9 +224,13 @@ __device__ __forceinline__ void sample_step(const Sample<R, NL> &q, R hs, R dtau
     }
 #pragma unroll
     for (int i = 0; i < BPL; ++i) {
-        const R nr = ceil(x[i]);
-        int ni = nr <= R(1) ? 1 : int(fmin(nr, R(kMaxSubdiv)));
-        if (nr > R(kMaxSubdiv)) dev_fail(status, kDevSubdivLimit);
+        const R cm = fmax(w[i].chi, chi_q[i]);
+        int ni = 1;
+        if (sizeof(R) == 8 || cm > thr) {
+            const R nr = ceil(Ar<R>::ratio(cm, hs, dtau_max, inv_dtau_max));  // Eq. 2
+            ni = nr <= R(1) ? 1 : int(fmin(nr, R(kMaxSubdiv)));
+            if (nr > R(kMaxSubdiv)) dev_fail(status, kDevSubdivLimit);
+        }
         const R rni = R(1) / R(ni);
         const R hh = hs * rni * R(0.5);
         const R c0 = w[i].chi, e0 = w[i].eta;
@@ -255,13 +272,14 @@ __device__ __forceinline__ int velocity_samples(R da, R wa, R db, R wb, R dv_max
 // loop with a select: the interpolation increments stay out of the common
 // one-sample path.)
 template <typename R, int NL, int BPL>
-__device__ __forceinline__ void interval(Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds, int nv,
-                                         const SolveArgs &a, R dtau_max, R inv_dtau_max,
+__device__ __forceinline__ void interval(Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds, R thr, int nv,
+                                         R &cmax, const SolveArgs &a, R dtau_max, R inv_dtau_max,
                                          const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
                                          unsigned &n_extra) {
     if (nv > 1) {
         const R rnv = Ar<R>::rcp(R(nv));
         const R hs = ds * rnv;
+        const R ths = thr * R(nv);  // dtau_max / hs
         Sample<R, NL> st;
         st.delta = (nxt.delta - cur.delta) * rnv;
         st.dv = (nxt.dv - cur.dv) * rnv;
@@ -282,11 +300,11 @@ __device__ __forceinline__ void interval(Sample<R, NL> &cur, const Sample<R, NL>
                 cur.chi0[l] += st.chi0[l];
                 cur.eta0[l] += st.eta0[l];
             }
-            sample_step<R, NL, BPL>(cur, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+            sample_step<R, NL, BPL>(cur, hs, ths, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
         }
-        sample_step<R, NL, BPL>(nxt, hs, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+        sample_step<R, NL, BPL>(nxt, hs, ths, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
     } else {
-        sample_step<R, NL, BPL>(nxt, ds, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+        sample_step<R, NL, BPL>(nxt, ds, thr, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
     }
     cur = nxt;
 }
@@ -330,7 +348,7 @@ __device__ __forceinline__ HalfList half_list(const SolveArgs &a, int64_t h) {
 // Per-warp staging area of 32 line points in shared memory.
 template <typename R, int NL>
 struct Stage {
-    R delta[32], dv[32], chic[32], etac[32], ds[32];
+    R delta[32], dv[32], chic[32], etac[32], ds[32], thr[32];
     R chi0[NL][32], eta0[NL][32];
     int nv[32];
 };
@@ -361,6 +379,7 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
     const R dtau_max = R(a.dtau_max), inv_dtau_max = R(1.0 / a.dtau_max), dv_max = R(a.dv_max);
     const R d0 = R(e0), d1 = R(e1), d2 = R(e2);
     Sample<R, NL> cur, nxt;
+    R cmax = R(0);  // running maximum of chi over the lane's bins at the current sample
     double zcarry = 0.0;          // Z of the entry just beyond the current chunk (farther)
     R dcarry = R(0), wcarry = R(1);  // its projected velocity and width
     for (int32_t kb = cnt - 1; kb >= 0; kb -= 32) {
@@ -397,6 +416,7 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
                 sg.eta0[l][lane] = st.eta0[l];
             }
             sg.ds[lane] = R(zf - zk);  // distance increment, differenced in double
+            sg.thr[lane] = dtau_max / sg.ds[lane];  // Eq. 2 threshold on chi (single precision)
             sg.nv[lane] = far_end ? 0 : velocity_samples<R>(df, wf, st.delta, st.dv, dv_max, a.status);
         }
         __syncwarp();
@@ -416,10 +436,14 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
                 const R rdv = Ar<R>::rcp(cur.dv);
 #pragma unroll
                 for (int i = 0; i < BPL; ++i) optics<R, NL>(cur, rdv, f[i], w[i].chi, w[i].eta);
+                cmax = w[0].chi;
+#pragma unroll
+                for (int i = 1; i < BPL; ++i) cmax = fmax(cmax, w[i].chi);
                 continue;
             }
             n_smp += unsigned(nv);
-            interval<R, NL, BPL>(cur, nxt, sg.ds[j], nv, a, dtau_max, inv_dtau_max, f, act, w, n_extra);
+            interval<R, NL, BPL>(cur, nxt, sg.ds[j], sg.thr[j], nv, cmax, a, dtau_max, inv_dtau_max, f, act, w,
+                                 n_extra);
         }
     }
     Sample<R, NL> origin;
@@ -427,7 +451,9 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
     origin.delta = R(0);
     const int nv = velocity_samples<R>(cur.delta, cur.dv, origin.delta, origin.dv, dv_max, a.status);
     n_smp += unsigned(nv);
-    interval<R, NL, BPL>(cur, origin, R(zcarry), nv, a, dtau_max, inv_dtau_max, f, act, w, n_extra);
+    const R ds_o = R(zcarry);
+    interval<R, NL, BPL>(cur, origin, ds_o, dtau_max / ds_o, nv, cmax, a, dtau_max, inv_dtau_max, f, act, w,
+                         n_extra);
 }
 
 // CTAs of 128 threads; the minimum resident CTAs per SM caps the registers
