@@ -158,14 +158,94 @@ __device__ Step step_contenders(const DevMesh &m, int32_t c, float4 oh, float Xo
     return Step{best, zbest};
 }
 
+// State of one lane's current walk.
+struct Walk {
+    int64_t h, w;          // half-ray, write base of its entries
+    double d0, d1, d2;     // direction (double)
+    float4 oh;             // origin position (float) and id
+    float f0, f1, f2, Xo;  // direction (float), |x_o|_1
+    float zc32, ezc;       // Z of the current point (float) and its bound
+    int32_t o, c, k, expect;
+};
+
+// Set up the walk of half-ray h; false when h needs no walk (MODE 4: no
+// tail) or its output range is inconsistent (reported through status).
+template <int MODE>
+__device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, int32_t o_begin, int64_t h,
+                                           const int64_t *__restrict__ lens, const int64_t *__restrict__ offs,
+                                           int64_t base, int64_t cap, int32_t pad, const int4 *__restrict__ resume,
+                                           int *status, Walk &wk) {
+    int64_t expect_len = 0;
+    if (MODE == 4) {  // only the half-rays longer than their row
+        expect_len = lens[h];
+        if (expect_len <= pad) return false;
+    }
+    const int64_t pr = h >> 1;
+    wk.h = h;
+    wk.o = o_begin + int32_t(pr / R.npairs);
+    const uint32_t ray = R.rays[int64_t(wk.o) * R.npairs + (pr % R.npairs)];
+    const double *r = R.dir + 3 * (level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
+    wk.d0 = r[0];
+    wk.d1 = r[1];
+    wk.d2 = r[2];
+    if ((h & 1) == 0) {  // backward half: exact negation of the pair direction
+        wk.d0 = -wk.d0;
+        wk.d1 = -wk.d1;
+        wk.d2 = -wk.d2;
+    }
+    wk.f0 = __double2float_rn(wk.d0);
+    wk.f1 = __double2float_rn(wk.d1);
+    wk.f2 = __double2float_rn(wk.d2);
+    wk.oh = m.phi[wk.o];
+    wk.Xo = fabsf(wk.oh.x) + fabsf(wk.oh.y) + fabsf(wk.oh.z);
+    wk.w = 0;
+    wk.expect = 0;
+    if (MODE == 1 || MODE == 2) {
+        wk.w = offs[h] - base;
+        wk.expect = int32_t(offs[h + 1] - offs[h]);
+        if (wk.w < 0 || offs[h + 1] - base > cap) {
+            dev_fail(status, kDevArenaOverflow);
+            return false;
+        }
+    } else if (MODE == 3) {
+        wk.w = h * int64_t(pad);
+    } else if (MODE == 4) {
+        wk.w = offs[h] - base - pad;  // entry k >= pad goes to w + k
+        wk.expect = int32_t(expect_len);
+        if (offs[h] - base < 0 || offs[h + 1] - base > cap || offs[h + 1] - offs[h] != expect_len - pad) {
+            dev_fail(status, kDevArenaOverflow);
+            return false;
+        }
+    }
+    wk.c = wk.o;
+    wk.k = 0;
+    wk.zc32 = 0.0f;  // Z of the origin is exactly 0
+    wk.ezc = 0.0f;
+    if (MODE == 4) {  // resume after the row's last entry
+        const int4 rs = resume[h];
+        wk.c = rs.x;
+        wk.zc32 = __int_as_float(rs.y);
+        wk.ezc = __int_as_float(rs.z);
+        wk.k = pad;
+        if (wk.c < 0 || wk.c >= m.n) {
+            dev_fail(status, kDevTraceMismatch);
+            return false;
+        }
+    }
+    return true;
+}
+
 // MODE 0: count the points of each half-ray; MODE 1: write their ids;
 // MODE 2: write ids, exact double Z and (optionally) projected velocities;
 // MODE 3: padded pass (ids k < pad to row h, length to lens[h], excess over
 // the row to excess[h], the walk state after entry pad - 1 to resume[h] when
 // the half-ray is longer); MODE 4: tail pass (ids k >= pad of the half-rays
 // longer than the row, at offs[h] - base + k - pad, resumed from resume[h]).
-// Each thread walks half-rays h = tid, tid + T, ... (T = all threads), which
-// evens out the very different lengths of the rays a warp's lanes trace.
+//
+// Lane t walks half-rays t, t + T, t + 2T, ... (T = all threads).  The loop
+// advances every lane by one step per iteration, and a lane whose walk ends
+// sets up its next half-ray inside the iteration, so the lanes of a warp stay
+// busy although the half-rays they trace differ widely in length.
 template <int MODE>
 __global__ void __launch_bounds__(128)
 k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restrict__ lens,
@@ -175,118 +255,83 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         int4 *__restrict__ resume) {
     const int64_t T = int64_t(gridDim.x) * blockDim.x;
     unsigned long long n_steps = 0, n_exact = 0;
-    for (int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; h < n_half; h += T) {
-        int64_t expect_len = 0;
-        if (MODE == 4) {  // only the half-rays longer than their row
-            expect_len = lens[h];
-            if (expect_len <= pad) continue;
+    Walk wk;
+    int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    bool live = false;
+    for (; h < n_half && !live; h += T) live = begin_walk<MODE>(m, R, o_begin, h, lens, offs, base, cap, pad, resume,
+                                                                status, wk);
+    while (live) {
+        FStep s = step_screen(m, wk.c, wk.oh, wk.Xo, wk.f0, wk.f1, wk.f2, wk.zc32, wk.ezc);
+        ++n_steps;
+        double zexact = 0.0;
+        bool have_exact = false;
+        if (s.next == -2) {  // undecided in single precision: its contenders in double
+            const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
+            const double zc = (wk.c == wk.o) ? 0.0 : exact_Z(m, wk.c, xo, yo, zo, wk.d0, wk.d1, wk.d2);
+            const Step x = step_contenders(m, wk.c, wk.oh, wk.Xo, wk.f0, wk.f1, wk.f2, wk.zc32, wk.ezc, s.z32, zc,
+                                           xo, yo, zo, wk.d0, wk.d1, wk.d2);
+            s.next = x.next;
+            zexact = x.Z;
+            ++n_exact;
+            have_exact = true;
+            s.z32 = __double2float_rn(x.Z);
+            s.ez = 2.0f * kU * fabsf(s.z32);
         }
-        const int64_t pr = h >> 1;
-        const int32_t o = o_begin + int32_t(pr / R.npairs);
-        const uint32_t ray = R.rays[int64_t(o) * R.npairs + (pr % R.npairs)];
-        const double *r = R.dir + 3 * (level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
-        double d0 = r[0], d1 = r[1], d2 = r[2];
-        if ((h & 1) == 0) {  // backward half: exact negation of the pair direction
-            d0 = -d0;
-            d1 = -d1;
-            d2 = -d2;
-        }
-        const float f0 = __double2float_rn(d0), f1 = __double2float_rn(d1), f2 = __double2float_rn(d2);
-        const float4 oh = m.phi[o];
-        const float Xo = fabsf(oh.x) + fabsf(oh.y) + fabsf(oh.z);
-        int64_t w = 0;
-        int32_t expect = 0;
-        if (MODE == 1 || MODE == 2) {
-            w = offs[h] - base;
-            expect = int32_t(offs[h + 1] - offs[h]);
-            if (w < 0 || offs[h + 1] - base > cap) {
-                dev_fail(status, kDevArenaOverflow);
-                continue;
-            }
-        } else if (MODE == 3) {
-            w = h * int64_t(pad);
-        } else if (MODE == 4) {
-            w = offs[h] - base - pad;  // entry k >= pad goes to w + k
-            expect = int32_t(expect_len);
-            if (offs[h] - base < 0 || offs[h + 1] - base > cap || offs[h + 1] - offs[h] != expect_len - pad) {
-                dev_fail(status, kDevArenaOverflow);
-                continue;
-            }
-        }
-        int32_t c = o, k = 0;
-        float zc32 = 0.0f, ezc = 0.0f;  // Z of the origin is exactly 0
-        if (MODE == 4) {  // resume after the row's last entry
-            const int4 r = resume[h];
-            c = r.x;
-            zc32 = __int_as_float(r.y);
-            ezc = __int_as_float(r.z);
-            k = pad;
-            if (c < 0 || c >= m.n) {
-                dev_fail(status, kDevTraceMismatch);
-                continue;
-            }
-        }
-        for (;;) {
-            FStep s = step_screen(m, c, oh, Xo, f0, f1, f2, zc32, ezc);
-            ++n_steps;
-            double zexact = 0.0;
-            bool have_exact = false;
-            if (s.next == -2) {  // undecided in single precision: its contenders in double
-                const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
-                const double zc = (c == o) ? 0.0 : exact_Z(m, c, xo, yo, zo, d0, d1, d2);
-                const Step x = step_contenders(m, c, oh, Xo, f0, f1, f2, zc32, ezc, s.z32, zc, xo, yo, zo, d0, d1,
-                                               d2);
-                s.next = x.next;
-                zexact = x.Z;
-                ++n_exact;
-                have_exact = true;
-                s.z32 = __double2float_rn(x.Z);
-                s.ez = 2.0f * kU * fabsf(s.z32);
-            }
-            if (s.next < 0) break;
+        bool ended = s.next < 0, failed = false;
+        if (!ended) {
+            const int32_t k = wk.k;
             if (MODE == 3) {
-                if (k < pad) idx_out[w + k] = s.next;
+                if (k < pad) idx_out[wk.w + k] = s.next;
             } else if (MODE == 4) {
-                if (k >= expect) {
-                    dev_fail(status, kDevTraceMismatch);
-                    return;
-                }
-                if (k >= pad) idx_out[w + k] = s.next;
+                if (k >= wk.expect) failed = true;
+                else idx_out[wk.w + k] = s.next;  // k >= pad here
             } else if (MODE > 0) {
-                if (k >= expect) {
-                    dev_fail(status, kDevTraceMismatch);
-                    return;
-                }
-                idx_out[w + k] = s.next;
-                if (MODE == 2) {
-                    const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
-                    Z_out[w + k] = have_exact ? zexact : exact_Z(m, s.next, xo, yo, zo, d0, d1, d2);
-                    if (delta_out) {
-                        const double ux = __dsub_rn(m.vx[s.next], m.vx[o]);
-                        const double uy = __dsub_rn(m.vy[s.next], m.vy[o]);
-                        const double uz = __dsub_rn(m.vz[s.next], m.vz[o]);
-                        delta_out[w + k] =
-                            __dadd_rn(__dadd_rn(__dmul_rn(ux, d0), __dmul_rn(uy, d1)), __dmul_rn(uz, d2));
+                if (k >= wk.expect) {
+                    failed = true;
+                } else {
+                    idx_out[wk.w + k] = s.next;
+                    if (MODE == 2) {
+                        const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
+                        Z_out[wk.w + k] = have_exact ? zexact : exact_Z(m, s.next, xo, yo, zo, wk.d0, wk.d1, wk.d2);
+                        if (delta_out) {
+                            const double ux = __dsub_rn(m.vx[s.next], m.vx[wk.o]);
+                            const double uy = __dsub_rn(m.vy[s.next], m.vy[wk.o]);
+                            const double uz = __dsub_rn(m.vz[s.next], m.vz[wk.o]);
+                            delta_out[wk.w + k] =
+                                __dadd_rn(__dadd_rn(__dmul_rn(ux, wk.d0), __dmul_rn(uy, wk.d1)), __dmul_rn(uz, wk.d2));
+                        }
                     }
                 }
             }
-            ++k;
-            c = s.next;
-            zc32 = s.z32;
-            ezc = s.ez;
-            if (MODE == 3 && k == pad) resume[h] = make_int4(c, __float_as_int(zc32), __float_as_int(ezc), 0);
-            if (k > m.n) {  // Z increases strictly, so this cannot happen
-                dev_fail(status, kDevTraceGuard);
-                break;
+            if (failed) {
+                dev_fail(status, kDevTraceMismatch);
+                ended = true;
+            } else {
+                wk.k = k + 1;
+                wk.c = s.next;
+                wk.zc32 = s.z32;
+                wk.ezc = s.ez;
+                if (MODE == 3 && wk.k == pad)
+                    resume[wk.h] = make_int4(wk.c, __float_as_int(wk.zc32), __float_as_int(wk.ezc), 0);
+                if (wk.k > m.n) {  // Z increases strictly, so this cannot happen
+                    dev_fail(status, kDevTraceGuard);
+                    ended = true;
+                    failed = true;
+                }
             }
         }
-        if (MODE == 0) {
-            lens[h] = k;
-        } else if (MODE == 3) {
-            lens[h] = k;
-            excess[h] = k > pad ? k - pad : 0;
-        } else if (k != expect) {
-            dev_fail(status, kDevTraceMismatch);
+        if (ended) {
+            if (MODE == 0) {
+                lens[wk.h] = wk.k;
+            } else if (MODE == 3) {
+                lens[wk.h] = wk.k;
+                excess[wk.h] = wk.k > pad ? wk.k - pad : 0;
+            } else if (!failed && wk.k != wk.expect) {
+                dev_fail(status, kDevTraceMismatch);
+            }
+            live = false;
+            for (; h < n_half && !live; h += T)
+                live = begin_walk<MODE>(m, R, o_begin, h, lens, offs, base, cap, pad, resume, status, wk);
         }
     }
     if (counters) {
