@@ -242,6 +242,11 @@ def run_mgx(args):
             ctx.profile(False)
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3, prof
 
+    # launch parameters of the batched step from the autotuner (untimed; results do not depend on them)
+    trials, _ = ctx.autotune([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32],
+                             flags=batched, reps=3)
+    tuning = ctx.tuning()
+
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -337,27 +342,32 @@ def run_mgx(args):
     arena_bytes = prof32["trace_points"] * 12 * ((NB + 31) // 32) + n * NB * 8  # point lists per tile + J
     hbm_gbs = arena_bytes / max(1, prof32["launches"]["solve"]) / (ms_solve * 1e-3) / 1e9
     step_ms = {k: v / kb for k, v in prof32["ms"].items()}
-    launches = args.steps * sum(v for k, v in prof32["launches"].items() if k != "scan") // kb
+    # own kernels per step: ray sets, padded trace, tail trace, the three work-list kernels, the solve
+    # (the scan is CUB's)
+    lp = prof32["launches"]
+    launches = args.steps * (lp["rays"] + lp["trace_count"] + lp["trace_emit"] + 3 * lp["other"] + lp["solve"]) // kb
+    traffic = solve_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t32 / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD, parallelism=f"replicas x{ws}", l2="flushed between timed steps (256 MiB write)",
-                       step="one CUDA-graph replay: ray sets, trace count, scan, work list, trace emit, "
-                            "persistent length-binned solve"),
+                       step="one CUDA-graph replay: ray sets, padded trace, tail offsets (scan), tail trace, "
+                            "length-binned work list, persistent solve",
+                       tuning=tuning, autotune_trials=trials),
         "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
                        "speedup_fp32_over_fp64": value / ws / value64},
         "accuracy": {"fp32_vs_fp64_max_rel": float(rel32_64.max()),
                      "fp32_vs_fp64_p99_rel": float(np.quantile(rel32_64, 0.99)),
                      "oracle_sample": acc_oracle},
         "kernel_ms_per_step": step_ms,
-        "kernel_breakdown_step_ms": 1e3 * tb / kb,
+        "eager_step_ms": 1e3 * tb / kb,  # same step without the graph, re-planned each call
         "work_per_step": {"solves": solves_per_step, "trace_points": prof32["trace_points"] // kb,
                           "updates": prof32["updates"] // kb, "samples": prof32["samples"] // kb,
                           "trace_steps": prof32["trace_steps"] // kb,
                           "trace_steps_redone_fp64": prof32["trace_exact_steps"] // kb},
         "roofline": {"kernel": "k_solve_queue<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",
                      "hbm_algorithmic_gbs": hbm_gbs},
         "cpu_baseline": cpu,
@@ -370,6 +380,26 @@ def run_mgx(args):
     if ws > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
+
+
+SOLVE_PROFILE = os.path.join(ROOT, "profiles", "k_solve_queue_wind50k.md")
+
+
+def solve_traffic():
+    """DRAM bytes per launch of the solve kernel from its committed ncu summary,
+    or None when the kernel source has changed since the counters were taken
+    (the summary records the SHA-256 of k_solve.cu it was measured with)."""
+    import hashlib
+
+    try:
+        kv = dict(l.split(":", 1) for l in open(SOLVE_PROFILE).read().splitlines() if l.startswith("dram_") or
+                  l.startswith("k_solve_sha256"))
+        src = open(os.path.join(ROOT, "paper_2011_14998_gb300", "csrc", "k_solve.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest() != kv["k_solve_sha256"].strip():
+            return None
+        return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 def run_profile_case(args):

@@ -184,24 +184,64 @@ enum {
 };
 
 /* Mean intensity of several models in one launch (the batched form of
- * mgx_solve_J, same results).  All models' half-rays are traced and prefix-
- * summed together; each (model, origin, frequency tile) item's cost is the
- * number of points on its traced lines, items are binned by log2 of that cost
- * and laid out longest bin first, and one persistent kernel (one warp per item,
- * items taken from a global counter) solves them all, so very uneven ray
- * lengths and model sizes share the GPU without a long tail.
+ * mgx_solve_J, same results).  All models' half-rays are traced together into
+ * fixed-width rows (the width chosen from the length distribution when the
+ * call plans) plus a packed overflow for the longer ones; each (model, origin,
+ * frequency tile) item's cost is the number of points on its traced lines,
+ * items are binned by log2 of that cost and laid out longest bin first, and
+ * one persistent kernel (one warp per item, items taken from a global counter)
+ * solves them all, so very uneven ray lengths and model sizes share the GPU
+ * without a long tail.  Launch parameters come from the context's tuning
+ * (mgx_set_tuning / mgx_autotune).
  *   models  [n_models] distinct model handles (1..65535), lines and rays set
  *   J_out   [n_models] device pointers, J_out[k] of size [n_k][n_lines_k*n_freq_k]
  *   flags   MGX_BATCH_RAYS: the step starts by rebuilding the ray sets;
- *           MGX_BATCH_GRAPH: the first call plans the arena (one host
+ *           MGX_BATCH_GRAPH: the first call plans the layout (one host
  *           synchronisation), runs the step and captures it as a CUDA graph;
- *           later calls with the same models, parameters, outputs and flags
- *           replay the graph without host work.  A replay whose traced lists
- *           no longer fit the planned arena fails with MGX_ERANGE and drops the
- *           plan.  Freeing a model drops the plan.
+ *           later calls with the same models, parameters, outputs, flags and
+ *           tuning replay the graph without host work.  A replay whose traced
+ *           lists no longer fit the planned layout fails with MGX_ERANGE and
+ *           drops the plan.  Freeing a model drops the plan.
  * The call synchronises the stream before returning. */
 mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_models, const mgx_solve_params *params,
                              double *const *J_out, int32_t flags);
+
+/* Launch parameters of the batched solve (no counterpart in the paper).  The
+ * tracer grid and the row width change only the speed of mgx_solve_J_batch;
+ * the bins per lane select a differently compiled single-precision kernel,
+ * whose J may differ from the other's in its rounding (about 1e-8 relative:
+ * the compilers' fused multiply-adds differ), never beyond that. */
+typedef struct {
+    int32_t bins_per_lane;     /* single-precision frequency bins per lane: 0 automatic (2 above 32 bins), 1, 2 */
+    int32_t trace_ctas_per_sm; /* resident tracer CTAs of 128 threads per SM: 0 = 8, else 1..32 (capped at
+                                  what fits) */
+    int32_t tail_permille;     /* row width of the traced lists: the narrowest power of two leaving at most this
+                                  share of the points (per mille) to the overflow pass; 0 = 20, else 1..1000 */
+    int32_t reserved;          /* 0 */
+} mgx_tuning;
+
+/* Set (NULL: reset to automatic) or read the context's tuning; out-of-range
+ * fields give MGX_EINVAL.  Setting it drops a planned batch. */
+mgx_status mgx_set_tuning(mgx_ctx *ctx, const mgx_tuning *tuning);
+mgx_status mgx_get_tuning(mgx_ctx *ctx, mgx_tuning *tuning);
+
+/* One timed candidate of mgx_autotune. */
+typedef struct {
+    mgx_tuning tuning;
+    double step_ms; /* median device time of one step (CUDA events on the context's stream) */
+} mgx_tune_trial;
+
+/* Autotuner of the batched solve: times candidate tunings of
+ * mgx_solve_J_batch(ctx, models, n_models, params, J_out, flags) by coordinate
+ * descent (bins per lane 1/2 in single precision, tracer CTAs per SM 4/6/8,
+ * tail share 5/20/80 per mille), each candidate planned once and then run
+ * `reps` times (1..100), and leaves the fastest as the context's tuning.
+ * J_out receives the solution of the chosen tuning.  trials
+ * [max_trials] (may be NULL) receives the timed candidates in order, *n_trials
+ * their number.  Same argument rules and errors as mgx_solve_J_batch. */
+mgx_status mgx_autotune(mgx_ctx *ctx, const int32_t *models, int32_t n_models, const mgx_solve_params *params,
+                        double *const *J_out, int32_t flags, int32_t reps, mgx_tune_trial *trials,
+                        int32_t max_trials, int32_t *n_trials);
 
 /* Allocation-free variant of mgx_solve_J, for callers that must not allocate
  * device memory during their step: code running while a framework owns every

@@ -27,7 +27,8 @@ ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs
                "mgx_free_model", "mgx_set_lines", "mgx_set_rays", "mgx_get_rays", "mgx_trace",
                "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read",
                "mgx_solve_J_noalloc", "mgx_solve_J_batch", "mgx_mlp_set_params", "mgx_mlp_get_params",
-               "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned")
+               "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned",
+               "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune")
 MGX_MLP_NPARAM = 4801
 MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
@@ -48,6 +49,18 @@ class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("trace_points", C.c_int64),
                 ("solves", C.c_int64), ("updates", C.c_int64), ("samples", C.c_int64),
                 ("trace_steps", C.c_int64), ("trace_exact_steps", C.c_int64)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("bins_per_lane", C.c_int32), ("trace_ctas_per_sm", C.c_int32), ("tail_permille", C.c_int32),
+                ("reserved", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+
+
+class TuneTrial(C.Structure):
+    _fields_ = [("tuning", Tuning), ("step_ms", C.c_double)]
 
 
 _lib = None
@@ -92,6 +105,10 @@ def load_library(path: str = LIB_PATH):
         "mgx_reduce_mesh_learned": (i32, [vp, i32, vp, dbl, vp, C.POINTER(i64)]),
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
+        "mgx_set_tuning": (i32, [vp, C.POINTER(Tuning)]),
+        "mgx_get_tuning": (i32, [vp, C.POINTER(Tuning)]),
+        "mgx_autotune": (i32, [vp, vp, i32, C.POINTER(SolveParams), vp, i32, i32, C.POINTER(TuneTrial), i32,
+                               C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -205,6 +222,29 @@ def mgx_solve_J_batch(ctx, models, params: SolveParams, J_outs, flags: int = 0) 
     ids = np.ascontiguousarray(models, np.int32)
     ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
     _check(ctx, load_library().mgx_solve_J_batch(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags)))
+
+
+def mgx_set_tuning(ctx, tuning: dict | None) -> None:
+    """Set the batched solve's launch parameters (None: automatic; see include/mgx.h)."""
+    t = None if tuning is None else C.byref(Tuning(**{k: int(v) for k, v in tuning.items()}))
+    _check(ctx, load_library().mgx_set_tuning(ctx, t))
+
+
+def mgx_get_tuning(ctx) -> dict:
+    t = Tuning()
+    _check(ctx, load_library().mgx_get_tuning(ctx, C.byref(t)))
+    return t.as_dict()
+
+
+def mgx_autotune(ctx, models, params: SolveParams, J_outs, flags: int = 0, reps: int = 3) -> list[dict]:
+    """Time candidate tunings of the batched solve and keep the fastest; returns the trials."""
+    ids = np.ascontiguousarray(models, np.int32)
+    ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
+    trials = (TuneTrial * 16)()
+    n = C.c_int32(0)
+    _check(ctx, load_library().mgx_autotune(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags), int(reps),
+                                            trials, 16, C.byref(n)))
+    return [dict(trials[i].tuning.as_dict(), step_ms=float(trials[i].step_ms)) for i in range(min(n.value, 16))]
 
 
 def mgx_mlp_set_params(ctx, theta) -> None:
@@ -361,6 +401,24 @@ class Context:
                                 dtype=torch.float64, device=f"cuda:{self.device}") for m in mids]
         mgx_solve_J_batch(self.ptr, list(mids), solve_params(dtau_max, dv_max, I_bdy, precision, True), outs, flags)
         return outs
+
+    def set_tuning(self, tuning: dict | None):
+        mgx_set_tuning(self.ptr, tuning)
+
+    def tuning(self) -> dict:
+        return mgx_get_tuning(self.ptr)
+
+    def autotune(self, mids, precision=MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, outs=None, flags=0,
+                 reps=3):
+        """Pick the batched solve's launch parameters for these models by timing; returns (trials, outs)."""
+        import torch
+
+        if outs is None:
+            outs = [torch.empty((self.models[m]["n"], self.models[m]["L"] * self.models[m]["F"]),
+                                dtype=torch.float64, device=f"cuda:{self.device}") for m in mids]
+        trials = mgx_autotune(self.ptr, list(mids), solve_params(dtau_max, dv_max, I_bdy, precision, True), outs,
+                              flags, reps)
+        return trials, outs
 
     def reduce_mesh(self, mid, f, f_small, f_large, G_thres, seed):
         return mgx_reduce_mesh(self.ptr, mid, f, f_small, f_large, G_thres, seed)

@@ -33,8 +33,6 @@
 //
 // Template R selects the arithmetic: double (plain form) or float (the distance
 // increments come from double Z differences; J is summed in double).
-#include <cstdlib>
-
 #include "mgx_internal.cuh"
 
 namespace mgx {
@@ -608,11 +606,8 @@ void launch_RB(const DevMesh &m, const DevLines &Ln, const DevRays &R_, const So
 
 // Bins per lane of the single-precision kernel: 2 when there are more bins than
 // lanes (the frequency-independent work is then shared by two bins), else 1.
-// MGX_BINS_PER_LANE=1|2 overrides the choice (tuning).
 int solve_bins_per_lane(int precision, int32_t n_bins) {
     if (precision != MGX_FP32) return 1;
-    const char *env = getenv("MGX_BINS_PER_LANE");
-    if (env && (env[0] == '1' || env[0] == '2') && env[1] == 0) return env[0] - '0';
     return n_bins > 32 ? 2 : 1;
 }
 

@@ -158,15 +158,27 @@ __device__ Step step_contenders(const DevMesh &m, int32_t c, float4 oh, float Xo
     return Step{best, zbest};
 }
 
-// State of one lane's current walk.
+// State of one lane's current walk.  It holds the direction in float only
+// (the rounded table entry, negated for a backward half, which equals the
+// rounded negation); the double direction is read from the table on the rare
+// steps that need it, so setting up a walk executes no double-precision
+// operation.
 struct Walk {
     int64_t h, w;          // half-ray, write base of its entries
-    double d0, d1, d2;     // direction (double)
     float4 oh;             // origin position (float) and id
     float f0, f1, f2, Xo;  // direction (float), |x_o|_1
     float zc32, ezc;       // Z of the current point (float) and its bound
     int32_t o, c, k, expect;
+    int32_t pix;           // table index of the pair direction
+    bool back;             // backward half (direction negated)
 };
+
+__device__ __forceinline__ void walk_dir(const DevRays &R, const Walk &wk, double &d0, double &d1, double &d2) {
+    const double *r = R.dir + 3 * int64_t(wk.pix);
+    d0 = wk.back ? -r[0] : r[0];
+    d1 = wk.back ? -r[1] : r[1];
+    d2 = wk.back ? -r[2] : r[2];
+}
 
 // Set up the walk of half-ray h; false when h needs no walk (MODE 4: no
 // tail) or its output range is inconsistent (reported through status).
@@ -184,18 +196,12 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
     wk.h = h;
     wk.o = o_begin + int32_t(pr / R.npairs);
     const uint32_t ray = R.rays[int64_t(wk.o) * R.npairs + (pr % R.npairs)];
-    const double *r = R.dir + 3 * (level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
-    wk.d0 = r[0];
-    wk.d1 = r[1];
-    wk.d2 = r[2];
-    if ((h & 1) == 0) {  // backward half: exact negation of the pair direction
-        wk.d0 = -wk.d0;
-        wk.d1 = -wk.d1;
-        wk.d2 = -wk.d2;
-    }
-    wk.f0 = __double2float_rn(wk.d0);
-    wk.f1 = __double2float_rn(wk.d1);
-    wk.f2 = __double2float_rn(wk.d2);
+    wk.pix = int32_t(level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
+    wk.back = (h & 1) == 0;  // backward half: exact negation of the pair direction
+    const float4 df = R.dirf[wk.pix];
+    wk.f0 = wk.back ? -df.x : df.x;
+    wk.f1 = wk.back ? -df.y : df.y;
+    wk.f2 = wk.back ? -df.z : df.z;
     wk.oh = m.phi[wk.o];
     wk.Xo = fabsf(wk.oh.x) + fabsf(wk.oh.y) + fabsf(wk.oh.z);
     wk.w = 0;
@@ -247,7 +253,7 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
 // sets up its next half-ray inside the iteration, so the lanes of a warp stay
 // busy although the half-rays they trace differ widely in length.
 template <int MODE>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 8)
 k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restrict__ lens,
         const int64_t *__restrict__ offs, int64_t base, int64_t cap, int32_t *__restrict__ idx_out,
         double *__restrict__ Z_out, double *__restrict__ delta_out, int *status,
@@ -267,9 +273,11 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         bool have_exact = false;
         if (s.next == -2) {  // undecided in single precision: its contenders in double
             const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
-            const double zc = (wk.c == wk.o) ? 0.0 : exact_Z(m, wk.c, xo, yo, zo, wk.d0, wk.d1, wk.d2);
+            double d0, d1, d2;
+            walk_dir(R, wk, d0, d1, d2);
+            const double zc = (wk.c == wk.o) ? 0.0 : exact_Z(m, wk.c, xo, yo, zo, d0, d1, d2);
             const Step x = step_contenders(m, wk.c, wk.oh, wk.Xo, wk.f0, wk.f1, wk.f2, wk.zc32, wk.ezc, s.z32, zc,
-                                           xo, yo, zo, wk.d0, wk.d1, wk.d2);
+                                           xo, yo, zo, d0, d1, d2);
             s.next = x.next;
             zexact = x.Z;
             ++n_exact;
@@ -292,13 +300,15 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
                     idx_out[wk.w + k] = s.next;
                     if (MODE == 2) {
                         const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
-                        Z_out[wk.w + k] = have_exact ? zexact : exact_Z(m, s.next, xo, yo, zo, wk.d0, wk.d1, wk.d2);
+                        double d0, d1, d2;
+                        walk_dir(R, wk, d0, d1, d2);
+                        Z_out[wk.w + k] = have_exact ? zexact : exact_Z(m, s.next, xo, yo, zo, d0, d1, d2);
                         if (delta_out) {
                             const double ux = __dsub_rn(m.vx[s.next], m.vx[wk.o]);
                             const double uy = __dsub_rn(m.vy[s.next], m.vy[wk.o]);
                             const double uz = __dsub_rn(m.vz[s.next], m.vz[wk.o]);
                             delta_out[wk.w + k] =
-                                __dadd_rn(__dadd_rn(__dmul_rn(ux, wk.d0), __dmul_rn(uy, wk.d1)), __dmul_rn(uz, wk.d2));
+                                __dadd_rn(__dadd_rn(__dmul_rn(ux, d0), __dmul_rn(uy, d1)), __dmul_rn(uz, d2));
                         }
                     }
                 }
@@ -340,11 +350,19 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
     }
 }
 
-unsigned trace_grid(int64_t n_half) {
-    int dev = 0, sms = 152;
+// Grid of the strided walk: ctas_per_sm CTAs of 128 threads per SM (8 when
+// not positive), at most as many as can be resident at once (so the whole
+// grid is one wave and every lane's share of half-rays runs concurrently),
+// fewer when there are fewer half-rays.
+template <int MODE>
+unsigned trace_grid(int64_t n_half, int ctas_per_sm = 0) {
+    int dev = 0, sms = 152, fit = 8;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_trace<MODE>, 128, 0) != cudaSuccess || fit < 1) fit = 1;
+    int per = ctas_per_sm > 0 ? ctas_per_sm : 8;
+    if (per > fit) per = fit;
     const int64_t want = (n_half + 127) / 128;
-    const int64_t cap = int64_t(sms) * 8;  // 8 CTAs of 128 threads per SM
+    const int64_t cap = int64_t(sms) * per;
     return unsigned(want < cap ? want : cap);
 }
 
@@ -354,7 +372,7 @@ void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int
                         int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st) {
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
-    k_trace<0><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, nullptr, nullptr,
+    k_trace<0><<<trace_grid<0>(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, nullptr, nullptr,
                                                   nullptr, status, counters, 0, nullptr, nullptr);
 }
 
@@ -364,29 +382,29 @@ void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int3
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
     if (Z) {
-        k_trace<2><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx, Z,
+        k_trace<2><<<trace_grid<2>(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx, Z,
                                                       delta, status, nullptr, 0, nullptr, nullptr);
     } else {
-        k_trace<1><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx,
+        k_trace<1><<<trace_grid<1>(n_half), 128, 0, st>>>(m, R, o_begin, n_half, nullptr, offs, base, cap, idx,
                                                       nullptr, nullptr, status, nullptr, 0, nullptr, nullptr);
     }
 }
 
 void launch_trace_pad(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
                       int64_t *lens, int64_t *excess, int4 *resume, int32_t *rows, int *status,
-                      unsigned long long *counters, cudaStream_t st) {
+                      unsigned long long *counters, cudaStream_t st, int ctas_per_sm) {
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
-    k_trace<3><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, rows, nullptr,
+    k_trace<3><<<trace_grid<3>(n_half, ctas_per_sm), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, rows, nullptr,
                                                   nullptr, status, counters, pad, excess, resume);
 }
 
 void launch_trace_tail(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
                        const int64_t *lens, const int4 *resume, const int64_t *offs, int64_t base, int64_t cap,
-                       int32_t *tail, int *status, cudaStream_t st) {
+                       int32_t *tail, int *status, cudaStream_t st, int ctas_per_sm) {
     const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
     if (n_half == 0) return;
-    k_trace<4><<<trace_grid(n_half), 128, 0, st>>>(m, R, o_begin, n_half, const_cast<int64_t *>(lens), offs, base,
+    k_trace<4><<<trace_grid<4>(n_half, ctas_per_sm), 128, 0, st>>>(m, R, o_begin, n_half, const_cast<int64_t *>(lens), offs, base,
                                                   cap, tail, nullptr, nullptr, status, nullptr, pad, nullptr,
                                                   const_cast<int4 *>(resume));
 }

@@ -59,6 +59,7 @@ struct BatchPlan {
     int64_t total_half = 0, n_origins = 0, n_work = 0, tail_cap = 0, total_points = 0;
     int32_t pad = 0;
     int bpl = 1, max_lines = 1;
+    mgx_tuning tune{};
     int64_t *lens = nullptr, *excess = nullptr, *offs = nullptr, *obase = nullptr;
     int32_t *rows = nullptr, *tail = nullptr;
     int4 *resume = nullptr;
@@ -84,6 +85,7 @@ struct mgx_ctx {
     // HEALPix tables of levels 0..tab_level
     int tab_level = -1;
     double *dir = nullptr;    // [level_offset(tab_level+1)][3]
+    float4 *dirf = nullptr;   // [level_offset(tab_level+1)], dir rounded to float
     int32_t *anti = nullptr;  // [level_offset(tab_level+1)]
     std::vector<std::vector<uint32_t>> pair_lists;  // per level, host
     std::vector<uint32_t *> pair_lists_dev;         // per level, device
@@ -96,6 +98,7 @@ struct mgx_ctx {
     unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples, [2] trace steps, [3] redone
     int64_t trace_points = 0, solves = 0;
     BatchPlan plan;
+    mgx_tuning tune{};  // launch parameters of the batched solve (zero: automatic)
     cudaStream_t capture_stream = nullptr;
     // learned reduction network: FP32 master parameters, Adam moments, gradient
     // accumulator, loss accumulator, bf16 copies of W1 (padded) and W2
@@ -266,6 +269,7 @@ DevRays rays_view(const mgx_ctx *ctx, const Model &m) {
     r.npairs = m.npairs;
     r.rays = m.rays;
     r.dir = ctx->dir;
+    r.dirf = ctx->dirf;
     return r;
 }
 
@@ -275,6 +279,7 @@ mgx_status ensure_tables(mgx_ctx *ctx, int level) {
     if (level <= ctx->tab_level) return MGX_OK;
     const int64_t total = level_offset(level + 1);
     std::vector<double> dir(size_t(total) * 3);
+    std::vector<float4> dirf(static_cast<size_t>(total));
     std::vector<int32_t> anti(static_cast<size_t>(total));
     std::vector<std::vector<uint32_t>> lists(size_t(level) + 1);
     for (int l = 0; l <= level; ++l) {
@@ -285,6 +290,7 @@ mgx_status ensure_tables(mgx_ctx *ctx, int level) {
             dir[size_t(base + p) * 3 + 0] = v[0];
             dir[size_t(base + p) * 3 + 1] = v[1];
             dir[size_t(base + p) * 3 + 2] = v[2];
+            dirf[size_t(base + p)] = make_float4(float(v[0]), float(v[1]), float(v[2]), 0.0f);  // round to nearest
             const double w[3] = {-v[0], -v[1], -v[2]};
             anti[size_t(base + p)] = int32_t(hpx_vec2pix(l, w));
         }
@@ -296,8 +302,11 @@ mgx_status ensure_tables(mgx_ctx *ctx, int level) {
         }
     }
     double *ddir = nullptr;
+    float4 *ddirf = nullptr;
     int32_t *danti = nullptr;
     CK(dalloc(ctx, &ddir, dir.size()));
+    CK(dalloc(ctx, &ddirf, dirf.size()));
+    CK(cudaMemcpyAsync(ddirf, dirf.data(), dirf.size() * sizeof(float4), cudaMemcpyHostToDevice, ctx->stream));
     CK(dalloc(ctx, &danti, anti.size()));
     CK(cudaMemcpyAsync(ddir, dir.data(), dir.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(danti, anti.data(), anti.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx->stream));
@@ -309,9 +318,11 @@ mgx_status ensure_tables(mgx_ctx *ctx, int level) {
     }
     CK(cudaStreamSynchronize(ctx->stream));
     dfree(ctx, ctx->dir);
+    dfree(ctx, ctx->dirf);
     dfree(ctx, ctx->anti);
     for (auto *p : ctx->pair_lists_dev) dfree(ctx, p);
     ctx->dir = ddir;
+    ctx->dirf = ddirf;
     ctx->anti = danti;
     ctx->pair_lists = std::move(lists);
     ctx->pair_lists_dev = std::move(dl);
@@ -421,7 +432,7 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
         Timed t(ctx, MGX_K_TRACE_COUNT);
         launch_trace_pad(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.pad, pl.lens + hb, pl.excess + hb,
                          pl.resume + hb, pl.rows + hb * pl.pad, ctx->d_status,
-                         ctx->prof ? ctx->d_counters : nullptr, ctx->stream);
+                         ctx->prof ? ctx->d_counters : nullptr, ctx->stream, pl.tune.trace_ctas_per_sm);
         hb += int64_t(m->n) * m->npairs * 2;
     }
     CK(cudaMemsetAsync(pl.offs, 0, sizeof(int64_t), ctx->stream));
@@ -435,7 +446,8 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
         for (Model *m : ms) {
             Timed t(ctx, MGX_K_TRACE_EMIT);
             launch_trace_tail(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.pad, pl.lens + hb, pl.resume + hb,
-                              pl.offs + hb, 0, pl.tail_cap, pl.tail, ctx->d_status, ctx->stream);
+                              pl.offs + hb, 0, pl.tail_cap, pl.tail, ctx->d_status, ctx->stream,
+                              pl.tune.trace_ctas_per_sm);
             hb += int64_t(m->n) * m->npairs * 2;
         }
     }
@@ -455,22 +467,32 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
 }
 
 // Row width of the padded layout: the narrowest power of two that leaves at
-// most 2 % of the traced points to the tail pass, within the memory budget
-// for the rows (else the widest that fits).
-int32_t choose_pad(const unsigned long long *tot, int64_t total_half, size_t budget_bytes) {
+// most `permille` / 1000 of the traced points to the tail pass, within the
+// memory budget for the rows (else the widest that fits).
+int32_t choose_pad(const unsigned long long *tot, int64_t total_half, size_t budget_bytes, int32_t permille) {
     const unsigned long long all = tot[kPadCandidates];
     int best = -1;
     for (int j = 0; j < kPadCandidates; ++j) {
         if (size_t(total_half) * (size_t(1) << j) * sizeof(int32_t) > budget_bytes) break;
         best = j;
-        if (double(tot[j]) <= 0.02 * double(all)) break;
+        if (double(tot[j]) * 1000.0 <= double(permille) * double(all)) break;
     }
     return best < 0 ? 1 : int32_t(1) << best;
 }
 
+bool same_tuning(const mgx_tuning &a, const mgx_tuning &b) {
+    return a.bins_per_lane == b.bins_per_lane && a.trace_ctas_per_sm == b.trace_ctas_per_sm &&
+           a.tail_permille == b.tail_permille;
+}
+
+bool valid_tuning(const mgx_tuning &t) {
+    return t.bins_per_lane >= 0 && t.bins_per_lane <= 2 && t.trace_ctas_per_sm >= 0 && t.trace_ctas_per_sm <= 32 &&
+           t.tail_permille >= 0 && t.tail_permille <= 1000 && t.reserved == 0;
+}
+
 bool plan_matches(const BatchPlan &pl, const int32_t *models, int32_t n, const mgx_solve_params *p,
-                  double *const *J, int32_t flags) {
-    if (!pl.valid || int32_t(pl.models.size()) != n || pl.flags != flags) return false;
+                  double *const *J, int32_t flags, const mgx_tuning &tune) {
+    if (!pl.valid || int32_t(pl.models.size()) != n || pl.flags != flags || !same_tuning(pl.tune, tune)) return false;
     for (int32_t k = 0; k < n; ++k)
         if (pl.models[size_t(k)] != models[k] || pl.J[size_t(k)] != J[k]) return false;
     return pl.p.dtau_max == p->dtau_max && pl.p.dv_max == p->dv_max && pl.p.I_bdy == p->I_bdy &&
@@ -520,6 +542,7 @@ void mgx_destroy(mgx_ctx *ctx) {
         if (ctx->mlp_W2b) cudaFreeAsync(ctx->mlp_W2b, ctx->stream);
         for (auto &m : ctx->models)
             if (m.live) free_model(ctx, m);
+        dfree(ctx, ctx->dirf);
         dfree(ctx, ctx->dir);
         dfree(ctx, ctx->anti);
         for (auto *p : ctx->pair_lists_dev) dfree(ctx, p);
@@ -968,7 +991,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     DeviceGuard g(ctx->device);
     BatchPlan &pl = ctx->plan;
     const bool graph = (flags & MGX_BATCH_GRAPH) != 0;
-    if (graph && plan_matches(pl, models, n_models, p, J_out, flags) && pl.exec) {
+    if (graph && plan_matches(pl, models, n_models, p, J_out, flags, ctx->tune) && pl.exec) {
         CK(cudaGraphLaunch(pl.exec, ctx->stream));
         ctx->launches[MGX_K_SOLVE] += 1;
         const mgx_status s = sync_status(ctx);
@@ -980,6 +1003,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     pl.J.assign(J_out, J_out + n_models);
     pl.p = *p;
     pl.flags = flags;
+    pl.tune = ctx->tune;
     int64_t max_nb = 1;
     pl.max_lines = 1;
     for (Model *m : ms) {
@@ -987,6 +1011,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         pl.max_lines = std::max(pl.max_lines, int(m->L));
     }
     pl.bpl = solve_bins_per_lane(p->precision, int32_t(max_nb));
+    if (p->precision == MGX_FP32 && pl.tune.bins_per_lane > 0) pl.bpl = pl.tune.bins_per_lane;
     std::vector<BatchGeom> geo(static_cast<size_t>(n_models));
     std::vector<int64_t> obase(static_cast<size_t>(n_models));
     pl.total_half = pl.n_origins = pl.n_work = 0;
@@ -1036,7 +1061,8 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     }
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
-    pl.pad = choose_pad(tot, pl.total_half, std::min(ctx->arena_budget, free_b / 3));
+    pl.pad = choose_pad(tot, pl.total_half, std::min(ctx->arena_budget, free_b / 3),
+                        pl.tune.tail_permille > 0 ? pl.tune.tail_permille : 20);
     int j = 0;
     while ((int32_t(1) << j) < pl.pad) ++j;
     pl.tail_cap = int64_t(tot[j]);
@@ -1114,6 +1140,112 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     return MGX_OK;
 }
 
+
+mgx_status mgx_set_tuning(mgx_ctx *ctx, const mgx_tuning *t) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    mgx_tuning v{};
+    if (t) {
+        v = *t;
+        if (!valid_tuning(v)) return fail(ctx, MGX_EINVAL, "set_tuning: a field is out of range");
+    }
+    if (!same_tuning(v, ctx->tune)) {
+        DeviceGuard g(ctx->device);
+        free_plan(ctx, ctx->plan);
+    }
+    ctx->tune = v;
+    return MGX_OK;
+}
+
+mgx_status mgx_get_tuning(mgx_ctx *ctx, mgx_tuning *t) {
+    if (!ctx || !t) return MGX_EINVAL;
+    *t = ctx->tune;
+    return MGX_OK;
+}
+
+mgx_status mgx_autotune(mgx_ctx *ctx, const int32_t *models, int32_t n_models, const mgx_solve_params *p,
+                        double *const *J_out, int32_t flags, int32_t reps, mgx_tune_trial *trials,
+                        int32_t max_trials, int32_t *n_trials) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (n_trials) *n_trials = 0;
+    if (reps < 1 || reps > 100) return fail(ctx, MGX_EINVAL, "autotune: reps must be in 1..100");
+    if (max_trials < 0 || (max_trials > 0 && !trials)) return fail(ctx, MGX_EINVAL, "autotune: bad trial buffer");
+    if (!models || !p || n_models < 1) return fail(ctx, MGX_EINVAL, "autotune: bad model list or params");
+    int64_t max_nb = 1;
+    for (int32_t k = 0; k < n_models; ++k) {
+        const Model *m = get_model(ctx, models[k]);
+        if (!m) return fail(ctx, MGX_EINVAL, "autotune: no model %d", models[k]);
+        max_nb = std::max<int64_t>(max_nb, int64_t(m->L) * m->F);
+    }
+    DeviceGuard g(ctx->device);
+    const mgx_tuning saved = ctx->tune;
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int32_t count = 0;
+    // candidate -> median step time; the plan (and graph) is built by an untimed first call
+    auto time_one = [&](const mgx_tuning &t, double *ms) -> mgx_status {
+        ctx->tune = t;
+        mgx_status s = mgx_solve_J_batch(ctx, models, n_models, p, J_out, flags);
+        if (s != MGX_OK) return s;
+        std::vector<float> v;
+        for (int32_t r = 0; r < reps; ++r) {
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) return fail(ctx, MGX_ECUDA, "autotune: event");
+            s = mgx_solve_J_batch(ctx, models, n_models, p, J_out, flags);
+            if (s != MGX_OK) return s;
+            if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                return fail(ctx, MGX_ECUDA, "autotune: event");
+            float x = 0.0f;
+            cudaEventElapsedTime(&x, e0, e1);
+            v.push_back(x);
+        }
+        std::sort(v.begin(), v.end());
+        *ms = double(v[v.size() / 2]);
+        if (count < max_trials) trials[count] = mgx_tune_trial{t, *ms};
+        ++count;
+        return MGX_OK;
+    };
+    // start from the current tuning with its automatic fields made explicit
+    mgx_tuning best = saved;
+    if (best.bins_per_lane == 0 && p->precision == MGX_FP32) best.bins_per_lane = solve_bins_per_lane(MGX_FP32, int32_t(max_nb));
+    if (best.trace_ctas_per_sm == 0) best.trace_ctas_per_sm = 8;
+    if (best.tail_permille == 0) best.tail_permille = 20;
+    double best_ms = 0.0;
+    mgx_status s = time_one(best, &best_ms);
+    const int32_t bpl_c[] = {1, 2}, trace_c[] = {4, 6, 8}, tail_c[] = {5, 20, 80};
+    for (int dim = 0; dim < 3 && s == MGX_OK; ++dim) {
+        if (dim == 0 && p->precision != MGX_FP32) continue;
+        const int32_t *cand = dim == 0 ? bpl_c : dim == 1 ? trace_c : tail_c;
+        const int nc = dim == 0 ? 2 : 3;
+        const mgx_tuning base = best;
+        for (int c = 0; c < nc && s == MGX_OK; ++c) {
+            mgx_tuning t = base;
+            int32_t &field = dim == 0 ? t.bins_per_lane : dim == 1 ? t.trace_ctas_per_sm : t.tail_permille;
+            if (field == cand[c]) continue;
+            field = cand[c];
+            double ms = 0.0;
+            s = time_one(t, &ms);
+            if (s == MGX_OK && ms < best_ms) {
+                best = t;
+                best_ms = ms;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->prof = prof;
+    if (n_trials) *n_trials = count;
+    if (s != MGX_OK) {
+        ctx->tune = saved;
+        free_plan(ctx, ctx->plan);
+        return s;
+    }
+    ctx->tune = best;
+    return mgx_solve_J_batch(ctx, models, n_models, p, J_out, flags);  // leaves the fastest plan in place
+}
 
 mgx_status mgx_mlp_set_params(mgx_ctx *ctx, const float *theta) {
     if (!ctx) return MGX_EINVAL;

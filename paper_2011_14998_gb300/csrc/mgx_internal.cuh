@@ -61,6 +61,7 @@ struct DevRays {
     int32_t lmin, lmax, npairs;
     const uint32_t *rays;  // [n][npairs], (level << 28) | pixel
     const double *dir;     // [level_offset(lmax+1)][3] pixel-centre unit vectors
+    const float4 *dirf;    // the same vectors rounded to float (w = 0)
 };
 
 struct SolveArgs {
@@ -122,10 +123,10 @@ void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int3
 // pad, walk state after the row for the half-rays longer than it
 void launch_trace_pad(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
                       int64_t *lens, int64_t *excess, int4 *resume, int32_t *rows, int *status,
-                      unsigned long long *counters, cudaStream_t st);
+                      unsigned long long *counters, cudaStream_t st, int ctas_per_sm = 0);
 void launch_trace_tail(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end, int32_t pad,
                        const int64_t *lens, const int4 *resume, const int64_t *offs, int64_t base, int64_t cap,
-                       int32_t *tail, int *status, cudaStream_t st);
+                       int32_t *tail, int *status, cudaStream_t st, int ctas_per_sm = 0);
 
 // One model of a batched solve (device-resident descriptor).
 struct BatchSlot {

@@ -74,3 +74,50 @@ def test_batch_rejects_bad_arguments(setup):
         mgx.mgx_solve_J_batch(ctx.ptr, [mids[0], mids[0]], mgx.solve_params(), [out, out])
     with pytest.raises(mgx.MgxError):  # host output
         mgx.mgx_solve_J_batch(ctx.ptr, [mids[0]], mgx.solve_params(), [torch.empty((900, 50), dtype=torch.float64)])
+
+
+def test_tuning_changes_speed_not_results(setup):
+    """The tracer grid and the row width never change J; the bins per lane
+    select a differently compiled kernel, so single-precision J may differ in
+    its rounding (fused multiply-adds), far inside the FP32 tolerance."""
+    import paper_2011_14998_gb300 as mgx
+
+    ctx, models, mids = setup
+    flags = mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS
+    ctx.set_tuning(None)
+    ref = [o.cpu().numpy() for o in ctx.solve_J_batch(mids, precision=1, flags=flags)]
+    for t in ({"bins_per_lane": 2, "trace_ctas_per_sm": 4, "tail_permille": 5},
+              {"bins_per_lane": 2, "trace_ctas_per_sm": 16, "tail_permille": 1000},
+              {"bins_per_lane": 1, "trace_ctas_per_sm": 8, "tail_permille": 80}):
+        ctx.set_tuning(t)
+        assert ctx.tuning() == t
+        outs = ctx.solve_J_batch(mids, precision=1, flags=flags)
+        for o, r in zip(outs, ref):
+            if t["bins_per_lane"] == 2:  # the automatic choice for this batch (up to 50 bins)
+                assert np.array_equal(o.cpu().numpy(), r)
+            else:
+                assert j_rel_err(o.cpu().numpy(), r)[0] < 1e-5
+    ctx.set_tuning(None)
+    assert ctx.tuning() == {"bins_per_lane": 0, "trace_ctas_per_sm": 0, "tail_permille": 0}
+    with pytest.raises(mgx.MgxError):
+        ctx.set_tuning({"bins_per_lane": 3})
+    with pytest.raises(mgx.MgxError):
+        ctx.set_tuning({"trace_ctas_per_sm": 33})
+
+
+def test_autotune_keeps_fastest_candidate(setup):
+    import paper_2011_14998_gb300 as mgx
+
+    ctx, models, mids = setup
+    flags = mgx.MGX_BATCH_GRAPH | mgx.MGX_BATCH_RAYS
+    ctx.set_tuning(None)
+    ref = [o.cpu().numpy() for o in ctx.solve_J_batch(mids, precision=1, flags=flags)]
+    trials, outs = ctx.autotune(mids, precision=1, flags=flags, reps=2)
+    assert 4 <= len(trials) <= 8
+    assert all(t["step_ms"] > 0 for t in trials)
+    best = min(trials, key=lambda t: t["step_ms"])
+    chosen = ctx.tuning()
+    assert chosen == {k: best[k] for k in chosen}
+    for o, r in zip(outs, ref):
+        assert j_rel_err(o.cpu().numpy(), r)[0] < 1e-5
+    ctx.set_tuning(None)
