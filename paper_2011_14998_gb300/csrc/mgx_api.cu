@@ -200,7 +200,8 @@ struct Timed {
     mgx_ctx *c;
     int slot;
     cudaEvent_t a = nullptr, b = nullptr;
-    Timed(mgx_ctx *c_, int slot_) : c(c_), slot(slot_) {
+    Timed(mgx_ctx *c_, int slot_) : c(c_), slot(slot_) {  // slot < 0: not recorded
+        if (slot < 0) return;
         c->launches[slot] += 1;
         if (c->prof) {
             a = take_event(c);
@@ -407,8 +408,8 @@ void free_plan(mgx_ctx *ctx, BatchPlan &pl) {
 }
 
 // Rebuild the ray set of a model with its current levels and sample (enqueue only).
-void enqueue_rays(mgx_ctx *ctx, Model &m) {
-    Timed t(ctx, MGX_K_RAYS);
+void enqueue_rays(mgx_ctx *ctx, Model &m, bool timed = true) {
+    Timed t(ctx, timed ? MGX_K_RAYS : -1);
     if (m.lmin == m.lmax) {
         launch_rays_fixed(m.n, m.lmin, m.npairs, ctx->pair_lists_dev[size_t(m.lmin)], m.rays, ctx->stream);
     } else {
@@ -1042,7 +1043,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     CK(cudaMemcpyAsync(pl.obase, obase.data(), obase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
     // plan the layout from the half-ray lengths (the only host synchronisation)
     if (flags & MGX_BATCH_RAYS)
-        for (Model *m : ms) enqueue_rays(ctx, *m);
+        for (Model *m : ms) enqueue_rays(ctx, *m, false);  // planning is not part of a step's profile
     {
         int64_t hb = 0;
         for (Model *m : ms) {
