@@ -3,8 +3,8 @@
 Workload: 50 000-point spherical wind (log-uniform r in [1, 100] R*, Delaunay
 neighbours, beta-law velocity, T ~ r^-0.7), one line, 50 frequency bins,
 HEALPix nside 4 (96 ray pairs per point).  One step = the whole hot path on
-device-resident inputs: ray set -> trace (count + emit) -> velocity and
-optical-depth sampling -> Feautrier solve of every (point, pair, bin) -> J.
+device-resident inputs: ray set -> trace (padded rows + overflow) -> velocity
+and optical-depth sampling -> Feautrier solve of every (point, pair, bin) -> J.
 
 Metric: ray-pair x frequency Feautrier solves per second of the single-precision
 form (FP64 only for distance increments and the J sum); the FP64 plain form is
@@ -45,6 +45,24 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(t: float, ws: int, device=None) -> float:
+    """The slowest rank's value of t (t itself on one rank); device is "cuda"
+    for NCCL process groups and None (host tensor) for gloo."""
+    if ws <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(ws: int, units_per_rank_step: float, steps: int, t_max: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return ws * units_per_rank_step * steps / t_max
 
 
 def make_workload(n=50000, seed=2):
@@ -252,12 +270,10 @@ def run_mgx(args):
     torch.cuda.synchronize()
     with ClockSampler(gpu_physical_index(local)) as clk:
         t32, _ = timed(step32, args.steps, args.warmup, False)
+    t32 = max_over_ranks(t32, ws, "cuda")
     if ws > 1:
-        tt = torch.tensor([t32], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t32 = float(tt.item())
         torch.distributed.barrier()
-    value = ws * solves_per_step * args.steps / t32
+    value = job_throughput(ws, solves_per_step, args.steps, t32)
     # per-kernel CUDA-event breakdown of the same step, launched without the graph
     kb = max(1, min(args.steps, 3))
     tb, prof32 = timed(step32_profiled, kb, 1, True)
@@ -298,11 +314,8 @@ def run_mgx(args):
         e2e_step()
     torch.cuda.synchronize()
     te = time.perf_counter() - t0
-    if ws > 1:
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e_value = ws * solves_per_step * k_e2e / te
+    te = max_over_ranks(te, ws, "cuda")
+    e2e_value = job_throughput(ws, solves_per_step, k_e2e, te)
     assert np.array_equal(Jh.numpy(), J32), "end-to-end J differs from the device-resident run"
 
     if rank != 0:

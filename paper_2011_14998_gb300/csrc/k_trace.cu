@@ -165,7 +165,7 @@ __device__ Step step_contenders(const DevMesh &m, int32_t c, float4 oh, float Xo
 // operation.
 struct Walk {
     int64_t h, w;          // half-ray, write base of its entries
-    float4 oh;             // origin position (float) and id
+    float4 oh;             // origin position (float)
     float f0, f1, f2, Xo;  // direction (float), |x_o|_1
     float zc32, ezc;       // Z of the current point (float) and its bound
     int32_t o, c, k, expect;
