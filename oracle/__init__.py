@@ -46,7 +46,7 @@ class Model(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("dtau_max", C.c_double), ("dv_max", C.c_double), ("I_bdy", C.c_double),
-                ("decide32", C.c_int32)]
+                ("decide32", C.c_int32), ("order", C.c_int32)]
 
 
 def lib():
@@ -69,6 +69,7 @@ def lib():
                 "orc_bin_x": (dbl, [i32, dbl, i32]),
                 "orc_subdivide": (i64, [i64, vp, vp, vp, i64, dbl, i32, i64, vp, vp, vp]),
                 "orc_feautrier": (dbl, [i64, vp, vp, i64, dbl, vp]),
+                "orc_feautrier4": (dbl, [i64, vp, vp, i64, dbl, vp]),
                 "orc_pair_line": (i64, [vp, vp, i64, C.c_uint32, i32, i32, i64, vp, vp, vp]),
                 "orc_vline_size": (i64, [vp, vp, i64, C.c_uint32, vp]),
                 "orc_solve_J": (C.c_int, [vp, vp, i64, vp, i64, vp, C.c_int]),
@@ -202,18 +203,22 @@ class OracleModel:
         return J
 
 
-def params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, decide32=False) -> Params:
+def params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, decide32=False, order=2) -> Params:
     """decide32: take the velocity-sample count and Eq. 2's n_inter in single
-    precision, the precision in which the single-precision kernel decides them."""
-    return Params(dtau_max, dv_max, I_bdy, int(bool(decide32)))
+    precision, the precision in which the single-precision kernel decides them.
+    order: 2 (second-order scheme) or 4 (Hermitian scheme, Section 2.1)."""
+    if order not in (2, 4):
+        raise ValueError("order must be 2 or 4")
+    return Params(dtau_max, dv_max, I_bdy, int(bool(decide32)), int(order))
 
 
-def feautrier(dtau, S, io, I_bdy=0.0, all_rows=False):
+def feautrier(dtau, S, io, I_bdy=0.0, all_rows=False, order=2):
     dtau = np.ascontiguousarray(dtau, np.float64)
     S = np.ascontiguousarray(S, np.float64)
     M = len(dtau)
     u = np.empty(M + 1)
-    uo = lib().orc_feautrier(M, _p(dtau), _p(S), int(io), float(I_bdy), _p(u))
+    fn = lib().orc_feautrier4 if order == 4 else lib().orc_feautrier
+    uo = fn(M, _p(dtau), _p(S), int(io), float(I_bdy), _p(u))
     return u if all_rows else uo
 
 

@@ -306,6 +306,9 @@ typedef struct {
                          Eq. 2's n_inter as 1 unless chi_max > dtau_max / ds,
                          else ceil((chi_max ds) fl32(1/dtau_max));
                          everything else stays double */
+    int32_t order;    /* 2: the second-order scheme with second-order boundary
+                         conditions; 4: Auer's (1976) Hermitian fourth-order
+                         scheme with third-order boundary conditions (Section 2.1) */
 } orc_params;
 
 /* ------------------------------------------------------------------------- */
@@ -625,6 +628,79 @@ double orc_feautrier(int64_t M, const double *dtau, const double *S, int64_t io,
 }
 
 /* ------------------------------------------------------------------------- */
+/* Hermitian (fourth-order) Feautrier solve, Auer (1976), named in Section 2.1 */
+/* as the more accurate scheme Magritte provides, with the third-order          */
+/* boundary condition of Auer (1967).                                           */
+/* Interior row i (h- = dtau_{i-1}, h+ = dtau_i): the compact approximation     */
+/*   2/(h- + h+) [(u_{i+1} - u_i)/h+ - (u_i - u_{i-1})/h-]                      */
+/*     = a f_{i-1} + b f_i + g f_{i+1},   f = u - S  (Eq. 1: d2u/dtau2 = u - S), */
+/* with the weights that make it exact for polynomials of degree four on a      */
+/* non-uniform grid (Taylor expansion about tau_i):                             */
+/*   a = (h-^2 + h- h+ - h+^2) / (6 h- (h- + h+)),                              */
+/*   g = (h+^2 + h- h+ - h-^2) / (6 h+ (h- + h+)),   b = 1 - a - g,             */
+/* (1/12, 10/12, 1/12 on a uniform grid), i.e.                                  */
+/*   -(A_i - a) u_{i-1} + (1 + A_i - a + C_i - g) u_i - (C_i - g) u_{i+1}        */
+/*       = a S_{i-1} + b S_i + g S_{i+1}.                                        */
+/* Boundary row (h the increment to the neighbour, I the incoming intensity):   */
+/* du/dtau = u - I at the surface, the derivative from the Taylor series to     */
+/* third order, its third-derivative term from the difference of f over the     */
+/* first increment:                                                             */
+/*   (2/3 + 2/h + 2/h^2) u_end - (2/h^2 - 1/3) u_next = 2/3 S_end + 1/3 S_next   */
+/*                                                      + 2 I / h.              */
+/* Every row has diagonal excess (diagonal minus off-diagonals) 1 inside and    */
+/* 1 + 2/h at the ends, so the elimination keeps the form of Rybicki & Hummer   */
+/* with general off-diagonals a_i, c_i:                                         */
+/*   F_i = (B_i + a_i F_{i-1}/(1 + F_{i-1})) / c_i,                              */
+/*   z_i = (r_i + a_i z_{i-1}) / (c_i (1 + F_i)),  u_i = u_{i+1}/(1 + F_i) + z_i. */
+/* The right-hand side is formed as S_i + a (S_{i-1} - S_i) + g (S_{i+1} - S_i). */
+/* Returns u at row io (every row in u_all if not NULL); M = 0: u = I.          */
+/* ------------------------------------------------------------------------- */
+double orc_feautrier4(int64_t M, const double *dtau, const double *S, int64_t io, double I, double *u_all)
+{
+    if (M == 0) {
+        if (u_all) u_all[0] = I;
+        return I;
+    }
+    double *F = (double *)malloc(sizeof(double) * (size_t)M);
+    double *z = (double *)malloc(sizeof(double) * (size_t)M);
+    double *u = u_all ? u_all : (double *)malloc(sizeof(double) * (size_t)(M + 1));
+    {   /* boundary row 0 */
+        const double h = dtau[0];
+        const double c0 = 2.0 / (h * h) - 1.0 / 3.0;
+        const double B0 = 1.0 + 2.0 / h;
+        const double r0 = 2.0 / 3.0 * S[0] + 1.0 / 3.0 * S[1] + 2.0 * I / h;
+        F[0] = B0 / c0;
+        z[0] = r0 / (c0 * (1.0 + F[0]));
+    }
+    for (int64_t i = 1; i < M; ++i) {
+        const double hm = dtau[i - 1], hp = dtau[i], hs = hm + hp;
+        const double A = 2.0 / (hm * hs), C = 2.0 / (hp * hs);
+        const double wa = (hm * hm + hm * hp - hp * hp) / (6.0 * hm * hs);
+        const double wg = (hp * hp + hm * hp - hm * hm) / (6.0 * hp * hs);
+        const double a = A - wa, c = C - wg;
+        /* a S_{i-1} + b S_i + g S_{i+1} with b = 1 - a - g, written on the
+         * differences: next to a vanishing increment the weights grow like the
+         * ratio of the increments and b = 1 - a - g would cancel */
+        const double r = S[i] + wa * (S[i - 1] - S[i]) + wg * (S[i + 1] - S[i]);
+        F[i] = (1.0 + a * F[i - 1] / (1.0 + F[i - 1])) / c;
+        z[i] = (r + a * z[i - 1]) / (c * (1.0 + F[i]));
+    }
+    {   /* boundary row M */
+        const double h = dtau[M - 1];
+        const double aM = 2.0 / (h * h) - 1.0 / 3.0;
+        const double BM = 1.0 + 2.0 / h;
+        const double rM = 2.0 / 3.0 * S[M] + 1.0 / 3.0 * S[M - 1] + 2.0 * I / h;
+        u[M] = (rM + aM * z[M - 1]) / (BM + aM * F[M - 1] / (1.0 + F[M - 1]));
+    }
+    for (int64_t i = M - 1; i >= 0; --i) u[i] = u[i + 1] / (1.0 + F[i]) + z[i];
+    const double uo = u[io];
+    free(F);
+    free(z);
+    if (!u_all) free(u);
+    return uo;
+}
+
+/* ------------------------------------------------------------------------- */
 /* One pair line for one bin, exposed for the tests: fills dtau[0..M), S[0..M]  */
 /* and returns M (and the origin row in *io), or -1 on overflow of max_pts.      */
 /* ------------------------------------------------------------------------- */
@@ -698,7 +774,8 @@ int orc_solve_J(const orc_model *m, const orc_params *pr, int64_t n_orig, const 
                         bad = 1;
                         break;
                     }
-                    const double x = w2 * orc_feautrier(M, dtau, S, io, pr->I_bdy, NULL);
+                    const double x = w2 * (pr->order == 4 ? orc_feautrier4(M, dtau, S, io, pr->I_bdy, NULL)
+                                                          : orc_feautrier(M, dtau, S, io, pr->I_bdy, NULL));
                     const int b = l * F + k;
                     const double t = sum[b] + x;
                     if (fabs(sum[b]) >= fabs(x)) comp[b] += (sum[b] - t) + x;
