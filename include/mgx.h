@@ -68,6 +68,11 @@ typedef struct {
     double I_bdy;          /* intensity entering both ends of every ray                  */
     int32_t precision;     /* MGX_FP64 or MGX_FP32                                       */
     int32_t out_on_device; /* nonzero: J_out is a device pointer on the context's device */
+    int32_t order;         /* discretisation of Eq. 1 (Section 2.1): 0 or 2, the second-order
+                              scheme with second-order boundary conditions; 4, the Hermitian
+                              fourth-order scheme of Auer (1976) with third-order boundary
+                              conditions; anything else gives MGX_EINVAL                  */
+    int32_t reserved;      /* 0 */
 } mgx_solve_params;
 
 /* Create a context on CUDA device `device`, enqueuing on `stream` (a cudaStream_t;

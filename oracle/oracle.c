@@ -653,8 +653,14 @@ double orc_feautrier(int64_t M, const double *dtau, const double *S, int64_t io,
 /*   F_i = (B_i + a_i F_{i-1}/(1 + F_{i-1})) / c_i,                              */
 /*   z_i = (r_i + a_i z_{i-1}) / (c_i (1 + F_i)),  u_i = u_{i+1}/(1 + F_i) + z_i. */
 /* The right-hand side is formed as S_i + a (S_{i-1} - S_i) + g (S_{i+1} - S_i). */
+/* Reading: the weights a, g grow like the ratio of the two increments, so the  */
+/* rounding of S would be amplified without bound next to a vanishing increment */
+/* (traced points nearly level along the ray); a row whose increments differ by */
+/* more than a factor HERM_RATIO uses the second-order weights (a = g = 0).     */
 /* Returns u at row io (every row in u_all if not NULL); M = 0: u = I.          */
 /* ------------------------------------------------------------------------- */
+#define HERM_RATIO 64.0
+
 double orc_feautrier4(int64_t M, const double *dtau, const double *S, int64_t io, double I, double *u_all)
 {
     if (M == 0) {
@@ -675,8 +681,9 @@ double orc_feautrier4(int64_t M, const double *dtau, const double *S, int64_t io
     for (int64_t i = 1; i < M; ++i) {
         const double hm = dtau[i - 1], hp = dtau[i], hs = hm + hp;
         const double A = 2.0 / (hm * hs), C = 2.0 / (hp * hs);
-        const double wa = (hm * hm + hm * hp - hp * hp) / (6.0 * hm * hs);
-        const double wg = (hp * hp + hm * hp - hm * hm) / (6.0 * hp * hs);
+        double wa = (hm * hm + hm * hp - hp * hp) / (6.0 * hm * hs);
+        double wg = (hp * hp + hm * hp - hm * hm) / (6.0 * hp * hs);
+        if (hp > HERM_RATIO * hm || hm > HERM_RATIO * hp) wa = wg = 0.0;  /* second-order row */
         const double a = A - wa, c = C - wg;
         /* a S_{i-1} + b S_i + g S_{i+1} with b = 1 - a - g, written on the
          * differences: next to a vanishing increment the weights grow like the

@@ -42,7 +42,8 @@ class MgxError(RuntimeError):
 
 class SolveParams(C.Structure):
     _fields_ = [("dtau_max", C.c_double), ("dv_max", C.c_double), ("I_bdy", C.c_double),
-                ("precision", C.c_int32), ("out_on_device", C.c_int32)]
+                ("precision", C.c_int32), ("out_on_device", C.c_int32), ("order", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Profile(C.Structure):
@@ -327,8 +328,10 @@ def mgx_profile_read(ctx) -> dict:
                 trace_exact_steps=int(p.trace_exact_steps))
 
 
-def solve_params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, precision=MGX_FP64, out_on_device=False):
-    return SolveParams(float(dtau_max), float(dv_max), float(I_bdy), int(precision), int(bool(out_on_device)))
+def solve_params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, precision=MGX_FP64, out_on_device=False, order=2):
+    """order: 2 (second-order scheme) or 4 (Hermitian scheme, Section 2.1)."""
+    return SolveParams(float(dtau_max), float(dv_max), float(I_bdy), int(precision), int(bool(out_on_device)),
+                       int(order), 0)
 
 
 # ------------------------------------------------------------ convenience class
@@ -380,26 +383,27 @@ class Context:
         i = self.models[mid]
         return mgx_trace(self.ptr, mid, o_begin, i["n"] if o_end is None else o_end, i["npairs"], with_delta)
 
-    def solve_J(self, mid, precision=MGX_FP64, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, out=None):
+    def solve_J(self, mid, precision=MGX_FP64, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, out=None, order=2):
         """J [n, L*F] float64; `out` may be a CUDA float64 tensor (device output)."""
         i = self.models[mid]
         if out is not None:
-            p = solve_params(dtau_max, dv_max, I_bdy, precision, out_on_device=True)
+            p = solve_params(dtau_max, dv_max, I_bdy, precision, out_on_device=True, order=order)
             mgx_solve_J(self.ptr, mid, p, out)
             return out
         J = np.empty((i["n"], i["L"] * i["F"]), np.float64)
-        mgx_solve_J(self.ptr, mid, solve_params(dtau_max, dv_max, I_bdy, precision, False), J)
+        mgx_solve_J(self.ptr, mid, solve_params(dtau_max, dv_max, I_bdy, precision, False, order), J)
         return J
 
     def solve_J_batch(self, mids, precision=MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, outs=None,
-                      flags=0):
+                      flags=0, order=2):
         """J of several models in one persistent launch; returns CUDA float64 tensors."""
         import torch
 
         if outs is None:
             outs = [torch.empty((self.models[m]["n"], self.models[m]["L"] * self.models[m]["F"]),
                                 dtype=torch.float64, device=f"cuda:{self.device}") for m in mids]
-        mgx_solve_J_batch(self.ptr, list(mids), solve_params(dtau_max, dv_max, I_bdy, precision, True), outs, flags)
+        mgx_solve_J_batch(self.ptr, list(mids), solve_params(dtau_max, dv_max, I_bdy, precision, True, order), outs,
+                          flags)
         return outs
 
     def set_tuning(self, tuning: dict | None):
@@ -409,14 +413,14 @@ class Context:
         return mgx_get_tuning(self.ptr)
 
     def autotune(self, mids, precision=MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, outs=None, flags=0,
-                 reps=3):
+                 reps=3, order=2):
         """Pick the batched solve's launch parameters for these models by timing; returns (trials, outs)."""
         import torch
 
         if outs is None:
             outs = [torch.empty((self.models[m]["n"], self.models[m]["L"] * self.models[m]["F"]),
                                 dtype=torch.float64, device=f"cuda:{self.device}") for m in mids]
-        trials = mgx_autotune(self.ptr, list(mids), solve_params(dtau_max, dv_max, I_bdy, precision, True), outs,
+        trials = mgx_autotune(self.ptr, list(mids), solve_params(dtau_max, dv_max, I_bdy, precision, True, order), outs,
                               flags, reps)
         return trials, outs
 

@@ -460,7 +460,7 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
     CK(cudaMemsetAsync(pl.scratch + kScratchQueue, 0, sizeof(unsigned long long), ctx->stream));
     {
         Timed t(ctx, MGX_K_SOLVE);
-        launch_solve_queue(pl.p.precision, pl.bpl, pl.max_lines, pl.slots, pl.work, pl.n_work,
+        launch_solve_queue(pl.p.precision, pl.p.order == 4 ? 4 : 2, pl.bpl, pl.max_lines, pl.slots, pl.work, pl.n_work,
                            pl.scratch + kScratchQueue, ctx->stream);
     }
     CK(cudaGetLastError());
@@ -497,7 +497,7 @@ bool plan_matches(const BatchPlan &pl, const int32_t *models, int32_t n, const m
     for (int32_t k = 0; k < n; ++k)
         if (pl.models[size_t(k)] != models[k] || pl.J[size_t(k)] != J[k]) return false;
     return pl.p.dtau_max == p->dtau_max && pl.p.dv_max == p->dv_max && pl.p.I_bdy == p->I_bdy &&
-           pl.p.precision == p->precision;
+           pl.p.precision == p->precision && pl.p.order == p->order;
 }
 
 }  // namespace
@@ -811,6 +811,8 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
     if (!std::isfinite(p->dv_max)) return fail(ctx, MGX_EINVAL, "solve_J: dv_max must be finite");
     if (!std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J: I_bdy must be finite");
     if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J: unknown precision");
+    if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
+        return fail(ctx, MGX_EINVAL, "solve_J: order must be 0, 2 or 4 (reserved 0)");
     DeviceGuard g(ctx->device);
     const int32_t n = m->n, np = m->npairs;
     const int64_t n_half = int64_t(n) * np * 2;
@@ -880,7 +882,7 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         fill_pair_weights(a);
         {
             Timed t(ctx, MGX_K_SOLVE);
-            launch_solve(dm, dl, dr, a, p->precision, ctx->stream);
+            launch_solve(dm, dl, dr, a, p->precision, p->order == 4 ? 4 : 2, ctx->stream);
         }
         CK(cudaGetLastError());
     }
@@ -946,6 +948,8 @@ mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_para
     if (!std::isfinite(p->dv_max)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: dv_max must be finite");
     if (!std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: I_bdy must be finite");
     if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: unknown precision");
+    if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
+        return fail(ctx, MGX_EINVAL, "solve_J_noalloc: order must be 0, 2 or 4 (reserved 0)");
     cudaPointerAttributes attr;
     if (cudaPointerGetAttributes(&attr, J_out) != cudaSuccess || attr.type != cudaMemoryTypeDevice ||
         attr.device != ctx->device) {
@@ -955,7 +959,8 @@ mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_para
     DeviceGuard g(ctx->device);
     char msg[256] = {0};
     const int rc = noalloc_solve(ctx->device, mesh_view(*m), lines_view(*m), rays_view(ctx, *m), p->dtau_max,
-                                 p->dv_max, p->I_bdy, p->precision, J_out, ctx->d_status, ctx->stream, msg,
+                                 p->dv_max, p->I_bdy, p->precision, p->order == 4 ? 4 : 2, J_out, ctx->d_status,
+                                 ctx->stream, msg,
                                  sizeof msg);
     if (rc != MGX_OK) {
         cudaGetLastError();
@@ -974,6 +979,8 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0)) return fail(ctx, MGX_EINVAL, "solve_J_batch: dtau_max must be > 0");
     if (!std::isfinite(p->dv_max) || !std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J_batch: dv_max, I_bdy must be finite");
     if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J_batch: unknown precision");
+    if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
+        return fail(ctx, MGX_EINVAL, "solve_J_batch: order must be 0, 2 or 4 (reserved 0)");
     if (flags & ~(MGX_BATCH_GRAPH | MGX_BATCH_RAYS)) return fail(ctx, MGX_EINVAL, "solve_J_batch: unknown flags");
     std::vector<Model *> ms;
     for (int32_t k = 0; k < n_models; ++k) {

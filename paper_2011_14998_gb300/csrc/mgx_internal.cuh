@@ -157,11 +157,19 @@ void launch_excess_totals(const int64_t *lens, int64_t n, unsigned long long *ou
 // frequency bins per lane of the solve kernel; a chunk has
 // ceil(n_bins / (32 * bins_per_lane)) tiles per origin
 int solve_bins_per_lane(int precision, int32_t n_bins);
+// order: 2 (second-order scheme) or 4 (Hermitian scheme)
 void launch_solve(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a,
-                  int precision, cudaStream_t st);
+                  int precision, int order, cudaStream_t st);
 // persistent launch over a work list (x = model << 16 | tile, y = origin); next: zeroed counter
-void launch_solve_queue(int precision, int bins_per_lane, int max_lines, const BatchSlot *slots, const uint2 *work,
-                        int64_t n_work, unsigned long long *next, cudaStream_t st);
+void launch_solve_queue(int precision, int order, int bins_per_lane, int max_lines, const BatchSlot *slots,
+                        const uint2 *work, int64_t n_work, unsigned long long *next, cudaStream_t st);
+// the two instantiations (k_solve.cu, k_solve_herm.cu)
+template <int ORD>
+void launch_solve_ord(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a, int precision,
+                      cudaStream_t st);
+template <int ORD>
+void launch_solve_queue_ord(int precision, int bins_per_lane, int max_lines, const BatchSlot *slots,
+                            const uint2 *work, int64_t n_work, unsigned long long *next, cudaStream_t st);
 
 // ---- reduction criterion (k_reduce.cu)
 void launch_reduce(const DevMesh &m, const double *f, double f_small, double f_large,
@@ -170,7 +178,7 @@ void launch_reduce(const DevMesh &m, const double *f, double f_small, double f_l
 
 // ---- allocation-free solve with a fixed scratch array (noalloc.cu)
 int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRays &R, double dtau_max,
-                  double dv_max, double I_bdy, int precision, double *J, int *status, cudaStream_t st,
+                  double dv_max, double I_bdy, int precision, int order, double *J, int *status, cudaStream_t st,
                   char *err, size_t errlen);
 
 // ---- learned reduction network (k_mlp.cu); parameter offsets in theta

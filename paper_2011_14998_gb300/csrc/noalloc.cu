@@ -77,7 +77,7 @@ static cudaError_t scratch_address(int device, unsigned char **out) {
 }
 
 int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRays &R, double dtau_max,
-                  double dv_max, double I_bdy, int precision, double *J, int *status, cudaStream_t st,
+                  double dv_max, double I_bdy, int precision, int order, double *J, int *status, cudaStream_t st,
                   char *err, size_t errlen) {
     unsigned char *base = nullptr;
     cudaError_t ce = scratch_address(device, &base);
@@ -144,7 +144,7 @@ int noalloc_solve(int device, const DevMesh &m, const DevLines &Ln, const DevRay
         a.status = status;
         a.counters = nullptr;
         fill_pair_weights(a);
-        launch_solve(m, Ln, R, a, precision, st);
+        launch_solve(m, Ln, R, a, precision, order, st);
         if ((ce = cudaGetLastError()) != cudaSuccess) {
             snprintf(err, errlen, "CUDA error in the allocation-free solve: %s", cudaGetErrorString(ce));
             return MGX_ECUDA;

@@ -96,8 +96,11 @@ def test_thick_medium_and_single_point(orc):
 
 
 def test_vanishing_increment_next_to_normal_ones(orc):
-    # traced points can be 1e-17 apart in tau (grid lines along axis directions);
-    # the slab solution must not notice them
+    # traced points can be 1e-17 apart in tau (grid lines along axis directions):
+    # rows whose increments differ by more than a factor 64 take the second-order
+    # weights, so the result stays finite and close to the slab solution, and it
+    # is unchanged when S carries rounding-level noise (the compact weights would
+    # amplify that noise by the increment ratio, 1e15 here)
     base = np.full(40, 0.05)
     d = np.concatenate([np.full(5, 2e-17), base])
     tau = np.concatenate([[0.0], np.cumsum(d)])
@@ -105,7 +108,9 @@ def test_vanishing_increment_next_to_normal_ones(orc):
     io = 20
     exact = 1.0 - 0.5 * (np.exp(-tau[io]) + np.exp(-(tau[-1] - tau[io])))
     u = orc.feautrier(d, S, io, order=4)
-    assert abs(u - exact) < 1e-6
+    assert abs(u - exact) < 1e-4
+    Sn = S * (1 + 1e-16 * np.random.default_rng(0).choice([-1.0, 1.0], len(S)))
+    assert abs(orc.feautrier(d, Sn, io, order=4) - u) < 1e-12
 
 
 def test_two_point_line_boundary_rows(orc):
@@ -132,9 +137,10 @@ def test_solve_J_order_parameter(orc):
         orc.params(order=3)
 
 
-def test_grid_J_closed_form_third_order(orc):
-    # the 16^3 homogeneous cube: J against the closed form converges at third order
-    # with the Hermitian scheme (second order with the default one)
+def test_grid_J_closed_form_hermitian(orc):
+    # the 16^3 homogeneous cube: the axis rays carry points 1e-17 apart (libm's
+    # cos(pi/2) is not 0), whose rows take the second-order weights, so J
+    # converges at second order here, below the second-order scheme's error
     import synth
 
     from test_oracle_solver import _grid_closed_form
@@ -143,9 +149,8 @@ def test_grid_J_closed_form_third_order(orc):
     om = orc.OracleModel(m)
     origins = np.arange(0, 4096, 37)
     ref = _grid_closed_form(orc, m, om, None, origins)
-    errs = [np.abs(om.solve_J(orc.params(dtau_max=d, order=4), origins=origins) - ref).max()
-            for d in (0.2, 0.1, 0.05)]
-    assert errs[-1] <= 2e-6
-    assert errs[0] / errs[1] > 5.5 and errs[1] / errs[2] > 5.5, errs
-    e2 = np.abs(om.solve_J(orc.params(dtau_max=0.05), origins=origins) - ref).max()
-    assert errs[-1] < 0.05 * e2
+    for dtm in (0.2, 0.1, 0.05):
+        e4 = np.abs(om.solve_J(orc.params(dtau_max=dtm, order=4), origins=origins) - ref).max()
+        e2 = np.abs(om.solve_J(orc.params(dtau_max=dtm), origins=origins) - ref).max()
+        assert e4 < 0.6 * e2, (dtm, e4, e2)
+    assert e4 <= 2e-5
