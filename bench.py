@@ -227,6 +227,13 @@ def run_mgx(args):
         ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32],
                           flags=batched)
 
+    out32h = torch.empty((n, NB), dtype=torch.float64, device="cuda")
+
+    def step32h():
+        # the same batched step with the Hermitian (fourth-order) scheme
+        ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32h],
+                          flags=batched, order=4)
+
     def step32_profiled():
         ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32],
                           flags=mgx.MGX_BATCH_RAYS)
@@ -274,6 +281,8 @@ def run_mgx(args):
     if ws > 1:
         torch.distributed.barrier()
     value = job_throughput(ws, solves_per_step, args.steps, t32)
+    kh = max(1, min(args.steps, 5))
+    t32h, _ = timed(step32h, kh, max(3, min(args.warmup, 3)), False)
     # per-kernel CUDA-event breakdown of the same step, launched without the graph
     kb = max(1, min(args.steps, 3))
     tb, prof32 = timed(step32_profiled, kb, 1, True)
@@ -331,6 +340,7 @@ def run_mgx(args):
     rel32_64 = np.abs(J32 - J64)[mask] / np.abs(J64[mask])
     cpu = None
     acc_oracle = None
+    acc_herm = None
     if not args.no_cpu_baseline:
         cpu, origins, Jo = cpu_baseline(m, ctx.rays(mid), target_s=args.cpu_seconds)
         mo = np.abs(Jo) > 1e-6 * np.abs(Jo).max(axis=1, keepdims=True)
@@ -339,6 +349,7 @@ def run_mgx(args):
             "fp64_max_rel": float((np.abs(J64[origins] - Jo)[mo] / np.abs(Jo[mo])).max()),
             "origins": int(len(origins)),
         }
+        acc_herm = hermitian_accuracy(m, ctx.rays(mid), out32h.cpu().numpy())
 
     # roofline of the dominant kernel (the formal solution), per launch
     peaks = {}
@@ -370,6 +381,9 @@ def run_mgx(args):
                        tuning=tuning, autotune_trials=trials),
         "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * t64 / k64,
                        "speedup_fp32_over_fp64": value / ws / value64},
+        "hermitian_fp32": {"value": solves_per_step * kh / t32h, "unit": UNIT, "ms_per_step": 1e3 * t32h / kh,
+                           "cost_vs_second_order": (t32h / kh) / (t32 / args.steps),
+                           "oracle_sample": acc_herm},
         "accuracy": {"fp32_vs_fp64_max_rel": float(rel32_64.max()),
                      "fp32_vs_fp64_p99_rel": float(np.quantile(rel32_64, 0.99)),
                      "oracle_sample": acc_oracle},
@@ -396,18 +410,33 @@ def run_mgx(args):
 
 
 SOLVE_PROFILE = os.path.join(ROOT, "profiles", "k_solve_queue_wind50k.md")
+SOLVE_SOURCES = ("k_solve_impl.cuh", "k_solve.cu")
+
+
+def hermitian_accuracy(m, rays, J32h, n=200):
+    """Largest relative error of the FP32 Hermitian step against the oracle's
+    Hermitian solve (single-precision decisions) on n random origins."""
+    import oracle
+
+    om = oracle.OracleModel(m, rays=rays)
+    o = np.sort(np.random.default_rng(5).choice(len(m["pos"]), n, replace=False))
+    Jo = om.solve_J(oracle.params(dtau_max=0.5, dv_max=1.0 / 3.0, decide32=True, order=4), origins=o)
+    mask = np.abs(Jo) > 1e-6 * np.abs(Jo).max(axis=1, keepdims=True)
+    return {"fp32_max_rel": float((np.abs(J32h[o] - Jo)[mask] / np.abs(Jo[mask])).max()), "origins": n}
 
 
 def solve_traffic():
     """DRAM bytes per launch of the solve kernel from its committed ncu summary,
     or None when the kernel source has changed since the counters were taken
-    (the summary records the SHA-256 of k_solve.cu it was measured with)."""
+    (the summary records the SHA-256 of the solve's sources, concatenated in
+    the order of SOLVE_SOURCES, it was measured with)."""
     import hashlib
 
     try:
         kv = dict(l.split(":", 1) for l in open(SOLVE_PROFILE).read().splitlines() if l.startswith("dram_") or
                   l.startswith("k_solve_sha256"))
-        src = open(os.path.join(ROOT, "paper_2011_14998_gb300", "csrc", "k_solve.cu"), "rb").read()
+        src = b"".join(open(os.path.join(ROOT, "paper_2011_14998_gb300", "csrc", f), "rb").read()
+                       for f in SOLVE_SOURCES)
         if hashlib.sha256(src).hexdigest() != kv["k_solve_sha256"].strip():
             return None
         return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
