@@ -70,6 +70,7 @@ def lib():
                 "orc_subdivide": (i64, [i64, vp, vp, vp, i64, dbl, i32, i64, vp, vp, vp]),
                 "orc_feautrier": (dbl, [i64, vp, vp, i64, dbl, vp]),
                 "orc_feautrier4": (dbl, [i64, vp, vp, i64, dbl, vp]),
+                "orc_analytic_mesh": (i64, [i32, i32, i32, vp, dbl, dbl, dbl, C.c_uint64, vp, vp, vp]),
                 "orc_pair_line": (i64, [vp, vp, i64, C.c_uint32, i32, i32, i64, vp, vp, vp]),
                 "orc_vline_size": (i64, [vp, vp, i64, C.c_uint32, vp]),
                 "orc_solve_J": (C.c_int, [vp, vp, i64, vp, i64, vp, C.c_int]),
@@ -260,3 +261,16 @@ def reduce(pos, nbr_off, nbr_idx, f, f_small, f_large, G_thres, seed):
     lib().orc_reduce(n, _p(pos), _p(nbr_off), _p(nbr_idx), _p(f), f_small, f_large, G_thres,
                      C.c_uint64(seed & (2**64 - 1)), _p(Gf), _p(L), _p(ell), _p(keep))
     return Gf, L, ell, keep
+
+
+def analytic_mesh(f, h, ell_min, ell_max, seed):
+    """Element-size field of a tracer f [nx, ny, nz] on a Cartesian background
+    mesh of spacing h (Section 2.2.1, Eq. 5) and its thinning: (Gf, ell, keep)."""
+    f = np.ascontiguousarray(f, np.float64)
+    nx, ny, nz = f.shape
+    Gf = np.empty(f.size)
+    ell = np.empty(f.size)
+    keep = np.empty(f.size, np.uint8)
+    lib().orc_analytic_mesh(nx, ny, nz, _p(f), float(h), float(ell_min), float(ell_max), int(seed), _p(Gf),
+                            _p(ell), _p(keep))
+    return Gf.reshape(f.shape), ell.reshape(f.shape), keep.reshape(f.shape)

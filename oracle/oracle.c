@@ -840,3 +840,48 @@ void orc_reduce(int64_t n, const double *pos, const int64_t *nbr_off, const int3
         keep[i] = (deg == 0 || orc_uniform01(seed, i) < p) ? 1 : 0;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Element-size field of an analytic model (Section 2.2.1, Eq. 5).           */
+/* f > 0 is the tracer on a regular Cartesian background mesh of spacing h,  */
+/* index (i ny + j) nz + k.  Gf = max_n n.grad f / f = ||grad f|| / f, the    */
+/* gradient by central differences (first differences on the faces, 0 along */
+/* an axis with one point); ell maps [max Gf, min Gf] linearly onto         */
+/* [ell_min, ell_max] (all ell_max when Gf is constant).  Reading (Gmsh is   */
+/* not available): the mesh is the background mesh thinned to the density   */
+/* ell^-3, point i kept when u_i < (ell_min / ell_i)^3, u_i the SplitMix64   */
+/* uniform of (seed, i) as in the reduction.  Returns the number kept.       */
+/* ------------------------------------------------------------------------- */
+static double axis_diff(const double *f, int64_t idx, int64_t stride, int32_t pos, int32_t n, double h)
+{
+    if (n < 2) return 0.0;
+    if (pos == 0) return (f[idx + stride] - f[idx]) / h;
+    if (pos == n - 1) return (f[idx] - f[idx - stride]) / h;
+    return (f[idx + stride] - f[idx - stride]) / (2.0 * h);
+}
+
+int64_t orc_analytic_mesh(int32_t nx, int32_t ny, int32_t nz, const double *f, double h, double ell_min,
+                          double ell_max, uint64_t seed, double *Gf, double *ell, uint8_t *keep)
+{
+    const int64_t n = (int64_t)nx * ny * nz;
+    double gmin = INFINITY, gmax = -INFINITY;
+    for (int32_t i = 0; i < nx; ++i)
+        for (int32_t j = 0; j < ny; ++j)
+            for (int32_t k = 0; k < nz; ++k) {
+                const int64_t q = ((int64_t)i * ny + j) * nz + k;
+                const double gx = axis_diff(f, q, (int64_t)ny * nz, i, nx, h);
+                const double gy = axis_diff(f, q, nz, j, ny, h);
+                const double gz = axis_diff(f, q, 1, k, nz, h);
+                Gf[q] = sqrt(gx * gx + gy * gy + gz * gz) / f[q];
+                if (Gf[q] < gmin) gmin = Gf[q];
+                if (Gf[q] > gmax) gmax = Gf[q];
+            }
+    int64_t kept = 0;
+    for (int64_t q = 0; q < n; ++q) {
+        ell[q] = gmax > gmin ? ell_max - (Gf[q] - gmin) * (ell_max - ell_min) / (gmax - gmin) : ell_max;
+        const double r = ell_min / ell[q];
+        keep[q] = orc_uniform01(seed, q) < r * r * r ? 1 : 0;
+        kept += keep[q];
+    }
+    return kept;
+}
