@@ -182,6 +182,27 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
                            double f_large, double G_thres, uint64_t seed, double *Gf, double *L,
                            double *ell, uint8_t *keep, int64_t *n_kept);
 
+/* Element-size field of an analytic model and its mesh (Section 2.2.1, Eq. 5).
+ * f [nx][ny][nz] (index (i*ny + j)*nz + k, host, every value finite and > 0)
+ * is the tracer at the points of a regular Cartesian background mesh of
+ * spacing h.  For every point:
+ *   Gf = ||grad f|| / f  (the maximal relative change of Eq. 5), the gradient by
+ *        central differences, first differences on the faces, 0 along an axis
+ *        with a single point;
+ *   ell = ell_max - (Gf - min Gf)(ell_max - ell_min) / (max Gf - min Gf), the
+ *        linear map of [max Gf, min Gf] onto [ell_min, ell_max] (ell_max
+ *        everywhere when Gf is constant);
+ *   keep = u < (h / ell)^3, u the SplitMix64 uniform of (seed, point index) as
+ *        in mgx_reduce_mesh: the background mesh (point density h^-3) thinned to
+ *        the density ell^-3, in place of the paper's Gmsh meshing.
+ * Requires nx, ny, nz >= 1 and 0 < h <= ell_min <= ell_max (the background
+ * resolves the smallest desired element).  Gf, ell [n] (may be NULL) and keep [n] are host outputs;
+ * *n_kept (may be NULL) receives the number kept.  Every operation is
+ * explicitly rounded: the outputs are reproducible bit for bit. */
+mgx_status mgx_analytic_mesh(mgx_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, const double *f, double h,
+                             double ell_min, double ell_max, uint64_t seed, double *Gf, double *ell,
+                             uint8_t *keep, int64_t *n_kept);
+
 /* Flags of mgx_solve_J_batch. */
 enum {
     MGX_BATCH_GRAPH = 1, /* capture the step in a CUDA graph and replay it on later calls */

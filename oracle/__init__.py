@@ -265,7 +265,8 @@ def reduce(pos, nbr_off, nbr_idx, f, f_small, f_large, G_thres, seed):
 
 def analytic_mesh(f, h, ell_min, ell_max, seed):
     """Element-size field of a tracer f [nx, ny, nz] on a Cartesian background
-    mesh of spacing h (Section 2.2.1, Eq. 5) and its thinning: (Gf, ell, keep)."""
+    mesh of spacing h (Section 2.2.1, Eq. 5) and its thinning to the density
+    ell^-3 (keep probability (h / ell)^3): (Gf, ell, keep)."""
     f = np.ascontiguousarray(f, np.float64)
     nx, ny, nz = f.shape
     Gf = np.empty(f.size)

@@ -848,9 +848,10 @@ void orc_reduce(int64_t n, const double *pos, const int64_t *nbr_off, const int3
 /* gradient by central differences (first differences on the faces, 0 along */
 /* an axis with one point); ell maps [max Gf, min Gf] linearly onto         */
 /* [ell_min, ell_max] (all ell_max when Gf is constant).  Reading (Gmsh is   */
-/* not available): the mesh is the background mesh thinned to the density   */
-/* ell^-3, point i kept when u_i < (ell_min / ell_i)^3, u_i the SplitMix64   */
-/* uniform of (seed, i) as in the reduction.  Returns the number kept.       */
+/* not available): the mesh is the background mesh (density h^-3) thinned to */
+/* the density ell^-3, point i kept when u_i < (h / ell_i)^3, u_i the        */
+/* SplitMix64 uniform of (seed, i) as in the reduction (h <= ell_min).       */
+/* Returns the number kept.                                                   */
 /* ------------------------------------------------------------------------- */
 static double axis_diff(const double *f, int64_t idx, int64_t stride, int32_t pos, int32_t n, double h)
 {
@@ -879,7 +880,7 @@ int64_t orc_analytic_mesh(int32_t nx, int32_t ny, int32_t nz, const double *f, d
     int64_t kept = 0;
     for (int64_t q = 0; q < n; ++q) {
         ell[q] = gmax > gmin ? ell_max - (Gf[q] - gmin) * (ell_max - ell_min) / (gmax - gmin) : ell_max;
-        const double r = ell_min / ell[q];
+        const double r = h / ell[q];
         keep[q] = orc_uniform01(seed, q) < r * r * r ? 1 : 0;
         kept += keep[q];
     }

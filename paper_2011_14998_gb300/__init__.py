@@ -28,7 +28,7 @@ ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs
                "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read",
                "mgx_solve_J_noalloc", "mgx_solve_J_batch", "mgx_mlp_set_params", "mgx_mlp_get_params",
                "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned",
-               "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune")
+               "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune", "mgx_analytic_mesh")
 MGX_MLP_NPARAM = 4801
 MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
         "mgx_set_tuning": (i32, [vp, C.POINTER(Tuning)]),
+        "mgx_analytic_mesh": (i32, [vp, i32, i32, i32, vp, dbl, dbl, dbl, u64, vp, vp, vp, C.POINTER(i64)]),
         "mgx_get_tuning": (i32, [vp, C.POINTER(Tuning)]),
         "mgx_autotune": (i32, [vp, vp, i32, C.POINTER(SolveParams), vp, i32, i32, C.POINTER(TuneTrial), i32,
                                C.POINTER(i32)]),
@@ -223,6 +224,21 @@ def mgx_solve_J_batch(ctx, models, params: SolveParams, J_outs, flags: int = 0) 
     ids = np.ascontiguousarray(models, np.int32)
     ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
     _check(ctx, load_library().mgx_solve_J_batch(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags)))
+
+
+def mgx_analytic_mesh(ctx, f, h, ell_min, ell_max, seed=0):
+    """Element-size field of a tracer f [nx, ny, nz] on a Cartesian background
+    mesh (Section 2.2.1, Eq. 5) and its thinning; returns (Gf, ell, keep, n_kept)."""
+    f = np.ascontiguousarray(f, np.float64)
+    nx, ny, nz = f.shape
+    Gf = np.empty(f.shape)
+    ell = np.empty(f.shape)
+    keep = np.empty(f.shape, np.uint8)
+    nk = C.c_int64(0)
+    _check(ctx, load_library().mgx_analytic_mesh(ctx, nx, ny, nz, _ptr(f), float(h), float(ell_min), float(ell_max),
+                                                 int(seed) & (2**64 - 1), _ptr(Gf), _ptr(ell), _ptr(keep),
+                                                 C.byref(nk)))
+    return Gf, ell, keep, int(nk.value)
 
 
 def mgx_set_tuning(ctx, tuning: dict | None) -> None:

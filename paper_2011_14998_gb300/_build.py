@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmgx.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-EXACT_FP = {"k_rays.cu", "k_reduce.cu", "hpx_host.cpp"}
+EXACT_FP = {"k_rays.cu", "k_reduce.cu", "k_analytic.cu", "hpx_host.cpp"}
 
 
 def _nvcc() -> str:

@@ -14,14 +14,6 @@ namespace mgx {
 
 namespace {
 
-__device__ __forceinline__ double splitmix_uniform(uint64_t seed, int64_t i) {
-    uint64_t z = seed + uint64_t(i + 1) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    z ^= z >> 31;
-    return __dmul_rn(double(z >> 11), 1.0 / 9007199254740992.0);
-}
-
 __global__ void k_reduce(DevMesh m, const double *__restrict__ f, double f_small, double f_large,
                          double G_thres, uint64_t seed, double *Gf, double *L, double *ell,
                          uint8_t *keep) {

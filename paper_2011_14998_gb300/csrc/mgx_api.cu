@@ -936,6 +936,47 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
     return MGX_OK;
 }
 
+mgx_status mgx_analytic_mesh(mgx_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, const double *f, double h,
+                             double ell_min, double ell_max, uint64_t seed, double *Gf, double *ell,
+                             uint8_t *keep, int64_t *n_kept) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (nx < 1 || ny < 1 || nz < 1 || !f || !keep) return fail(ctx, MGX_EINVAL, "analytic_mesh: bad sizes or null f/keep");
+    if (!(h > 0.0) || !std::isfinite(h) || !(ell_min >= h) || !(ell_max >= ell_min) || !std::isfinite(ell_max))
+        return fail(ctx, MGX_EINVAL, "analytic_mesh: need 0 < h <= ell_min <= ell_max, finite");
+    const int64_t n = int64_t(nx) * ny * nz;
+    for (int64_t q = 0; q < n; ++q)
+        if (!(f[q] > 0.0) || !std::isfinite(f[q])) return fail(ctx, MGX_EINVAL, "analytic_mesh: f[%lld] is not finite and > 0", (long long)q);
+    DeviceGuard g(ctx->device);
+    double *fd = nullptr, *gd = nullptr, *ed = nullptr;
+    uint8_t *kd = nullptr;
+    unsigned long long *cnt = nullptr;  // [0] min bits, [1] max bits, [2] kept
+    CK(dalloc(ctx, &fd, size_t(n)));
+    CK(dalloc(ctx, &gd, size_t(n)));
+    CK(dalloc(ctx, &kd, size_t(n)));
+    if (ell) CK(dalloc(ctx, &ed, size_t(n)));
+    CK(dalloc(ctx, &cnt, 3));
+    const unsigned long long init[3] = {~0ull, 0ull, 0ull};
+    CK(cudaMemcpyAsync(cnt, init, sizeof init, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(fd, f, size_t(n) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_size_field(nx, ny, nz, fd, h, gd, cnt, ctx->stream);
+        launch_size_map(n, gd, cnt, h, ell_min, ell_max, seed, ed, kd, cnt + 2, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    unsigned long long kept = 0;
+    CK(cudaMemcpyAsync(keep, kd, size_t(n), cudaMemcpyDeviceToHost, ctx->stream));
+    if (Gf) CK(cudaMemcpyAsync(Gf, gd, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    if (ell) CK(cudaMemcpyAsync(ell, ed, size_t(n) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&kept, cnt + 2, sizeof kept, cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, fd); dfree(ctx, gd); dfree(ctx, kd); dfree(ctx, ed); dfree(ctx, cnt);
+    const mgx_status s = sync_status(ctx);
+    if (s != MGX_OK) return s;
+    if (n_kept) *n_kept = int64_t(kept);
+    return MGX_OK;
+}
+
 mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, double *J_out) {
     if (!ctx) return MGX_EINVAL;
     ctx->err.clear();

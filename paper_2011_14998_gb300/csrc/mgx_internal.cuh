@@ -171,6 +171,25 @@ template <int ORD>
 void launch_solve_queue_ord(int precision, int bins_per_lane, int max_lines, const BatchSlot *slots,
                             const uint2 *work, int64_t n_work, unsigned long long *next, cudaStream_t st);
 
+// SplitMix64 (Steele, Lea & Flood 2014) started at seed + (i+1) * golden gamma,
+// its top 53 bits as a uniform in [0, 1): the thinning coin of point i.
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, int64_t i) {
+    uint64_t z = seed + uint64_t(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return __dmul_rn(double(z >> 11), 1.0 / 9007199254740992.0);
+}
+
+// ---- element-size field of an analytic model (k_analytic.cu); mm[0], mm[1]:
+// bits of the smallest and largest Gf (non-negative doubles order as integers),
+// kept: number of kept points
+void launch_size_field(int32_t nx, int32_t ny, int32_t nz, const double *f, double h, double *Gf,
+                       unsigned long long *mm, cudaStream_t st);
+void launch_size_map(int64_t n, const double *Gf, const unsigned long long *mm, double h, double ell_min,
+                     double ell_max, uint64_t seed, double *ell, uint8_t *keep, unsigned long long *kept,
+                     cudaStream_t st);
+
 // ---- reduction criterion (k_reduce.cu)
 void launch_reduce(const DevMesh &m, const double *f, double f_small, double f_large,
                    double G_thres, uint64_t seed, double *Gf, double *L, double *ell,

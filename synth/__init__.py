@@ -149,6 +149,20 @@ def random_cloud(n: int = 40, seed: int = 0, n_lines: int = 1, n_freq: int = 7,
         sample=sample_indices(n), rho=rng.uniform(0.1, 1.0, n), T=T)
 
 
+def spiral_density(x: np.ndarray, r_in: float = 10.0, arm_spacing: float = 50.0, contrast: float = 10.0) -> np.ndarray:
+    """Analytic tracer of the binary-wind spiral (the density of spiral_model):
+    (max(r, r_in)/r_in)^-2 (1 + (contrast - 1) g), g the Gaussian arm profile
+    about r = r_in + arm_spacing phi / 2 pi (half-width 8 AU, scale height 30 AU)."""
+    x = np.asarray(x, np.float64)
+    r = np.sqrt((x ** 2).sum(-1))
+    rc = np.sqrt(x[..., 0] ** 2 + x[..., 1] ** 2)
+    ph = np.arctan2(x[..., 1], x[..., 0]) % (2 * np.pi)
+    r0 = r_in + arm_spacing * ph / (2 * np.pi)
+    d = np.abs(((rc - r0 + 0.5 * arm_spacing) % arm_spacing) - 0.5 * arm_spacing)
+    g = np.exp(-(d / 8.0) ** 2) * np.exp(-(x[..., 2] / 30.0) ** 2)
+    return (np.maximum(r, r_in) / r_in) ** -2.0 * (1 + (contrast - 1) * g)
+
+
 def spiral_model(n: int = 1_000_000, seed: int = 4, n_freq: int = 100, x_span: float = 4.0, level: int = 2,
                  l_min: int | None = None, box: float = 1200.0, arm_spacing: float = 50.0,
                  contrast: float = 10.0, tau_radial: float = 10.0, cont_frac: float = 1e-4):

@@ -6,7 +6,7 @@ from [max Gf, min Gf] onto [ell_min, ell_max]) and of its thinning.
   Gf = sinh(a h) / h inside and (e^{ah} - 1)/h, (1 - e^{-ah})/h on the faces.
 * A Gaussian tracer approaches Gf = r / sigma^2 at second order in h.
 * ell is affine in Gf with the stated endpoints; a constant tracer gives ell_max.
-* The kept fraction follows (ell_min / ell)^3 in distribution.
+* The kept fraction follows (h / ell)^3 in distribution.
 """
 import math
 
@@ -55,7 +55,8 @@ def test_linear_map_and_constant_tracer(orc):
 
 def test_thinning_rate(orc):
     f, r, h, s = _gauss(41)
-    Gf, ell, keep = orc.analytic_mesh(f, h, h, 0.2, seed=5)
+    Gf, ell, keep = orc.analytic_mesh(f, h, 1.5 * h, 0.2, seed=5)
+    assert ell.min() == 1.5 * h
     p = (h / ell.ravel()) ** 3
     k = keep.sum()
     assert abs(k - p.sum()) < 5 * math.sqrt((p * (1 - p)).sum())
