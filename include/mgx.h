@@ -92,6 +92,13 @@ const char *mgx_last_error(const mgx_ctx *ctx);
  * Returns -1 for invalid levels. */
 int64_t mgx_rayset_npairs(int32_t l_min, int32_t l_max);
 
+/* HEALPix nested scheme (Gorski et al. 2005), host only: the unit vector of the
+ * centre of pixel p of level l (v [3]), and the pixel containing -v (its
+ * antipode).  Return 0 / the antipode, or -1 for l outside 0..MGX_MAX_LEVEL or
+ * p outside 0..12*4^l-1 (or a null v). */
+int32_t mgx_pix2vec(int32_t l, int64_t p, double *v);
+int64_t mgx_antipode(int32_t l, int64_t p);
+
 /* Load a point cloud with its neighbour graph (Section 2.2: "a point cloud and
  * nearest neighbour information").
  *   n        number of points, 1 <= n < 2^31
@@ -181,6 +188,15 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *para
 mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double f_small,
                            double f_large, double G_thres, uint64_t seed, double *Gf, double *L,
                            double *ell, uint8_t *keep, int64_t *n_kept);
+
+/* u at the origin of every pair line (Eq. 1 solved per ray pair and bin, the
+ * quantity that Eq. 3-4 weight into J), for origins [o_begin, o_end):
+ * u_out [o_end - o_begin][n_pairs][n_lines*n_freq], host or device as
+ * params->out_on_device says.  Same parameters and errors as mgx_solve_J; the
+ * traced lists of the range must fit the context's arena (16 GiB), else
+ * MGX_ERANGE (split the range). */
+mgx_status mgx_solve_u(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params, int64_t o_begin,
+                       int64_t o_end, double *u_out);
 
 /* Element-size field of an analytic model and its mesh (Section 2.2.1, Eq. 5).
  * f [nx][ny][nz] (index (i*ny + j)*nz + k, host, every value finite and > 0)

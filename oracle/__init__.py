@@ -74,6 +74,7 @@ def lib():
                 "orc_pair_line": (i64, [vp, vp, i64, C.c_uint32, i32, i32, i64, vp, vp, vp]),
                 "orc_vline_size": (i64, [vp, vp, i64, C.c_uint32, vp]),
                 "orc_solve_J": (C.c_int, [vp, vp, i64, vp, i64, vp, C.c_int]),
+                "orc_solve_u": (C.c_int, [vp, vp, i64, vp, i64, vp, C.c_int]),
                 "orc_uniform01": (dbl, [u64, i64]),
                 "orc_reduce": (None, [i64, vp, vp, vp, vp, dbl, dbl, dbl, u64, vp, vp, vp, vp]),
             }
@@ -202,6 +203,17 @@ class OracleModel:
         if rc != 0:
             raise ValueError("oracle solve failed (line longer than max_pts or bad sizes)")
         return J
+
+    def solve_u(self, params, origins, threads=None, max_pts=1 << 22) -> np.ndarray:
+        """u at the origin of every pair line: [len(origins), pairs, L*F]."""
+        origins = np.ascontiguousarray(origins, np.int64)
+        nb = len(self.nu0) * self.n_freq
+        u = np.zeros((len(origins), self.rays.shape[1], nb))
+        rc = lib().orc_solve_u(C.byref(self.s), C.byref(params), len(origins), _p(origins), max_pts, _p(u),
+                               threads or os.cpu_count() or 1)
+        if rc != 0:
+            raise ValueError("oracle solve failed (line longer than max_pts or bad sizes)")
+        return u
 
 
 def params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, decide32=False, order=2) -> Params:

@@ -747,8 +747,10 @@ int64_t orc_vline_size(const orc_model *m, const orc_params *pr, int64_t o, uint
 /* Neumaier's compensated summation.  J_out[no][L * n_freq], bin index l*F + k. */
 /* Returns 0, or -1 if a sub-divided line exceeds max_pts.                      */
 /* ------------------------------------------------------------------------- */
-int orc_solve_J(const orc_model *m, const orc_params *pr, int64_t n_orig, const int64_t *origins,
-                int64_t max_pts, double *J_out, int threads)
+/* J of the given origins (J_out [n_orig][L*F], may be NULL) and, when u_out is */
+/* not NULL, u at the origin of every pair line (u_out [n_orig][pairs][L*F]).   */
+static int solve_origins(const orc_model *m, const orc_params *pr, int64_t n_orig, const int64_t *origins,
+                         int64_t max_pts, double *J_out, double *u_out, int threads)
 {
     const int64_t np = orc_rayset_npairs(m->l_min, m->l_max);
     const int L = m->n_lines, F = m->n_freq, nb = L * F;
@@ -781,9 +783,11 @@ int orc_solve_J(const orc_model *m, const orc_params *pr, int64_t n_orig, const 
                         bad = 1;
                         break;
                     }
-                    const double x = w2 * (pr->order == 4 ? orc_feautrier4(M, dtau, S, io, pr->I_bdy, NULL)
-                                                          : orc_feautrier(M, dtau, S, io, pr->I_bdy, NULL));
+                    const double uo = pr->order == 4 ? orc_feautrier4(M, dtau, S, io, pr->I_bdy, NULL)
+                                                     : orc_feautrier(M, dtau, S, io, pr->I_bdy, NULL);
+                    const double x = w2 * uo;
                     const int b = l * F + k;
+                    if (u_out) u_out[(q * np + p) * nb + b] = uo;
                     const double t = sum[b] + x;
                     if (fabs(sum[b]) >= fabs(x)) comp[b] += (sum[b] - t) + x;
                     else comp[b] += (x - t) + sum[b];
@@ -791,10 +795,25 @@ int orc_solve_J(const orc_model *m, const orc_params *pr, int64_t n_orig, const 
                 }
             vline_free(&v);
         }
-        for (int b = 0; b < nb; ++b) J_out[q * nb + b] = sum[b] + comp[b];
+        if (J_out)
+            for (int b = 0; b < nb; ++b) J_out[q * nb + b] = sum[b] + comp[b];
         free(sum); free(comp); free(dtau); free(S); free(chi); free(eta);
     }
     return bad ? -1 : 0;
+}
+
+int orc_solve_J(const orc_model *m, const orc_params *pr, int64_t n_orig, const int64_t *origins,
+                int64_t max_pts, double *J_out, int threads)
+{
+    return solve_origins(m, pr, n_orig, origins, max_pts, J_out, NULL, threads);
+}
+
+/* u at the origin of every pair line of the given origins, [n_orig][pairs][L*F]
+ * (the per-ray mean intensity that J weights with Eq. 4). */
+int orc_solve_u(const orc_model *m, const orc_params *pr, int64_t n_orig, const int64_t *origins,
+                int64_t max_pts, double *u_out, int threads)
+{
+    return solve_origins(m, pr, n_orig, origins, max_pts, NULL, u_out, threads);
 }
 
 /* ------------------------------------------------------------------------- */

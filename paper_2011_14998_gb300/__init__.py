@@ -28,7 +28,8 @@ ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs
                "mgx_solve_J", "mgx_reduce_mesh", "mgx_profile_enable", "mgx_profile_read",
                "mgx_solve_J_noalloc", "mgx_solve_J_batch", "mgx_mlp_set_params", "mgx_mlp_get_params",
                "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned",
-               "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune", "mgx_analytic_mesh")
+               "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune", "mgx_analytic_mesh", "mgx_solve_u",
+               "mgx_pix2vec", "mgx_antipode")
 MGX_MLP_NPARAM = 4801
 MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
@@ -107,6 +108,9 @@ def load_library(path: str = LIB_PATH):
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
         "mgx_set_tuning": (i32, [vp, C.POINTER(Tuning)]),
+        "mgx_pix2vec": (i32, [i32, i64, vp]),
+        "mgx_antipode": (i64, [i32, i64]),
+        "mgx_solve_u": (i32, [vp, i32, C.POINTER(SolveParams), i64, i64, vp]),
         "mgx_analytic_mesh": (i32, [vp, i32, i32, i32, vp, dbl, dbl, dbl, u64, vp, vp, vp, C.POINTER(i64)]),
         "mgx_get_tuning": (i32, [vp, C.POINTER(Tuning)]),
         "mgx_autotune": (i32, [vp, vp, i32, C.POINTER(SolveParams), vp, i32, i32, C.POINTER(TuneTrial), i32,
@@ -224,6 +228,20 @@ def mgx_solve_J_batch(ctx, models, params: SolveParams, J_outs, flags: int = 0) 
     ids = np.ascontiguousarray(models, np.int32)
     ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
     _check(ctx, load_library().mgx_solve_J_batch(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags)))
+
+
+def mgx_pix2vec(l: int, p: int) -> np.ndarray:
+    v = np.empty(3)
+    if load_library().mgx_pix2vec(int(l), int(p), _ptr(v)) != 0:
+        raise ValueError("bad HEALPix level or pixel")
+    return v
+
+
+def mgx_antipode(l: int, p: int) -> int:
+    a = load_library().mgx_antipode(int(l), int(p))
+    if a < 0:
+        raise ValueError("bad HEALPix level or pixel")
+    return int(a)
 
 
 def mgx_analytic_mesh(ctx, f, h, ell_min, ell_max, seed=0):
@@ -409,6 +427,15 @@ class Context:
         J = np.empty((i["n"], i["L"] * i["F"]), np.float64)
         mgx_solve_J(self.ptr, mid, solve_params(dtau_max, dv_max, I_bdy, precision, False, order), J)
         return J
+
+    def solve_u(self, mid, o_begin, o_end, precision=MGX_FP64, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0,
+                order=2):
+        """u at the origin of every pair line of origins [o_begin, o_end): [n_o, pairs, L*F]."""
+        i = self.models[mid]
+        u = np.empty((o_end - o_begin, i["npairs"], i["L"] * i["F"]), np.float64)
+        _check(self.ptr, load_library().mgx_solve_u(self.ptr, mid, C.byref(solve_params(
+            dtau_max, dv_max, I_bdy, precision, False, order)), int(o_begin), int(o_end), _ptr(u)))
+        return u
 
     def solve_J_batch(self, mids, precision=MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, outs=None,
                       flags=0, order=2):

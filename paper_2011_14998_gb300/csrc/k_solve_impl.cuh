@@ -624,6 +624,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
             const R u = ORD == 4 ? origin_u4(wb[i], wf[i], S_o[i], R(a.I_bdy)) : origin_u2(wb[i], wf[i], S_o[i]);
+            if (a.u_out && act[i]) a.u_out[(int64_t(oc) * Rs.npairs + p) * NB + bin[i]] = double(u);
             const double xv = w2 * double(u);
             const double t = sum[i] + xv;  // Neumaier compensated sum
             if (fabs(sum[i]) >= fabs(xv)) comp[i] += (sum[i] - t) + xv;

@@ -566,6 +566,20 @@ void mgx_destroy(mgx_ctx *ctx) {
 
 const char *mgx_last_error(const mgx_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+int32_t mgx_pix2vec(int32_t l, int64_t p, double *v) {
+    if (!v || l < 0 || l > MGX_MAX_LEVEL || p < 0 || p >= hpx_npix(l)) return -1;
+    hpx_pix2vec(l, p, v);
+    return 0;
+}
+
+int64_t mgx_antipode(int32_t l, int64_t p) {
+    if (l < 0 || l > MGX_MAX_LEVEL || p < 0 || p >= hpx_npix(l)) return -1;
+    double v[3];
+    hpx_pix2vec(l, p, v);
+    const double w[3] = {-v[0], -v[1], -v[2]};
+    return hpx_vec2pix(l, w);
+}
+
 int64_t mgx_rayset_npairs(int32_t l_min, int32_t l_max) {
     if (l_min < 0 || l_max < l_min || l_max > MGX_MAX_LEVEL) return -1;
     if (l_min < l_max && l_max > MGX_MAX_ADAPT_LEVEL) return -1;
@@ -934,6 +948,75 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
         *n_kept = k;
     }
     return MGX_OK;
+}
+
+mgx_status mgx_solve_u(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, int64_t o_begin, int64_t o_end,
+                       double *u_out) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "solve_u: no model %d", model);
+    if (!p || !u_out) return fail(ctx, MGX_EINVAL, "solve_u: null params or output");
+    if (!m->has_lines || !m->has_rays) return fail(ctx, MGX_ESTATE, "solve_u: set_lines / set_rays not called");
+    if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0) || !std::isfinite(p->dv_max) || !std::isfinite(p->I_bdy))
+        return fail(ctx, MGX_EINVAL, "solve_u: dtau_max must be > 0, dv_max and I_bdy finite");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_u: unknown precision");
+    if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
+        return fail(ctx, MGX_EINVAL, "solve_u: order must be 0, 2 or 4 (reserved 0)");
+    if (o_begin < 0 || o_end > m->n || o_begin > o_end) return fail(ctx, MGX_EINVAL, "solve_u: bad origin range");
+    if (o_begin == o_end) return MGX_OK;
+    DeviceGuard g(ctx->device);
+    const int32_t o0 = int32_t(o_begin), o1 = int32_t(o_end), np = m->npairs;
+    const int64_t n_half = int64_t(o1 - o0) * np * 2, NB = int64_t(m->L) * m->F;
+    int64_t *offs = nullptr;
+    mgx_status s = trace_offsets(ctx, *m, o0, o1, &offs);
+    if (s != MGX_OK) return s;
+    int64_t total = 0;
+    CK(cudaMemcpyAsync(&total, offs + n_half, sizeof total, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_status(ctx);
+    if (s != MGX_OK || total > int64_t(ctx->arena_budget / sizeof(int32_t))) {
+        dfree(ctx, offs);
+        return s != MGX_OK ? s : fail(ctx, MGX_ERANGE, "solve_u: traced lists of the range exceed the arena");
+    }
+    const size_t n_u = size_t(o1 - o0) * size_t(np) * size_t(NB);
+    int32_t *aidx = nullptr;
+    double *J = nullptr, *u = nullptr;
+    CK(dalloc(ctx, &aidx, size_t(std::max<int64_t>(total, 1))));
+    CK(dalloc(ctx, &J, size_t(m->n) * size_t(NB)));  // the kernel indexes J by absolute origin
+    if (p->out_on_device) u = u_out;
+    else CK(dalloc(ctx, &u, n_u));
+    const DevMesh dm = mesh_view(*m);
+    const DevRays dr = rays_view(ctx, *m);
+    launch_trace_emit(dm, dr, o0, o1, offs, 0, total, aidx, nullptr, nullptr, ctx->d_status, ctx->stream);
+    SolveArgs a;
+    a.dtau_max = p->dtau_max;
+    a.dv_max = p->dv_max;
+    a.I_bdy = p->I_bdy;
+    a.o_begin = o0;
+    a.o_end = o1;
+    {
+        const int64_t per = 32 * solve_bins_per_lane(p->precision, int32_t(NB));
+        a.n_tiles = int32_t((NB + per - 1) / per);
+    }
+    a.offs = offs;
+    a.base = 0;
+    a.idx = aidx;
+    a.J = J;
+    a.u_out = u;
+    a.status = ctx->d_status;
+    a.counters = nullptr;
+    fill_pair_weights(a);
+    {
+        Timed t(ctx, MGX_K_SOLVE);
+        launch_solve(dm, lines_view(*m), dr, a, p->precision, p->order == 4 ? 4 : 2, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    if (!p->out_on_device) CK(cudaMemcpyAsync(u_out, u, n_u * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    dfree(ctx, aidx);
+    dfree(ctx, J);
+    dfree(ctx, offs);
+    if (!p->out_on_device) dfree(ctx, u);
+    return sync_status(ctx);
 }
 
 mgx_status mgx_analytic_mesh(mgx_ctx *ctx, int32_t nx, int32_t ny, int32_t nz, const double *f, double h,

@@ -78,6 +78,7 @@ struct SolveArgs {
     int32_t pad = 0;
     const int64_t *lens = nullptr;  // padded: half-ray lengths
     const int32_t *tail = nullptr;  // padded: entries beyond the row
+    double *u_out = nullptr;        // optional: u per (origin - o_begin, pair, bin)
     double *J;                // [n][L*F]
     int *status;
     unsigned long long *counters;  // nullable: [0] elimination updates, [1] optics samples,

@@ -1,0 +1,135 @@
+"""Experiments of Section 3 on the synthetic workloads, built from the library's
+entry points (no arithmetic of the method here, only bookkeeping and statistics).
+
+* `adaptive_vs_dense` -- Section 3.2 (Figs. 7-9): the adaptive ray set
+  (levels l_min -> l_max, 552 rays for 1 -> 4) against the dense set of level
+  l_max (3072 rays for 4).  Each adaptive ray stands for the dense rays inside
+  its pixel; its error is the relative difference between its u and the mean u
+  of those dense rays, averaged over the bins above 1e-6 of the point's
+  maximum.  Rays at l_max are dense rays themselves (error 0).
+* `reduction_speedup` -- Table 2 (Section 3.2): original against reduced
+  mesh, the reduction factor, the speed-up of the J solve and the error of the
+  reduced J mapped back to the original points (Section 3.2.1).
+
+`python -m paper_2011_14998_gb300.experiments rays|reduction` runs them on the
+synthetic stand-ins and prints one JSON line each.
+"""
+from __future__ import annotations
+
+import json
+import sys
+import time
+
+import numpy as np
+
+from . import MGX_FP32, MGX_FP64, mgx_antipode
+
+
+def _dense_columns(rays_dense_row: np.ndarray, lmax: int) -> np.ndarray:
+    """Column of the dense pair that contains each pixel of level lmax."""
+    col = {int(r & 0x0FFFFFFF): c for c, r in enumerate(rays_dense_row)}
+    npix = 12 * 4 ** lmax
+    out = np.empty(npix, np.int64)
+    for q in range(npix):
+        out[q] = col[q] if q in col else col[mgx_antipode(lmax, q)]
+    return out
+
+
+def adaptive_vs_dense(ctx, m: dict, origins, l_min=1, l_max=4, precision=MGX_FP64, floor=1e-6):
+    """Per-ray errors of the adaptive set against the dense set at the given origins."""
+    mid_a = ctx.load(m, l_min=l_min, l_max=l_max)
+    mid_d = ctx.load(m, l_min=l_max, l_max=l_max)
+    try:
+        ra, rd = ctx.rays(mid_a), ctx.rays(mid_d)
+        cols = _dense_columns(rd[0], l_max)
+        errs, levels, ja, jd = [], [], [], []
+        for o in origins:
+            ua = ctx.solve_u(mid_a, int(o), int(o) + 1, precision=precision)[0]
+            ud = ctx.solve_u(mid_d, int(o), int(o) + 1, precision=precision)[0]
+            lev = (ra[o] >> 28).astype(np.int64)
+            pix = (ra[o] & 0x0FFFFFFF).astype(np.int64)
+            wa = 2.0 / (12.0 * 4.0 ** lev)
+            ja.append((wa[:, None] * ua).sum(0))
+            jd.append((2.0 / (12.0 * 4.0 ** l_max)) * ud.sum(0))
+            mask = ja[-1] > floor * ja[-1].max()
+            for p in range(len(pix)):
+                k = 4 ** (l_max - lev[p])
+                desc = pix[p] * k + np.arange(k)
+                ref = ud[cols[desc]].mean(0)
+                rel = np.abs(ua[p] - ref)[mask] / np.abs(ref[mask])
+                errs.append(rel.mean())
+                levels.append(lev[p])
+        errs, levels = np.array(errs), np.array(levels)
+        ja, jd = np.array(ja), np.array(jd)
+        mj = jd > floor * jd.max(axis=1, keepdims=True)
+        return dict(n_origins=len(origins), rays_adaptive=2 * ra.shape[1], rays_dense=2 * rd.shape[1],
+                    frac_rays_below_10pct=float((errs < 0.1).mean()), frac_rays_below_20pct=float((errs < 0.2).mean()),
+                    frac_rays_below_1e3=float((errs < 1e-3).mean()),
+                    frac_rays_at_finest_level=float((levels == l_max).mean()),
+                    max_err_finest_level=float(errs[levels == l_max].max()) if (levels == l_max).any() else 0.0,
+                    median_ray_err=float(np.median(errs)),
+                    J_rel_err_mean=float((np.abs(ja - jd)[mj] / jd[mj]).mean()),
+                    J_rel_err_max=float((np.abs(ja - jd)[mj] / jd[mj]).max()))
+    finally:
+        ctx.free(mid_a)
+        ctx.free(mid_d)
+
+
+def reduction_speedup(ctx, m: dict, f_small, f_large, G_thres, seed=1, precision=MGX_FP32, reps=3):
+    """Plain reduction of m, solve times on both meshes and the reduced-mesh error (Table 2 shape)."""
+    import torch
+
+    from . import learned
+
+    def timed_solve(model):
+        mid = ctx.load(model)
+        ctx.solve_J(mid, precision=precision)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            J = ctx.solve_J(mid, precision=precision)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        return mid, J, dt
+
+    mid, J_full, t_full = timed_solve(m)
+    keep = ctx.reduce_mesh(mid, m["rho"], f_small, f_large, G_thres, seed)[3]
+    ctx.free(mid)
+    r = learned.remesh(m, keep)
+    mid_r, J_red, t_red = timed_solve(r)
+    ctx.free(mid_r)
+    err = learned.point_errors(J_full, learned.interpolate(r["pos"], J_red, m["pos"]))
+    return dict(n_original=len(m["pos"]), n_reduced=len(r["pos"]), reduction=len(m["pos"]) / len(r["pos"]),
+                t_full_s=t_full, t_reduced_s=t_red, speedup=t_full / t_red, mean_rel_err=float(err.mean()),
+                p90_rel_err=float(np.quantile(err, 0.9)), frac_below_1pct=float((err < 0.01).mean()),
+                frac_below_10pct=float((err < 0.1).mean()))
+
+
+def main(argv):
+    import synth
+
+    from . import Context, build
+
+    build()
+    ctx = Context(0)
+    try:
+        which = argv[1] if len(argv) > 1 else "rays"
+        if which == "rays":
+            m = synth.wind_model(int(argv[2]) if len(argv) > 2 else 50000, seed=2, n_freq=50)
+            o = np.sort(np.random.default_rng(0).choice(len(m["pos"]), 200, replace=False))
+            print(json.dumps(dict(experiment="adaptive_vs_dense", workload=m["name"],
+                                  **adaptive_vs_dense(ctx, m, o))), flush=True)
+        else:
+            n = int(argv[2]) if len(argv) > 2 else 200000
+            cases = [("AMR (clump octree)", synth.octree_model(n, seed=3, n_lines=1, n_freq=50, l_min=2, l_max=2),
+                      (0.90, 2.10, 0.10)),
+                     ("SPH (binary-wind spiral)", synth.spiral_model(n, seed=4, n_freq=50), (1.00, 2.15, 0.21))]
+            for name, m, prm in cases:
+                print(json.dumps(dict(experiment="reduction_speedup", model=name, table1=prm,
+                                      **reduction_speedup(ctx, m, *prm))), flush=True)
+    finally:
+        ctx.close()
+
+
+if __name__ == "__main__":
+    main(sys.argv)

@@ -42,3 +42,21 @@ def test_package_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in src.lower(), f
+
+
+def test_healpix_host_exports_match_oracle(orc):
+    import numpy as np
+
+    import paper_2011_14998_gb300 as mgx
+
+    mgx.build()
+    for l in range(5):
+        for p in range(0, 12 * 4**l, max(1, (12 * 4**l) // 29)):
+            assert mgx.mgx_antipode(l, p) == orc.antipode(l, p)
+            assert np.array_equal(mgx.mgx_pix2vec(l, p), orc.pix2vec(l, p))
+    import pytest
+
+    with pytest.raises(ValueError):
+        mgx.mgx_antipode(9, 0)
+    with pytest.raises(ValueError):
+        mgx.mgx_pix2vec(1, 48)
