@@ -556,10 +556,13 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
 }
 
 // CTAs of 128 threads; the minimum resident CTAs per SM caps the registers
-// (4 CTAs: 128 registers, 3 CTAs: 168) at the largest occupancy without spills.
+// (65536 / (128 x CTAs)).  Measured on GB300 with the persistent solve: more
+// resident warps beat the spills they cost down to 80 registers for one line
+// (6 CTAs: 15 % faster than 4), 96 for two lines (5), 128 for four (4) and
+// 168 for eight (3), where the per-line sample data need the registers.
 template <typename R, int NL, int BPL>
 struct Occ {
-    static constexpr int kMinBlocks = (sizeof(R) == 4 && (NL == 1 || BPL == 1)) ? 4 : (sizeof(R) == 4 ? 3 : 1);
+    static constexpr int kMinBlocks = sizeof(R) == 8 ? 1 : (NL == 1 ? 6 : NL == 2 ? 5 : NL == 4 ? 4 : 3);
 };
 
 // J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
