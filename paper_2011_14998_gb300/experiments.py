@@ -10,9 +10,13 @@ entry points (no arithmetic of the method here, only bookkeeping and statistics)
 * `reduction_speedup` -- Table 2 (Section 3.2): original against reduced
   mesh, the reduction factor, the speed-up of the J solve and the error of the
   reduced J mapped back to the original points (Section 3.2.1).
+* `learned_vs_plain` -- the learned reduction against the plain criterion at
+  one kept fraction: the network is trained on plain reductions of training
+  seeds; the plain criterion's factors are scaled until it keeps the target
+  fraction of the test mesh, and the network keeps as many points.
 
-`python -m paper_2011_14998_gb300.experiments rays|reduction` runs them on the
-synthetic stand-ins and prints one JSON line each.
+`python -m paper_2011_14998_gb300.experiments rays|reduction|learned` runs them
+on the synthetic stand-ins and prints one JSON line each.
 """
 from __future__ import annotations
 
@@ -105,6 +109,50 @@ def reduction_speedup(ctx, m: dict, f_small, f_large, G_thres, seed=1, precision
                 frac_below_10pct=float((err < 0.1).mean()))
 
 
+def learned_vs_plain(ctx, make_model, train_seeds, test_seed, table1, keep_fraction=0.2,
+                     scales=(1.0, 1.5, 2.2), epochs=60, seed=11):
+    """Reduced-mesh error of the learned and the plain criterion at one kept fraction."""
+    from . import learned
+
+    f_small, f_large, g_thres = table1
+    Xs, ys = [], []
+    for s_ in train_seeds:
+        m = make_model(s_)
+        reds = [(f_small * k, f_large * k, g_thres, 1000 + 10 * s_ + j) for j, k in enumerate(scales)]
+        X, y = learned.training_samples(ctx, m, reds)
+        Xs.append(X)
+        ys.append(y)
+    X, y = np.concatenate(Xs), np.concatenate(ys)
+    std, losses, _ = learned.train_network(ctx, X, y, epochs=epochs, seed=1)
+    test = make_model(test_seed)
+    mid = ctx.load(test)
+    try:
+        J_full = ctx.solve_J(mid, precision=MGX_FP32)
+        lo, hi = 0.25, 16.0  # scale of both factors; the kept fraction falls as it grows
+        for _ in range(40):
+            k = np.sqrt(lo * hi)
+            keep = ctx.reduce_mesh(mid, test["rho"], f_small * k, f_large * k, g_thres, seed)[3]
+            if keep.mean() > keep_fraction:
+                lo = k
+            else:
+                hi = k
+            if hi / lo < 1.001:
+                break
+        keep_plain = ctx.reduce_mesh(mid, test["rho"], f_small * hi, f_large * hi, g_thres, seed)[3]
+        keep_mlp = learned.reduce_learned(ctx, mid, test, std, float(keep_plain.mean()))
+    finally:
+        ctx.free(mid)
+    e_plain = learned.reduction_error(ctx, test, J_full, keep_plain)
+    e_mlp = learned.reduction_error(ctx, test, J_full, keep_mlp)
+    return dict(n=len(test["pos"]), kept_fraction=float(keep_plain.mean()),
+                reduction=float(1.0 / keep_plain.mean()), plain_scale=float(hi), train_samples=int(len(y)),
+                loss_first=float(losses[0]), loss_last=float(losses[-1]),
+                mean_rel_err_plain=float(e_plain.mean()), mean_rel_err_learned=float(e_mlp.mean()),
+                p90_plain=float(np.quantile(e_plain, 0.9)), p90_learned=float(np.quantile(e_mlp, 0.9)),
+                frac_below_1pct_plain=float((e_plain < 0.01).mean()),
+                frac_below_1pct_learned=float((e_mlp < 0.01).mean()))
+
+
 def main(argv):
     import synth
 
@@ -119,6 +167,21 @@ def main(argv):
             o = np.sort(np.random.default_rng(0).choice(len(m["pos"]), 200, replace=False))
             print(json.dumps(dict(experiment="adaptive_vs_dense", workload=m["name"],
                                   **adaptive_vs_dense(ctx, m, o))), flush=True)
+        elif which == "learned":
+            n = int(argv[2]) if len(argv) > 2 else 20000
+
+            def octree(s_):
+                return synth.octree_model(n, seed=s_, hi_level=7, n_lines=1, n_freq=20, l_min=1, l_max=1)
+
+            def spiral(s_):
+                return synth.spiral_model(n, seed=s_, n_freq=20, level=1)
+
+            for name, mk, t1, test_seed in (("AMR (clump octree)", octree, (0.90, 2.10, 0.10), 3),
+                                            ("SPH (binary-wind spiral)", spiral, (1.00, 2.15, 0.21), 4)):
+                for frac in (0.2, 0.1):
+                    print(json.dumps(dict(experiment="learned_vs_plain", model=name, table1=t1,
+                                          **learned_vs_plain(ctx, mk, (100, 101, 102, 103), test_seed, t1,
+                                                             keep_fraction=frac))), flush=True)
         else:
             n = int(argv[2]) if len(argv) > 2 else 200000
             cases = [("AMR (clump octree)", synth.octree_model(n, seed=3, n_lines=1, n_freq=50, l_min=2, l_max=2),
