@@ -366,10 +366,11 @@ def run_mgx(args):
     arena_bytes = prof32["trace_points"] * 12 * ((NB + 31) // 32) + n * NB * 8  # point lists per tile + J
     hbm_gbs = arena_bytes / max(1, prof32["launches"]["solve"]) / (ms_solve * 1e-3) / 1e9
     step_ms = {k: v / kb for k, v in prof32["ms"].items()}
-    # own kernels per step: ray sets, padded trace, tail trace, the three work-list kernels, the solve
-    # (the scan is CUB's)
+    # own kernels per step: ray sets, padded trace, tail trace, the work-list kernels (three for the
+    # cost-binned schedule, one for plain order), the solve (scans and the sort are CUB's)
     lp = prof32["launches"]
-    launches = args.steps * (lp["rays"] + lp["trace_count"] + lp["trace_emit"] + 3 * lp["other"] + lp["solve"]) // kb
+    wl = 3 if tuning.get("schedule", 0) == 0 else 1
+    launches = args.steps * (lp["rays"] + lp["trace_count"] + lp["trace_emit"] + wl * lp["other"] + lp["solve"]) // kb
     traffic = solve_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -259,7 +259,9 @@ typedef struct {
                                   what fits) */
     int32_t tail_permille;     /* row width of the traced lists: the narrowest power of two leaving at most this
                                   share of the points (per mille) to the overflow pass; 0 = 20, else 1..1000 */
-    int32_t reserved;          /* 0 */
+    int32_t schedule;          /* order of the persistent solve's work list: 0, items binned by log2 of
+                                  their traced length, longest bin first; 1, plain (model, origin,
+                                  tile) order (for comparison) */
 } mgx_tuning;
 
 /* Set (NULL: reset to automatic) or read the context's tuning; out-of-range
@@ -276,7 +278,7 @@ typedef struct {
 /* Autotuner of the batched solve: times candidate tunings of
  * mgx_solve_J_batch(ctx, models, n_models, params, J_out, flags) by coordinate
  * descent (bins per lane 1/2 in single precision, tracer CTAs per SM 4/6/8,
- * tail share 5/20/80 per mille), each candidate planned once and then run
+ * tail share 5/20/80 per mille, work-list schedule 0/1), each candidate planned once and then run
  * `reps` times (1..100), and leaves the fastest as the context's tuning.
  * J_out receives the solution of the chosen tuning.  trials
  * [max_trials] (may be NULL) receives the timed candidates in order, *n_trials

@@ -55,10 +55,10 @@ class Profile(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("bins_per_lane", C.c_int32), ("trace_ctas_per_sm", C.c_int32), ("tail_permille", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("schedule", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "reserved"}
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class TuneTrial(C.Structure):

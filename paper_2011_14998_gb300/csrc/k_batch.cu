@@ -7,8 +7,13 @@
 // that cost and the (model, origin, tile) items are laid out bin by bin,
 // longest bin first, so that the persistent warps start the longest items
 // first and the end of the launch is not held up by one long straggler.
-// The order within a bin follows atomics and does not affect any result:
-// every item writes only its own J entries.
+// The binning is a stable radix sort of the origins by bin, so within a bin
+// the items keep ascending (model, origin) order and neighbouring origins,
+// whose traced points overlap, stay together for the cache.  No order affects
+// a result: every item writes only its own J entries.
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+
 #include "mgx_internal.cuh"
 
 namespace mgx {
@@ -43,35 +48,36 @@ __device__ __forceinline__ int64_t origin_cost(const BatchGeom &g, int64_t o, co
     return cost;
 }
 
-__global__ void k_cost_hist(const BatchGeom *__restrict__ geo, const int64_t *__restrict__ origin_base,
+// Key (cost bin) and value (global origin) of every origin for the stable sort.
+__global__ void k_cost_keys(const BatchGeom *__restrict__ geo, const int64_t *__restrict__ origin_base,
                             int32_t n_models, int64_t n_origins, const int64_t *__restrict__ lens,
-                            unsigned long long *__restrict__ hist) {
+                            uint8_t *__restrict__ key, int32_t *__restrict__ val) {
     const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (g >= n_origins) return;
     const int32_t k = model_of(origin_base, n_models, g);
-    const int64_t cost = origin_cost(geo[k], g - origin_base[k], lens);
-    atomicAdd(&hist[cost_bin(cost)], (unsigned long long)geo[k].n_tiles);
+    key[g] = uint8_t(cost_bin(origin_cost(geo[k], g - origin_base[k], lens)));
+    val[g] = int32_t(g);
 }
 
-__global__ void k_cost_scan(unsigned long long *__restrict__ hist, unsigned long long *__restrict__ cursor) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    unsigned long long run = 0;
-    for (int b = 0; b < kBins; ++b) {
-        cursor[b] = run;
-        run += hist[b];
-    }
+// Work items of the s-th origin in sorted order.
+__global__ void k_sorted_tiles(const BatchGeom *__restrict__ geo, const int64_t *__restrict__ origin_base,
+                               int32_t n_models, int64_t n_origins, const int32_t *__restrict__ val,
+                               int64_t *__restrict__ tiles) {
+    const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (s >= n_origins) return;
+    tiles[s] = geo[model_of(origin_base, n_models, val[s])].n_tiles;
 }
 
-__global__ void k_cost_scatter(const BatchGeom *__restrict__ geo, const int64_t *__restrict__ origin_base,
-                               int32_t n_models, int64_t n_origins, const int64_t *__restrict__ lens,
-                               unsigned long long *__restrict__ cursor, uint2 *__restrict__ work) {
-    const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    if (g >= n_origins) return;
+__global__ void k_emit_items(const BatchGeom *__restrict__ geo, const int64_t *__restrict__ origin_base,
+                             int32_t n_models, int64_t n_origins, const int32_t *__restrict__ val,
+                             const int64_t *__restrict__ toff, uint2 *__restrict__ work) {
+    const int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (s >= n_origins) return;
+    const int64_t g = val[s];
     const int32_t k = model_of(origin_base, n_models, g);
     const int64_t o = g - origin_base[k];
-    const int64_t cost = origin_cost(geo[k], o, lens);
     const int32_t nt = geo[k].n_tiles;
-    const unsigned long long pos = atomicAdd(&cursor[cost_bin(cost)], (unsigned long long)nt);
+    const int64_t pos = s == 0 ? 0 : toff[s - 1];
     for (int32_t t = 0; t < nt; ++t) work[pos + t] = make_uint2((uint32_t(k) << 16) | uint32_t(t), uint32_t(o));
 }
 
@@ -97,6 +103,19 @@ __global__ void k_excess_totals(const int64_t *__restrict__ lens, int64_t n, uns
     }
 }
 
+// Plain order (for comparison with the cost bins): item (model k, origin o,
+// tile t) at work_base[k] + o n_tiles[k] + t.
+__global__ void k_work_natural(const BatchGeom *__restrict__ geo, const int64_t *__restrict__ origin_base,
+                               int32_t n_models, int64_t n_origins, uint2 *__restrict__ work) {
+    const int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    if (g >= n_origins) return;
+    const int32_t k = model_of(origin_base, n_models, g);
+    const int64_t o = g - origin_base[k];
+    const int32_t nt = geo[k].n_tiles;
+    const int64_t pos = geo[k].work_base + o * nt;
+    for (int32_t t = 0; t < nt; ++t) work[pos + t] = make_uint2((uint32_t(k) << 16) | uint32_t(t), uint32_t(o));
+}
+
 }  // namespace
 
 void launch_excess_totals(const int64_t *lens, int64_t n, unsigned long long *out, cudaStream_t st) {
@@ -107,15 +126,31 @@ void launch_excess_totals(const int64_t *lens, int64_t n, unsigned long long *ou
     k_excess_totals<<<unsigned(grid), 256, 0, st>>>(lens, n, out);
 }
 
+size_t batch_worklist_temp_bytes(int64_t n_origins) {
+    size_t a = 0, b = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, a, (const uint8_t *)nullptr, (uint8_t *)nullptr,
+                                    (const int32_t *)nullptr, (int32_t *)nullptr, int(n_origins), 0, 5);
+    cub::DeviceScan::InclusiveSum(nullptr, b, (const int64_t *)nullptr, (int64_t *)nullptr, int(n_origins));
+    return a > b ? a : b;
+}
+
 void launch_batch_worklist(const BatchGeom *geo, const int64_t *origin_base, int32_t n_models, int64_t n_origins,
-                           const int64_t *lens, unsigned long long *scratch64, uint2 *work, cudaStream_t st) {
-    unsigned long long *hist = scratch64, *cursor = scratch64 + kBins;
-    cudaMemsetAsync(hist, 0, kBins * sizeof(unsigned long long), st);
+                           const int64_t *lens, const WorkListBufs &b, uint2 *work, bool natural, cudaStream_t st) {
     const int tb = 256;
     const unsigned grid = unsigned((n_origins + tb - 1) / tb);
-    k_cost_hist<<<grid, tb, 0, st>>>(geo, origin_base, n_models, n_origins, lens, hist);
-    k_cost_scan<<<1, 32, 0, st>>>(hist, cursor);
-    k_cost_scatter<<<grid, tb, 0, st>>>(geo, origin_base, n_models, n_origins, lens, cursor, work);
+    if (n_origins == 0) return;
+    if (natural) {
+        k_work_natural<<<grid, tb, 0, st>>>(geo, origin_base, n_models, n_origins, work);
+        return;
+    }
+    k_cost_keys<<<grid, tb, 0, st>>>(geo, origin_base, n_models, n_origins, lens, b.key_in, b.val_in);
+    size_t bytes = b.tmp_bytes;
+    cub::DeviceRadixSort::SortPairs(b.tmp, bytes, b.key_in, b.key_out, b.val_in, b.val_out, int(n_origins), 0, 5,
+                                    st);
+    k_sorted_tiles<<<grid, tb, 0, st>>>(geo, origin_base, n_models, n_origins, b.val_out, b.tiles);
+    bytes = b.tmp_bytes;
+    cub::DeviceScan::InclusiveSum(b.tmp, bytes, b.tiles, b.toff, int(n_origins), st);
+    k_emit_items<<<grid, tb, 0, st>>>(geo, origin_base, n_models, n_origins, b.val_out, b.toff, work);
 }
 
 }  // namespace mgx

@@ -66,7 +66,8 @@ struct BatchPlan {
     BatchGeom *geo = nullptr;
     BatchSlot *slots = nullptr;
     uint2 *work = nullptr;
-    unsigned long long *scratch = nullptr;  // 64 work-list counters, the queue counter, row-width totals
+    unsigned long long *scratch = nullptr;  // the queue counter, row-width totals
+    WorkListBufs wl;
     void *cub_tmp = nullptr;
     size_t cub_bytes = 0;
     cudaGraph_t graph = nullptr;
@@ -402,6 +403,14 @@ void free_plan(mgx_ctx *ctx, BatchPlan &pl) {
     dfree(ctx, pl.slots);
     dfree(ctx, pl.work);
     dfree(ctx, pl.scratch);
+    dfree(ctx, pl.wl.key_in);
+    dfree(ctx, pl.wl.key_out);
+    dfree(ctx, pl.wl.val_in);
+    dfree(ctx, pl.wl.val_out);
+    dfree(ctx, pl.wl.tiles);
+    dfree(ctx, pl.wl.toff);
+    if (pl.wl.tmp) cudaFreeAsync(pl.wl.tmp, ctx->stream);
+    pl.wl = WorkListBufs{};
     if (pl.cub_tmp) cudaFreeAsync(pl.cub_tmp, ctx->stream);
     pl.cub_tmp = nullptr;
     pl.valid = false;
@@ -419,8 +428,8 @@ void enqueue_rays(mgx_ctx *ctx, Model &m, bool timed = true) {
     }
 }
 
-constexpr int kScratchQueue = 64;   // the persistent solve's work counter
-constexpr int kScratchTotals = 72;  // kPadCandidates + 1 row-width totals
+constexpr int kScratchQueue = 0;   // the persistent solve's work counter
+constexpr int kScratchTotals = 8;  // kPadCandidates + 1 row-width totals
 constexpr int kScratchSize = kScratchTotals + kPadCandidates + 1;
 
 // One step of a batched solve: (ray sets,) padded trace, tail offsets, tail
@@ -454,8 +463,8 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
     }
     {
         Timed t(ctx, MGX_K_OTHER);
-        launch_batch_worklist(pl.geo, pl.obase, int32_t(ms.size()), pl.n_origins, pl.lens, pl.scratch, pl.work,
-                              ctx->stream);
+        launch_batch_worklist(pl.geo, pl.obase, int32_t(ms.size()), pl.n_origins, pl.lens, pl.wl, pl.work,
+                              pl.tune.schedule == 1, ctx->stream);
     }
     CK(cudaMemsetAsync(pl.scratch + kScratchQueue, 0, sizeof(unsigned long long), ctx->stream));
     {
@@ -483,12 +492,12 @@ int32_t choose_pad(const unsigned long long *tot, int64_t total_half, size_t bud
 
 bool same_tuning(const mgx_tuning &a, const mgx_tuning &b) {
     return a.bins_per_lane == b.bins_per_lane && a.trace_ctas_per_sm == b.trace_ctas_per_sm &&
-           a.tail_permille == b.tail_permille;
+           a.tail_permille == b.tail_permille && a.schedule == b.schedule;
 }
 
 bool valid_tuning(const mgx_tuning &t) {
     return t.bins_per_lane >= 0 && t.bins_per_lane <= 2 && t.trace_ctas_per_sm >= 0 && t.trace_ctas_per_sm <= 32 &&
-           t.tail_permille >= 0 && t.tail_permille <= 1000 && t.reserved == 0;
+           t.tail_permille >= 0 && t.tail_permille <= 1000 && (t.schedule == 0 || t.schedule == 1);
 }
 
 bool plan_matches(const BatchPlan &pl, const int32_t *models, int32_t n, const mgx_solve_params *p,
@@ -1156,6 +1165,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         obase[size_t(k)] = pl.n_origins;
         pl.total_half += int64_t(m.n) * m.npairs * 2;
         pl.n_origins += m.n;
+        geo[size_t(k)].work_base = pl.n_work;
         pl.n_work += int64_t(m.n) * geo[size_t(k)].n_tiles;
         if (geo[size_t(k)].n_tiles > 65535) return fail(ctx, MGX_ERANGE, "solve_J_batch: too many frequency tiles");
     }
@@ -1168,6 +1178,15 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     CK(dalloc(ctx, &pl.slots, size_t(n_models)));
     CK(dalloc(ctx, &pl.work, size_t(pl.n_work)));
     CK(dalloc(ctx, &pl.scratch, kScratchSize));
+    if (pl.n_origins > int64_t(INT32_MAX)) return fail(ctx, MGX_ERANGE, "solve_J_batch: more than 2^31 origins");
+    CK(dalloc(ctx, &pl.wl.key_in, size_t(pl.n_origins)));
+    CK(dalloc(ctx, &pl.wl.key_out, size_t(pl.n_origins)));
+    CK(dalloc(ctx, &pl.wl.val_in, size_t(pl.n_origins)));
+    CK(dalloc(ctx, &pl.wl.val_out, size_t(pl.n_origins)));
+    CK(dalloc(ctx, &pl.wl.tiles, size_t(pl.n_origins)));
+    CK(dalloc(ctx, &pl.wl.toff, size_t(pl.n_origins)));
+    pl.wl.tmp_bytes = batch_worklist_temp_bytes(pl.n_origins);
+    CK(cudaMallocAsync(&pl.wl.tmp, pl.wl.tmp_bytes ? pl.wl.tmp_bytes : 1, ctx->stream));
     CK(cub::DeviceScan::InclusiveSum(nullptr, pl.cub_bytes, pl.excess, pl.offs + 1, pl.total_half, ctx->stream));
     CK(cudaMallocAsync(&pl.cub_tmp, pl.cub_bytes ? pl.cub_bytes : 1, ctx->stream));
     CK(cudaMemcpyAsync(pl.geo, geo.data(), geo.size() * sizeof(BatchGeom), cudaMemcpyHostToDevice, ctx->stream));
@@ -1347,15 +1366,16 @@ mgx_status mgx_autotune(mgx_ctx *ctx, const int32_t *models, int32_t n_models, c
     if (best.tail_permille == 0) best.tail_permille = 20;
     double best_ms = 0.0;
     mgx_status s = time_one(best, &best_ms);
-    const int32_t bpl_c[] = {1, 2}, trace_c[] = {4, 6, 8}, tail_c[] = {5, 20, 80};
-    for (int dim = 0; dim < 3 && s == MGX_OK; ++dim) {
+    const int32_t bpl_c[] = {1, 2}, trace_c[] = {4, 6, 8}, tail_c[] = {5, 20, 80}, sched_c[] = {0, 1};
+    for (int dim = 0; dim < 4 && s == MGX_OK; ++dim) {
         if (dim == 0 && p->precision != MGX_FP32) continue;
-        const int32_t *cand = dim == 0 ? bpl_c : dim == 1 ? trace_c : tail_c;
-        const int nc = dim == 0 ? 2 : 3;
+        const int32_t *cand = dim == 0 ? bpl_c : dim == 1 ? trace_c : dim == 2 ? tail_c : sched_c;
+        const int nc = (dim == 0 || dim == 3) ? 2 : 3;
         const mgx_tuning base = best;
         for (int c = 0; c < nc && s == MGX_OK; ++c) {
             mgx_tuning t = base;
-            int32_t &field = dim == 0 ? t.bins_per_lane : dim == 1 ? t.trace_ctas_per_sm : t.tail_permille;
+            int32_t &field = dim == 0 ? t.bins_per_lane : dim == 1 ? t.trace_ctas_per_sm
+                           : dim == 2 ? t.tail_permille : t.schedule;
             if (field == cand[c]) continue;
             field = cand[c];
             double ms = 0.0;

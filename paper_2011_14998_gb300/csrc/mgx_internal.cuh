@@ -143,12 +143,25 @@ struct BatchGeom {
     int64_t half_base;
     int32_t npairs2;
     int32_t n_tiles;
+    int64_t work_base;  // first work item of the model in plain order
 };
 
-// ---- batched work list (k_batch.cu); scratch64 holds 64 counters
+// ---- batched work list (k_batch.cu)
 // Work list from the half-ray lengths lens (all models' half-rays, in order).
+// Buffers of the cost-binned work list: sort keys and values [n_origins] (in
+// and out), item counts and their inclusive prefix sums [n_origins], CUB
+// temporary storage of batch_worklist_temp_bytes(n_origins) bytes.
+struct WorkListBufs {
+    uint8_t *key_in = nullptr, *key_out = nullptr;
+    int32_t *val_in = nullptr, *val_out = nullptr;
+    int64_t *tiles = nullptr, *toff = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+};
+size_t batch_worklist_temp_bytes(int64_t n_origins);
+// (natural: plain (model, origin, tile) order instead of the cost bins)
 void launch_batch_worklist(const BatchGeom *geo, const int64_t *origin_base, int32_t n_models, int64_t n_origins,
-                           const int64_t *lens, unsigned long long *scratch64, uint2 *work, cudaStream_t st);
+                           const int64_t *lens, const WorkListBufs &b, uint2 *work, bool natural, cudaStream_t st);
 // Row widths 2^j (j < kPadCandidates) considered for the padded layout:
 // out[j] = sum over half-rays of max(0, len - 2^j), out[kPadCandidates] = sum of len.
 constexpr int kPadCandidates = 11;

@@ -10,12 +10,15 @@ entry points (no arithmetic of the method here, only bookkeeping and statistics)
 * `reduction_speedup` -- Table 2 (Section 3.2): original against reduced
   mesh, the reduction factor, the speed-up of the J solve and the error of the
   reduced J mapped back to the original points (Section 3.2.1).
+* `batch_schedule` -- the batched persistent solve (one launch over many
+  models) with its work list binned by traced length, longest first, against
+  the same list in plain (model, origin, tile) order.
 * `learned_vs_plain` -- the learned reduction against the plain criterion at
   one kept fraction: the network is trained on plain reductions of training
   seeds; the plain criterion's factors are scaled until it keeps the target
   fraction of the test mesh, and the network keeps as many points.
 
-`python -m paper_2011_14998_gb300.experiments rays|reduction|learned` runs them
+`python -m paper_2011_14998_gb300.experiments rays|reduction|learned|batch` runs them
 on the synthetic stand-ins and prints one JSON line each.
 """
 from __future__ import annotations
@@ -109,6 +112,42 @@ def reduction_speedup(ctx, m: dict, f_small, f_large, G_thres, seed=1, precision
                 frac_below_10pct=float((err < 0.1).mean()))
 
 
+def batch_schedule(ctx, models, precision=MGX_FP32, reps=3):
+    """Step time of one batched solve over `models` with the cost-binned and the plain work list."""
+    import torch
+
+    from . import MGX_BATCH_GRAPH, MGX_BATCH_RAYS
+
+    mids = [ctx.load(m) for m in models]
+    saved = ctx.tuning()
+    out = dict(n_models=len(models), points=int(sum(len(m["pos"]) for m in models)))
+    try:
+        solves = 0
+        for mid, m in zip(mids, models):
+            solves += ctx.models[mid]["n"] * ctx.models[mid]["npairs"] * ctx.models[mid]["L"] * ctx.models[mid]["F"]
+        out["solves_per_step"] = int(solves)
+        outs = None
+        for name, sched in (("binned", 0), ("plain", 1)):
+            ctx.set_tuning(dict(saved, schedule=sched))
+            flags = MGX_BATCH_GRAPH | MGX_BATCH_RAYS
+            outs = ctx.solve_J_batch(mids, precision=precision, outs=outs, flags=flags)
+            ctx.solve_J_batch(mids, precision=precision, outs=outs, flags=flags)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                ctx.solve_J_batch(mids, precision=precision, outs=outs, flags=flags)
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / reps
+            out[f"step_s_{name}"] = dt
+            out[f"solves_per_s_{name}"] = solves / dt
+        out["binned_speedup"] = out["step_s_plain"] / out["step_s_binned"]
+    finally:
+        ctx.set_tuning(saved)
+        for k in mids:
+            ctx.free(k)
+    return out
+
+
 def learned_vs_plain(ctx, make_model, train_seeds, test_seed, table1, keep_fraction=0.2,
                      scales=(1.0, 1.5, 2.2), epochs=60, seed=11):
     """Reduced-mesh error of the learned and the plain criterion at one kept fraction."""
@@ -167,6 +206,11 @@ def main(argv):
             o = np.sort(np.random.default_rng(0).choice(len(m["pos"]), 200, replace=False))
             print(json.dumps(dict(experiment="adaptive_vs_dense", workload=m["name"],
                                   **adaptive_vs_dense(ctx, m, o))), flush=True)
+        elif which == "batch":
+            k = int(argv[2]) if len(argv) > 2 else 16
+            models = synth.batch_models(n_models=k, seed=5, n_min=10_000, n_max=50_000, n_lines=2, n_freq=50)
+            print(json.dumps(dict(experiment="batch_schedule", lines=2, bins_per_line=50, rays="adaptive l 0-3",
+                                  **batch_schedule(ctx, models))), flush=True)
         elif which == "learned":
             n = int(argv[2]) if len(argv) > 2 else 20000
 
