@@ -148,6 +148,35 @@ def batch_schedule(ctx, models, precision=MGX_FP32, reps=3):
     return out
 
 
+def batch_throughput(ctx, models, precision=MGX_FP32, reps=1):
+    """Aggregate solves/s of one graph-replayed batched step over all `models`
+    (one persistent launch), with the planning and first eager step timed apart."""
+    import torch
+
+    from . import MGX_BATCH_GRAPH, MGX_BATCH_RAYS
+
+    mids = [ctx.load(m) for m in models]
+    try:
+        solves = sum(ctx.models[k]["n"] * ctx.models[k]["npairs"] * ctx.models[k]["L"] * ctx.models[k]["F"]
+                     for k in mids)
+        flags = MGX_BATCH_GRAPH | MGX_BATCH_RAYS
+        t0 = time.perf_counter()
+        outs = ctx.solve_J_batch(mids, precision=precision, flags=flags)  # plan, eager step, capture
+        torch.cuda.synchronize()
+        t_plan = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.solve_J_batch(mids, precision=precision, outs=outs, flags=flags)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        ok = all(bool(torch.isfinite(o).all()) for o in outs)
+    finally:
+        for k in mids:
+            ctx.free(k)
+    return dict(n_models=len(models), points=int(sum(len(m["pos"]) for m in models)), solves_per_step=int(solves),
+                plan_and_first_step_s=t_plan, step_s=dt, solves_per_s=solves / dt, all_finite=ok)
+
+
 def learned_vs_plain(ctx, make_model, train_seeds, test_seed, table1, keep_fraction=0.2,
                      scales=(1.0, 1.5, 2.2), epochs=60, seed=11):
     """Reduced-mesh error of the learned and the plain criterion at one kept fraction."""
@@ -211,6 +240,14 @@ def main(argv):
             models = synth.batch_models(n_models=k, seed=5, n_min=10_000, n_max=50_000, n_lines=2, n_freq=50)
             print(json.dumps(dict(experiment="batch_schedule", lines=2, bins_per_line=50, rays="adaptive l 0-3",
                                   **batch_schedule(ctx, models))), flush=True)
+        elif which == "batch64":
+            n_max = int(argv[2]) if len(argv) > 2 else 200_000
+            t0 = time.perf_counter()
+            models = synth.batch_models(n_models=64, seed=5, n_min=10_000, n_max=n_max, n_lines=4, n_freq=100)
+            gen = time.perf_counter() - t0
+            print(json.dumps(dict(experiment="batch_throughput", n_max=n_max, lines=4, bins_per_line=100,
+                                  rays="adaptive l 0-3", generation_s=gen,
+                                  **batch_throughput(ctx, models))), flush=True)
         elif which == "learned":
             n = int(argv[2]) if len(argv) > 2 else 20000
 
