@@ -21,6 +21,12 @@
 // lattice meshes, ambiguous forward tests) the step is redone exactly in
 // double precision.  The winner's Z is always computed exactly in double.
 //
+// An undecided step is decided by the whole warp at once (step_exact_warp):
+// every neighbour of the current point is evaluated in double precision, one
+// per lane, and a warp reduction applies the defining rule.  Lanes wait for
+// one another only at these steps, and for a few tens of cycles rather than a
+// serial double-precision pass over the neighbour list.
+//
 // The fast path carries the winner's single-precision Z and its error bound
 // into the next step's forward test, so it executes no double-precision
 // operation at all; the exact Z is formed only on undecided steps (and for
@@ -61,7 +67,7 @@ __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t c, double xo
 
 struct FStep {
     int32_t next;  // -1: the half-ray ends; -2: undecided
-    float z32;     // single-precision Z of next; when undecided, H (see step_contenders)
+    float z32;     // single-precision Z of next; when undecided, the smallest upper bound of q
     float ez;      // bound on |z32 - Z(next)|, Z the double-precision value
 };
 
@@ -110,52 +116,6 @@ __device__ __forceinline__ FStep step_screen(const DevMesh &m, int32_t c, float4
     if (lo1_id < 0) return FStep{-1, 0.0f, 0.0f};  // no neighbour can be forward
     if (best >= 0 && best == lo1_id && hib < lo2) return FStep{best, zb, ezb};
     return FStep{-2, hib, 0.0f};
-}
-
-// An undecided step, exactly: only neighbours that are not surely backward and
-// whose interval reaches down to H (the smallest upper bound of a surely
-// forward neighbour, or infinity) can be the winner; every other neighbour has
-// a strictly larger double-precision q than that surely forward one.  The
-// contenders are re-screened (same single-precision values) and decided by
-// the defining rule in double precision.
-__device__ Step step_contenders(const DevMesh &m, int32_t c, float4 oh, float Xo, float f0, float f1, float f2,
-                                float zc32, float ezc, float H, double zc, double xo, double yo, double zo,
-                                double d0, double d1, double d2) {
-    const float zcm = ezc + 4.0f * kU * fabsf(zc32);
-    int32_t best = -1;
-    double qbest = 0.0, zbest = 0.0;
-    const int32_t e1 = m.off[c + 1];
-    for (int32_t e = m.off[c]; e < e1; ++e) {
-        const float4 rec = __ldg(m.nrec + e);
-        const int32_t nb = __float_as_int(rec.w);
-        const float dx = rec.x - oh.x, dy = rec.y - oh.y, dz = rec.z - oh.z;
-        const float S = fabsf(dx) + fabsf(dy) + fabsf(dz);
-        const float XS = fabsf(rec.x) + fabsf(rec.y) + fabsf(rec.z) + Xo;
-        const float z32 = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
-        const float ez = fmaf(3.0f * kU, XS, fmaf(12.0f * kU, S, m.g0));
-        const float diff = z32 - zc32;
-        const float E = ez + zcm + 4.0f * kU * fabsf(diff);
-        if (diff < -E) continue;
-        const float ex = fmaf(-z32, f0, dx), ey = fmaf(-z32, f1, dy), ez2 = fmaf(-z32, f2, dz);
-        const float q = fmaf(ez2, ez2, fmaf(ey, ey, ex * ex));
-        const float eq = fmaf(fmaf(32.0f * kU, XS, 128.0f * kU * S), S, fmaf(32.0f * m.g0, S, 1e-37f));
-        if (q - eq > H) continue;
-        const double ddx = __dsub_rn(__ldg(m.x + nb), xo);
-        const double ddy = __dsub_rn(__ldg(m.y + nb), yo);
-        const double ddz = __dsub_rn(__ldg(m.z + nb), zo);
-        const double zn = __dadd_rn(__dadd_rn(__dmul_rn(ddx, d0), __dmul_rn(ddy, d1)), __dmul_rn(ddz, d2));
-        if (!(zn > zc)) continue;
-        const double qx = __dsub_rn(ddx, __dmul_rn(zn, d0));
-        const double qy = __dsub_rn(ddy, __dmul_rn(zn, d1));
-        const double qz = __dsub_rn(ddz, __dmul_rn(zn, d2));
-        const double qd = __dadd_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(qz, qz));
-        if (best < 0 || qd < qbest || (qd == qbest && nb < best)) {
-            best = nb;
-            qbest = qd;
-            zbest = zn;
-        }
-    }
-    return Step{best, zbest};
 }
 
 // State of one lane's current walk.  It holds the direction in float only
@@ -241,6 +201,50 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
     return true;
 }
 
+// A step of lane L's walk decided exactly by the whole warp: lane j takes the
+// neighbours off[c] + j, off[c] + j + 32, ... of the current point c, forms
+// their exact Z and q in double precision (the defining rule, on every
+// neighbour, so no screen is needed), and a warp reduction picks the smallest
+// q among the forward ones, ties to the smaller index.  All lanes return the
+// same step.
+__device__ Step step_exact_warp(const DevMesh &m, int32_t c, int32_t o, double d0, double d1, double d2,
+                                int lane) {
+    const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
+    const double zc = (c == o) ? 0.0 : exact_Z(m, c, xo, yo, zo, d0, d1, d2);
+    int32_t best = -1;
+    double qbest = 0.0, zbest = 0.0;
+    const int32_t e1 = m.off[c + 1];
+    for (int32_t e = m.off[c] + lane; e < e1; e += 32) {
+        const int32_t nb = __ldg(m.nbr + e);
+        const double ddx = __dsub_rn(__ldg(m.x + nb), xo);
+        const double ddy = __dsub_rn(__ldg(m.y + nb), yo);
+        const double ddz = __dsub_rn(__ldg(m.z + nb), zo);
+        const double zn = __dadd_rn(__dadd_rn(__dmul_rn(ddx, d0), __dmul_rn(ddy, d1)), __dmul_rn(ddz, d2));
+        if (!(zn > zc)) continue;
+        const double qx = __dsub_rn(ddx, __dmul_rn(zn, d0));
+        const double qy = __dsub_rn(ddy, __dmul_rn(zn, d1));
+        const double qz = __dsub_rn(ddz, __dmul_rn(zn, d2));
+        const double qd = __dadd_rn(__dadd_rn(__dmul_rn(qx, qx), __dmul_rn(qy, qy)), __dmul_rn(qz, qz));
+        if (best < 0 || qd < qbest || (qd == qbest && nb < best)) {
+            best = nb;
+            qbest = qd;
+            zbest = zn;
+        }
+    }
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const int32_t b2 = __shfl_xor_sync(0xffffffffu, best, sh);
+        const double q2 = __shfl_xor_sync(0xffffffffu, qbest, sh);
+        const double z2 = __shfl_xor_sync(0xffffffffu, zbest, sh);
+        if (b2 >= 0 && (best < 0 || q2 < qbest || (q2 == qbest && b2 < best))) {
+            best = b2;
+            qbest = q2;
+            zbest = z2;
+        }
+    }
+    return Step{best, zbest};
+}
+
 // MODE 0: count the points of each half-ray; MODE 1: write their ids;
 // MODE 2: write ids, exact double Z and (optionally) projected velocities;
 // MODE 3: padded pass (ids k < pad to row h, length to lens[h], excess over
@@ -266,25 +270,39 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
     bool live = false;
     for (; h < n_half && !live; h += T) live = begin_walk<MODE>(m, R, o_begin, h, lens, offs, base, cap, pad, resume,
                                                                 status, wk);
-    while (live) {
-        FStep s = step_screen(m, wk.c, wk.oh, wk.Xo, wk.f0, wk.f1, wk.f2, wk.zc32, wk.ezc);
-        ++n_steps;
+    const int lane = threadIdx.x & 31;
+    // every lane stays in the loop until the whole warp is done, so that undecided
+    // steps can be resolved by the warp together
+    while (__any_sync(0xffffffffu, live)) {
+        FStep s{-1, 0.0f, 0.0f};
+        if (live) {
+            s = step_screen(m, wk.c, wk.oh, wk.Xo, wk.f0, wk.f1, wk.f2, wk.zc32, wk.ezc);
+            ++n_steps;
+        }
         double zexact = 0.0;
         bool have_exact = false;
-        if (s.next == -2) {  // undecided in single precision: its contenders in double
-            const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
-            double d0, d1, d2;
-            walk_dir(R, wk, d0, d1, d2);
-            const double zc = (wk.c == wk.o) ? 0.0 : exact_Z(m, wk.c, xo, yo, zo, d0, d1, d2);
-            const Step x = step_contenders(m, wk.c, wk.oh, wk.Xo, wk.f0, wk.f1, wk.f2, wk.zc32, wk.ezc, s.z32, zc,
-                                           xo, yo, zo, d0, d1, d2);
-            s.next = x.next;
-            zexact = x.Z;
-            ++n_exact;
-            have_exact = true;
-            s.z32 = __double2float_rn(x.Z);
-            s.ez = 2.0f * kU * fabsf(s.z32);
+        unsigned todo = __ballot_sync(0xffffffffu, live && s.next == -2);
+        while (todo) {  // undecided in single precision: decided exactly, one lane's step at a time
+            const int L = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int32_t c = __shfl_sync(0xffffffffu, wk.c, L);
+            const int32_t o = __shfl_sync(0xffffffffu, wk.o, L);
+            double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+            if (lane == L) walk_dir(R, wk, d0, d1, d2);
+            d0 = __shfl_sync(0xffffffffu, d0, L);
+            d1 = __shfl_sync(0xffffffffu, d1, L);
+            d2 = __shfl_sync(0xffffffffu, d2, L);
+            const Step x = step_exact_warp(m, c, o, d0, d1, d2, lane);
+            if (lane == L) {
+                s.next = x.next;
+                zexact = x.Z;
+                ++n_exact;
+                have_exact = true;
+                s.z32 = __double2float_rn(x.Z);
+                s.ez = 2.0f * kU * fabsf(s.z32);
+            }
         }
+        if (!live) continue;
         bool ended = s.next < 0, failed = false;
         if (!ended) {
             const int32_t k = wk.k;
