@@ -327,44 +327,79 @@ __device__ __forceinline__ int velocity_samples(R da, R wa, R db, R wb, R dv_max
 }
 
 // One interval from the current point (cur, modified in place) to nxt with nv
-// velocity samples: interpolated samples, then nxt itself.  (Inlining the
-// sample step at its three sites measured faster than one call site in a
-// loop with a select: the interpolation increments stay out of the common
-// one-sample path.)
+// velocity samples: interpolated samples, then nxt itself.  The code layout was
+// chosen by measurement on GB300: one line inlines the sample step at three
+// sites (the common one-sample path stays separate); several lines share the
+// final sample's site with the one-sample case, whose smaller code was 16 %
+// (two lines) to 33 % (four lines) faster.
 template <typename R, int NL, int BPL, int ORD>
 __device__ __forceinline__ void interval(Sample<R, NL> &cur, const Sample<R, NL> &nxt, R ds, R thr, int nv,
                                          R &cmax, const SolveArgs &a, R dtau_max, R inv_dtau_max,
                                          const Bin<R, NL> (&f)[BPL], const bool (&act)[BPL], Sweep<R> (&w)[BPL],
                                          unsigned &n_extra) {
-    if (nv > 1) {
-        const R rnv = Ar<R>::rcp(R(nv));
-        const R hs = ds * rnv;
-        const R ths = thr * R(nv);  // dtau_max / hs
-        Sample<R, NL> st;
-        st.delta = (nxt.delta - cur.delta) * rnv;
-        st.dv = (nxt.dv - cur.dv) * rnv;
-        st.chic = (nxt.chic - cur.chic) * rnv;
-        st.etac = (nxt.etac - cur.etac) * rnv;
-#pragma unroll
-        for (int l = 0; l < NL; ++l) {
-            st.chi0[l] = (nxt.chi0[l] - cur.chi0[l]) * rnv;
-            st.eta0[l] = (nxt.eta0[l] - cur.eta0[l]) * rnv;
-        }
-        for (int j = 1; j < nv; ++j) {
-            cur.delta += st.delta;
-            cur.dv += st.dv;
-            cur.chic += st.chic;
-            cur.etac += st.etac;
+    if constexpr (NL == 1) {
+        if (nv > 1) {
+            const R rnv = Ar<R>::rcp(R(nv));
+            const R hs = ds * rnv;
+            const R ths = thr * R(nv);  // dtau_max / hs
+            Sample<R, NL> st;
+            st.delta = (nxt.delta - cur.delta) * rnv;
+            st.dv = (nxt.dv - cur.dv) * rnv;
+            st.chic = (nxt.chic - cur.chic) * rnv;
+            st.etac = (nxt.etac - cur.etac) * rnv;
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
-                cur.chi0[l] += st.chi0[l];
-                cur.eta0[l] += st.eta0[l];
+                st.chi0[l] = (nxt.chi0[l] - cur.chi0[l]) * rnv;
+                st.eta0[l] = (nxt.eta0[l] - cur.eta0[l]) * rnv;
             }
-            sample_step<R, NL, BPL, ORD>(cur, hs, ths, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+            for (int j = 1; j < nv; ++j) {
+                cur.delta += st.delta;
+                cur.dv += st.dv;
+                cur.chic += st.chic;
+                cur.etac += st.etac;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    cur.chi0[l] += st.chi0[l];
+                    cur.eta0[l] += st.eta0[l];
+                }
+                sample_step<R, NL, BPL, ORD>(cur, hs, ths, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+            }
+            sample_step<R, NL, BPL, ORD>(nxt, hs, ths, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+        } else {
+            sample_step<R, NL, BPL, ORD>(nxt, ds, thr, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+        }
+    } else {
+        // several lines: two call sites (the nv = 1 case shares the final sample's);
+        // measured faster when the per-sample optics are longer
+        R hs = ds, ths = thr;
+        if (nv > 1) {
+            const R rnv = Ar<R>::rcp(R(nv));
+            hs = ds * rnv;
+            ths = thr * R(nv);  // dtau_max / hs
+            Sample<R, NL> st;
+            st.delta = (nxt.delta - cur.delta) * rnv;
+            st.dv = (nxt.dv - cur.dv) * rnv;
+            st.chic = (nxt.chic - cur.chic) * rnv;
+            st.etac = (nxt.etac - cur.etac) * rnv;
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                st.chi0[l] = (nxt.chi0[l] - cur.chi0[l]) * rnv;
+                st.eta0[l] = (nxt.eta0[l] - cur.eta0[l]) * rnv;
+            }
+            for (int j = 1; j < nv; ++j) {
+                cur.delta += st.delta;
+                cur.dv += st.dv;
+                cur.chic += st.chic;
+                cur.etac += st.etac;
+#pragma unroll
+                for (int l = 0; l < NL; ++l) {
+                    cur.chi0[l] += st.chi0[l];
+                    cur.eta0[l] += st.eta0[l];
+                }
+                sample_step<R, NL, BPL, ORD>(cur, hs, ths, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
+            }
         }
         sample_step<R, NL, BPL, ORD>(nxt, hs, ths, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
-    } else {
-        sample_step<R, NL, BPL, ORD>(nxt, ds, thr, cmax, dtau_max, inv_dtau_max, f, act, w, a.status, n_extra);
     }
     cur = nxt;
 }
@@ -558,11 +593,11 @@ __device__ void half_sweep(const DevMesh &m, const Data<R> &D, const SolveArgs &
 // CTAs of 128 threads; the minimum resident CTAs per SM caps the registers
 // (65536 / (128 x CTAs)).  Measured on GB300 with the persistent solve: more
 // resident warps beat the spills they cost down to 80 registers for one line
-// (6 CTAs: 15 % faster than 4), 96 for two lines (5), 128 for four (4) and
-// 168 for eight (3), where the per-line sample data need the registers.
+// (6 CTAs: 15 % faster than 4); two and four lines run best at 128 registers
+// (4 CTAs) and eight at 168 (3), where the per-line sample data need them.
 template <typename R, int NL, int BPL>
 struct Occ {
-    static constexpr int kMinBlocks = sizeof(R) == 8 ? 1 : (NL == 1 ? 6 : NL == 2 ? 5 : NL == 4 ? 4 : 3);
+    static constexpr int kMinBlocks = sizeof(R) == 8 ? 1 : (NL == 1 ? 6 : NL <= 4 ? 4 : 3);
 };
 
 // J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
