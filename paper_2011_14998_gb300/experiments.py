@@ -18,7 +18,7 @@ entry points (no arithmetic of the method here, only bookkeeping and statistics)
   seeds; the plain criterion's factors are scaled until it keeps the target
   fraction of the test mesh, and the network keeps as many points.
 
-`python -m paper_2011_14998_gb300.experiments rays|reduction|learned|batch` runs them
+`python -m paper_2011_14998_gb300.experiments rays|reduction|learned|batch|batch64|octree` runs them
 on the synthetic stand-ins and prints one JSON line each.
 """
 from __future__ import annotations
@@ -240,6 +240,14 @@ def main(argv):
             models = synth.batch_models(n_models=k, seed=5, n_min=10_000, n_max=50_000, n_lines=2, n_freq=50)
             print(json.dumps(dict(experiment="batch_schedule", lines=2, bins_per_line=50, rays="adaptive l 0-3",
                                   **batch_schedule(ctx, models))), flush=True)
+        elif which == "octree":
+            n = int(argv[2]) if len(argv) > 2 else 300_000
+            t0 = time.perf_counter()
+            m = synth.octree_model(n, seed=3)
+            gen = time.perf_counter() - t0
+            print(json.dumps(dict(experiment="batch_throughput", workload=m["name"], lines=2, bins_per_line=64,
+                                  rays="adaptive l 0-3", generation_s=gen,
+                                  **batch_throughput(ctx, [m], reps=3))), flush=True)
         elif which == "batch64":
             n_max = int(argv[2]) if len(argv) > 2 else 200_000
             t0 = time.perf_counter()
