@@ -198,6 +198,19 @@ mgx_status mgx_reduce_mesh(mgx_ctx *ctx, int32_t model, const double *f, double 
 mgx_status mgx_solve_u(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params, int64_t o_begin,
                        int64_t o_end, double *u_out);
 
+/* Learned reduction by weighted thinning (the learned variant of Section
+ * 2.2.2's random thinning; no counterpart in the paper).  With y_i the network's
+ * prediction for the features X [n][8] (as in mgx_reduce_mesh_learned), point i
+ * is kept when u_i < min(1, c 10^(alpha y_i)), u_i the SplitMix64 uniform of
+ * (seed, i) as in mgx_reduce_mesh, and c the scale at which the expected kept
+ * count sum_i min(1, c 10^(alpha y_i)) equals keep_fraction * n (bisection on
+ * log2 c).  alpha = 0 is uniform thinning.  keep [n] host; *n_kept and *scale
+ * (c) may be NULL.  Requires 0 <= keep_fraction <= 1, alpha finite and >= 0,
+ * and parameters set (mgx_mlp_set_params) else MGX_ESTATE. */
+mgx_status mgx_reduce_mesh_learned_weighted(mgx_ctx *ctx, int32_t model, const float *X, double keep_fraction,
+                                            double alpha, uint64_t seed, uint8_t *keep, int64_t *n_kept,
+                                            double *scale);
+
 /* Element-size field of an analytic model and its mesh (Section 2.2.1, Eq. 5).
  * f [nx][ny][nz] (index (i*ny + j)*nz + k, host, every value finite and > 0)
  * is the tracer at the points of a regular Cartesian background mesh of

@@ -29,7 +29,7 @@ ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs
                "mgx_solve_J_noalloc", "mgx_solve_J_batch", "mgx_mlp_set_params", "mgx_mlp_get_params",
                "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned",
                "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune", "mgx_analytic_mesh", "mgx_solve_u",
-               "mgx_pix2vec", "mgx_antipode")
+               "mgx_pix2vec", "mgx_antipode", "mgx_reduce_mesh_learned_weighted")
 MGX_MLP_NPARAM = 4801
 MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
@@ -109,6 +109,8 @@ def load_library(path: str = LIB_PATH):
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
         "mgx_set_tuning": (i32, [vp, C.POINTER(Tuning)]),
         "mgx_pix2vec": (i32, [i32, i64, vp]),
+        "mgx_reduce_mesh_learned_weighted": (i32, [vp, i32, vp, dbl, dbl, u64, vp, C.POINTER(i64),
+                                                   C.POINTER(dbl)]),
         "mgx_antipode": (i64, [i32, i64]),
         "mgx_solve_u": (i32, [vp, i32, C.POINTER(SolveParams), i64, i64, vp]),
         "mgx_analytic_mesh": (i32, [vp, i32, i32, i32, vp, dbl, dbl, dbl, u64, vp, vp, vp, C.POINTER(i64)]),
@@ -228,6 +230,19 @@ def mgx_solve_J_batch(ctx, models, params: SolveParams, J_outs, flags: int = 0) 
     ids = np.ascontiguousarray(models, np.int32)
     ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
     _check(ctx, load_library().mgx_solve_J_batch(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags)))
+
+
+def mgx_reduce_mesh_learned_weighted(ctx, model, X, keep_fraction, alpha=1.0, seed=0):
+    """Weighted learned thinning (see include/mgx.h); returns (keep, n_kept, scale)."""
+    X = np.ascontiguousarray(X, np.float32)
+    n = X.shape[0]
+    keep = np.empty(n, np.uint8)
+    nk = C.c_int64(0)
+    sc = C.c_double(0.0)
+    _check(ctx, load_library().mgx_reduce_mesh_learned_weighted(ctx, int(model), _ptr(X), float(keep_fraction),
+                                                                float(alpha), int(seed) & (2**64 - 1), _ptr(keep),
+                                                                C.byref(nk), C.byref(sc)))
+    return keep, int(nk.value), float(sc.value)
 
 
 def mgx_pix2vec(l: int, p: int) -> np.ndarray:

@@ -1616,6 +1616,62 @@ mgx_status mgx_reduce_mesh_learned(mgx_ctx *ctx, int32_t model, const float *X, 
     return s;
 }
 
+mgx_status mgx_reduce_mesh_learned_weighted(mgx_ctx *ctx, int32_t model, const float *X, double keep_fraction,
+                                            double alpha, uint64_t seed, uint8_t *keep, int64_t *n_kept,
+                                            double *scale) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    Model *m = get_model(ctx, model);
+    if (!m) return fail(ctx, MGX_EINVAL, "reduce_mesh_learned_weighted: no model %d", model);
+    if (!X || !keep || !(keep_fraction >= 0.0) || !(keep_fraction <= 1.0) || !(alpha >= 0.0) || !std::isfinite(alpha))
+        return fail(ctx, MGX_EINVAL, "reduce_mesh_learned_weighted: bad arguments");
+    if (!ctx->mlp_theta) return fail(ctx, MGX_ESTATE, "reduce_mesh_learned_weighted: mgx_mlp_set_params not called");
+    DeviceGuard g(ctx->device);
+    const int64_t n = m->n;
+    const double target = keep_fraction * double(n);
+    float *Xd = nullptr, *yd = nullptr, *wd = nullptr;
+    double *sd = nullptr;
+    unsigned long long *cnt = nullptr;
+    uint8_t *kd = nullptr;
+    CK(dalloc(ctx, &Xd, size_t(n) * 8));
+    CK(dalloc(ctx, &yd, size_t(n)));
+    CK(dalloc(ctx, &wd, size_t(n)));
+    CK(dalloc(ctx, &sd, 1));
+    CK(dalloc(ctx, &cnt, 1));
+    CK(dalloc(ctx, &kd, size_t(n)));
+    CK(cudaMemcpyAsync(Xd, X, size_t(n) * 8 * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    double c = 0.0;
+    {
+        Timed t(ctx, MGX_K_OTHER);
+        launch_mlp(false, Xd, nullptr, nullptr, n, ctx->mlp_W1b, ctx->mlp_W2b, ctx->mlp_theta, yd, nullptr, nullptr,
+                   0.0f, ctx->stream);
+        launch_thin_weights(yd, n, float(alpha), wd, ctx->stream);
+        // bisection on log2 c: the expected kept count grows with c
+        double lo = -400.0, hi = 400.0;
+        for (int it = 0; it < 80 && keep_fraction > 0.0 && keep_fraction < 1.0; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            double sum = 0.0;
+            launch_thin_expected(wd, n, std::exp2(mid), sd, ctx->stream);
+            CK(cudaMemcpyAsync(&sum, sd, sizeof sum, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            if (sum < target) lo = mid;
+            else hi = mid;
+        }
+        c = keep_fraction <= 0.0 ? 0.0 : keep_fraction >= 1.0 ? 1e300 : std::exp2(0.5 * (lo + hi));
+        launch_thin_mark(wd, n, c, seed, kd, cnt, ctx->stream);
+    }
+    CK(cudaGetLastError());
+    unsigned long long kept = 0;
+    CK(cudaMemcpyAsync(keep, kd, size_t(n), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&kept, cnt, sizeof kept, cudaMemcpyDeviceToHost, ctx->stream));
+    const mgx_status s = sync_status(ctx);
+    dfree(ctx, Xd); dfree(ctx, yd); dfree(ctx, wd); dfree(ctx, sd); dfree(ctx, cnt); dfree(ctx, kd);
+    if (s != MGX_OK) return s;
+    if (n_kept) *n_kept = int64_t(kept);
+    if (scale) *scale = c;
+    return MGX_OK;
+}
+
 mgx_status mgx_profile_enable(mgx_ctx *ctx, int32_t enable) {
     if (!ctx) return MGX_EINVAL;
     ctx->err.clear();

@@ -204,6 +204,13 @@ void launch_size_map(int64_t n, const double *Gf, const unsigned long long *mm, 
                      double ell_max, uint64_t seed, double *ell, uint8_t *keep, unsigned long long *kept,
                      cudaStream_t st);
 
+// ---- score-weighted thinning (k_thin.cu): w = 10^(alpha y); expected kept
+// count for a scale c; the coin flips
+void launch_thin_weights(const float *y, int64_t n, float alpha, float *w, cudaStream_t st);
+void launch_thin_expected(const float *w, int64_t n, double c, double *sum, cudaStream_t st);
+void launch_thin_mark(const float *w, int64_t n, double c, uint64_t seed, uint8_t *keep, unsigned long long *kept,
+                      cudaStream_t st);
+
 // ---- reduction criterion (k_reduce.cu)
 void launch_reduce(const DevMesh &m, const double *f, double f_small, double f_large,
                    double G_thres, uint64_t seed, double *Gf, double *L, double *ell,

@@ -16,7 +16,8 @@ entry points (no arithmetic of the method here, only bookkeeping and statistics)
 * `learned_vs_plain` -- the learned reduction against the plain criterion at
   one kept fraction: the network is trained on plain reductions of training
   seeds; the plain criterion's factors are scaled until it keeps the target
-  fraction of the test mesh, and the network keeps as many points.
+  fraction of the test mesh, and the network keeps as many points, either the
+  top-ranked ones or by thinning weighted with its prediction.
 
 `python -m paper_2011_14998_gb300.experiments rays|reduction|learned|batch|batch64|octree` runs them
 on the synthetic stand-ins and prints one JSON line each.
@@ -208,17 +209,24 @@ def learned_vs_plain(ctx, make_model, train_seeds, test_seed, table1, keep_fract
                 break
         keep_plain = ctx.reduce_mesh(mid, test["rho"], f_small * hi, f_large * hi, g_thres, seed)[3]
         keep_mlp = learned.reduce_learned(ctx, mid, test, std, float(keep_plain.mean()))
+        keep_w = {a: learned.reduce_learned_weighted(ctx, mid, test, std, float(keep_plain.mean()), a, seed)
+                  for a in (0.5, 1.0, 2.0, 3.0)}
     finally:
         ctx.free(mid)
     e_plain = learned.reduction_error(ctx, test, J_full, keep_plain)
     e_mlp = learned.reduction_error(ctx, test, J_full, keep_mlp)
+    weighted = {}
+    for a, kw in keep_w.items():
+        e = learned.reduction_error(ctx, test, J_full, kw)
+        weighted[f"alpha_{a}"] = dict(kept_fraction=float(kw.mean()), mean_rel_err=float(e.mean()),
+                                      p90=float(np.quantile(e, 0.9)))
     return dict(n=len(test["pos"]), kept_fraction=float(keep_plain.mean()),
                 reduction=float(1.0 / keep_plain.mean()), plain_scale=float(hi), train_samples=int(len(y)),
                 loss_first=float(losses[0]), loss_last=float(losses[-1]),
                 mean_rel_err_plain=float(e_plain.mean()), mean_rel_err_learned=float(e_mlp.mean()),
                 p90_plain=float(np.quantile(e_plain, 0.9)), p90_learned=float(np.quantile(e_mlp, 0.9)),
                 frac_below_1pct_plain=float((e_plain < 0.01).mean()),
-                frac_below_1pct_learned=float((e_mlp < 0.01).mean()))
+                frac_below_1pct_learned=float((e_mlp < 0.01).mean()), weighted=weighted)
 
 
 def main(argv):
@@ -267,7 +275,7 @@ def main(argv):
 
             for name, mk, t1, test_seed in (("AMR (clump octree)", octree, (0.90, 2.10, 0.10), 3),
                                             ("SPH (binary-wind spiral)", spiral, (1.00, 2.15, 0.21), 4)):
-                for frac in (0.2, 0.1):
+                for frac in ((0.2, 0.1) if len(argv) <= 3 else tuple(float(x) for x in argv[3].split(","))):
                     print(json.dumps(dict(experiment="learned_vs_plain", model=name, table1=t1,
                                           **learned_vs_plain(ctx, mk, (100, 101, 102, 103), test_seed, t1,
                                                              keep_fraction=frac))), flush=True)

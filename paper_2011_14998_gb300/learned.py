@@ -14,7 +14,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import (MGX_FP32, mgx_mlp_features, mgx_mlp_get_params, mgx_mlp_set_params, mgx_mlp_train,
-               mgx_reduce_mesh_learned)
+               mgx_reduce_mesh_learned, mgx_reduce_mesh_learned_weighted)
 
 POINT_FIELDS = ("pos", "vel", "chi0", "eta0", "dvw", "chi_c", "eta_c", "rho", "T")
 
@@ -125,4 +125,13 @@ def reduce_learned(ctx, mid: int, m: dict, std: Standardizer, keep_fraction: flo
     """Keep the points whose predicted J error (if dropped) is largest."""
     X = mgx_mlp_features(ctx.ptr, mid, m["rho"], m["T"])
     keep, _ = mgx_reduce_mesh_learned(ctx.ptr, mid, std(X), keep_fraction)
+    return keep
+
+
+def reduce_learned_weighted(ctx, mid: int, m: dict, std: Standardizer, keep_fraction: float, alpha: float = 2.0,
+                            seed: int = 0) -> np.ndarray:
+    """Keep each point with probability min(1, c 10^(alpha y)), y its predicted
+    log10 J error if dropped, c matching the expected count to keep_fraction."""
+    X = mgx_mlp_features(ctx.ptr, mid, m["rho"], m["T"])
+    keep, _, _ = mgx_reduce_mesh_learned_weighted(ctx.ptr, mid, std(X), keep_fraction, alpha, seed)
     return keep
