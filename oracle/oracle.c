@@ -302,7 +302,9 @@ typedef struct {
     double I_bdy;    /* boundary intensity entering both ends of every ray    */
     int32_t decide32; /* take the two integer decisions in single precision, as
                          the single-precision form of the solver does: the
-                         velocity-sample count as ceil(|d delta| / limit) and
+                         velocity-sample count as ceil(|d delta| / limit), on
+                         delta projected in single precision from the
+                         velocities and direction rounded to single, and
                          Eq. 2's n_inter as 1 unless chi_max > dtau_max / ds,
                          else ceil((chi_max ds) fl32(1/dtau_max));
                          everything else stays double */
@@ -385,6 +387,7 @@ double orc_bin_x(int32_t n_freq, double x_span, int32_t k)
 typedef struct {
     double s, delta, dvw, chic, etac;
     double chi0[ORC_MAX_LINES], eta0[ORC_MAX_LINES];
+    float delta32; /* delta projected in single precision (base points only) */
 } orc_sample;
 
 typedef struct {
@@ -426,10 +429,24 @@ static void sample_lerp(int L, const orc_sample *a, const orc_sample *b, double 
     x->dvw = a->dvw + (b->dvw - a->dvw) * t;
     x->chic = a->chic + (b->chic - a->chic) * t;
     x->etac = a->etac + (b->etac - a->etac) * t;
+    x->delta32 = 0.0f;
     for (int l = 0; l < L; ++l) {
         x->chi0[l] = a->chi0[l] + (b->chi0[l] - a->chi0[l]) * t;
         x->eta0[l] = a->eta0[l] + (b->eta0[l] - a->eta0[l]) * t;
     }
+}
+
+/* (v_n - v_o).d in single precision: every operand rounded to single, the
+ * components differenced, then (x + y) + z with each product and sum rounded
+ * (the sources are compiled without contraction).  Only the decide32 form of
+ * the velocity-sample count reads it. */
+static float delta_single(const double *vn, const double *vo, const double d[3])
+{
+    const float ux = (float)vn[0] - (float)vo[0];
+    const float uy = (float)vn[1] - (float)vo[1];
+    const float uz = (float)vn[2] - (float)vo[2];
+    const float px = ux * (float)d[0], py = uy * (float)d[1], pz = uz * (float)d[2];
+    return (px + py) + pz;
 }
 
 /* Build the velocity-sampled pair line of origin o along +-r.  The base points
@@ -466,18 +483,21 @@ static void build_vline(const orc_model *m, const orc_params *pr, int64_t o, con
             const double *vn = m->vel + 3 * id;
             const double de = ((vn[0] - vo[0]) * rm[0] + (vn[1] - vo[1]) * rm[1]) + (vn[2] - vo[2]) * rm[2];
             sample_of_point(m, id, -bz[nb - 1 - k], de, &cur);
+            cur.delta32 = delta_single(vn, vo, rm);
         } else if (k == nb) {
             sample_of_point(m, o, 0.0, 0.0, &cur);
+            cur.delta32 = 0.0f;
         } else {
             const int64_t id = fi[k - nb - 1];
             const double *vn = m->vel + 3 * id;
             const double de = ((vn[0] - vo[0]) * r[0] + (vn[1] - vo[1]) * r[1]) + (vn[2] - vo[2]) * r[2];
             sample_of_point(m, id, fz[k - nb - 1], de, &cur);
+            cur.delta32 = delta_single(vn, vo, r);
         }
         if (k > 0 && pr->dv_max > 0.0) {
             int64_t parts = 1;
             if (pr->decide32) {
-                const float jump = fabsf((float)cur.delta - (float)prev.delta);
+                const float jump = fabsf(cur.delta32 - prev.delta32);
                 const float lim = (float)pr->dv_max * fminf((float)prev.dvw, (float)cur.dvw);
                 if (jump > lim) parts = (int64_t)ceilf(jump / lim);
             } else {

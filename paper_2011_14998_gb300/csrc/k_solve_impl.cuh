@@ -55,6 +55,10 @@ struct Ar<double> {
         return cm * hs / dtau_max;
     }
     static __device__ __forceinline__ double src(double eta, double chi) { return eta / chi; }
+    // projected velocity (x + y) + z, every product and sum rounded (no contraction)
+    static __device__ __forceinline__ double proj(double ux, double uy, double uz, double d0, double d1, double d2) {
+        return __dadd_rn(__dadd_rn(__dmul_rn(ux, d0), __dmul_rn(uy, d1)), __dmul_rn(uz, d2));
+    }
 };
 
 // Single precision: the profile constants are prescaled by sqrt(log2 e), so
@@ -77,6 +81,11 @@ struct Ar<float> {
         return (cm * hs) * inv_dtau_max;
     }
     static __device__ __forceinline__ float src(float eta, float chi) { return eta * rcp(chi); }
+    // projected velocity (x + y) + z, every product and sum rounded (no
+    // contraction): the velocity-sample count of an interval is decided on it
+    static __device__ __forceinline__ float proj(float ux, float uy, float uz, float d0, float d1, float d2) {
+        return __fadd_rn(__fadd_rn(__fmul_rn(ux, d0), __fmul_rn(uy, d1)), __fmul_rn(uz, d2));
+    }
 };
 
 // Frequency-independent data of one line sample.
@@ -109,7 +118,7 @@ template <typename R, int NL>
 __device__ __forceinline__ void load_sample(const Data<R> &D, int32_t L, int32_t id, R vox, R voy, R voz,
                                             R d0, R d1, R d2, Sample<R, NL> &s) {
     const R ux = __ldg(D.vx + id) - vox, uy = __ldg(D.vy + id) - voy, uz = __ldg(D.vz + id) - voz;
-    s.delta = (ux * d0 + uy * d1) + uz * d2;
+    s.delta = Ar<R>::proj(ux, uy, uz, d0, d1, d2);
     s.dv = __ldg(D.dvw + id);
     s.chic = __ldg(D.chic + id);
     s.etac = __ldg(D.etac + id);

@@ -1,4 +1,4 @@
-"""Shared test helpers (comparison metrics); no method arithmetic."""
+"""Shared test helpers (comparison metrics, tiny hand-built models); no method arithmetic."""
 import numpy as np
 
 
@@ -12,3 +12,15 @@ def j_rel_err(Jg, Jo, floor=1e-6):
     mask = np.abs(Jo) > floor * mx
     rel = np.abs(Jg - Jo)[mask] / np.abs(Jo[mask]) if mask.any() else np.zeros(1)
     return float(rel.max()), float(np.abs(Jg - Jo).max())
+
+
+def line_model(vel_a, vel_b, dv=1.0):
+    """Three points on the x axis (0, 1, 2), chained neighbours, origin in the middle."""
+    pos = np.array([[0.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]])
+    off = np.array([0, 1, 3, 4])
+    nbr = np.array([1, 0, 2, 1], np.int32)
+    vel = np.array([[vel_a, 0, 0], [0.0, 0, 0], [vel_b, 0, 0]])
+    one = np.ones((3, 1))
+    return dict(pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr, nu0=np.array([1e11]), chi0=one,
+                eta0=one, dvw=np.full(3, dv), chi_c=np.full(3, 1e-3), eta_c=np.full(3, 1e-3),
+                n_freq=3, x_span=2.0, l_min=0, l_max=0)

@@ -8,7 +8,7 @@ everywhere).  Sizes span several 32-bin tiles and ragged tails.
 import numpy as np
 import pytest
 
-from helpers import j_rel_err
+from helpers import j_rel_err, line_model
 
 pytestmark = pytest.mark.gpu
 
@@ -207,6 +207,30 @@ def test_single_point_and_isolated_points(ctx, orc):
     ctx.free(mid)
     Jo = orc.OracleModel(m2, rays=rays).solve_J(orc.params(dtau_max=0.1))
     assert j_rel_err(Jg, Jo)[0] < FP64_TOL
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_velocity_count_single_precision(ctx, orc, order):
+    """An interval whose velocity jump is 6.0000005 limits in FP64 (7 samples)
+    and exactly 6 in single precision (Section 2.1.1): the FP32 kernel takes
+    6, as the oracle's single-precision decision does, and the FP64 kernel 7."""
+    import paper_2011_14998_gb300 as mgx
+
+    m = line_model(vel_a=0.7, vel_b=2.7000001586834803)
+    m["vel"][1, 0] = 0.7
+    mid = ctx.load(m)
+    rays = ctx.rays(mid)
+    u64 = ctx.solve_u(mid, 1, 2, precision=mgx.MGX_FP64, order=order)[0]
+    u32 = ctx.solve_u(mid, 1, 2, precision=mgx.MGX_FP32, order=order)[0]
+    ctx.free(mid)
+    om = orc.OracleModel(m, rays=rays)
+    uo64 = om.solve_u(orc.params(order=order), [1])[0]
+    uo32 = om.solve_u(orc.params(order=order, decide32=True), [1])[0]
+    p = int(np.flatnonzero((rays[1] == 4) | (rays[1] == 6))[0])
+    assert abs(uo32[p, 2] - uo64[p, 2]) > 1e-3 * uo64[p, 2]  # the two decisions differ here
+    assert j_rel_err(u64, uo64)[0] < FP64_TOL
+    assert j_rel_err(u32, uo32)[0] < FP32_TOL
+    assert abs(u32[p, 2] - uo32[p, 2]) < FP32_TOL * uo32[p, 2]
 
 
 def test_single_bin_and_zero_span(ctx, orc):

@@ -11,6 +11,8 @@ import math
 import numpy as np
 import pytest
 
+from helpers import line_model
+
 
 def _dense_system(dtau, S, I):
     M = len(dtau)
@@ -130,22 +132,10 @@ def test_subdivision_eq2(orc):
             assert io2 == 0
 
 
-def _line_model(vel_a, vel_b, dv=1.0):
-    """Three points on the x axis (0, 1, 2), chained neighbours, origin in the middle."""
-    pos = np.array([[0.0, 0, 0], [1.0, 0, 0], [2.0, 0, 0]])
-    off = np.array([0, 1, 3, 4])
-    nbr = np.array([1, 0, 2, 1], np.int32)
-    vel = np.array([[vel_a, 0, 0], [0.0, 0, 0], [vel_b, 0, 0]])
-    one = np.ones((3, 1))
-    return dict(pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr, nu0=np.array([1e11]), chi0=one,
-                eta0=one, dvw=np.full(3, dv), chi_c=np.full(3, 1e-3), eta_c=np.full(3, 1e-3),
-                n_freq=3, x_span=2.0, l_min=0, l_max=0)
-
-
 def test_velocity_sampling_counts(orc):
     # pair of base pixel 4 (+x) at the middle point: backward point 0 (direction -x),
     # forward point 2 (+x).  delta_0 = (v_0 - v_1).(-x), delta_2 = (v_2 - v_1).(+x)
-    m = _line_model(vel_a=-2.0, vel_b=0.9)
+    m = line_model(vel_a=-2.0, vel_b=0.9)
     om = orc.OracleModel(m, rays=np.zeros((3, 6), np.uint32))
     ray = np.uint32(4)
     assert orc.antipode(0, 4) == 6
@@ -162,6 +152,24 @@ def test_velocity_sampling_counts(orc):
     dtau, S, io = om.pair_line(1, ray, 0, 1, orc.params(dv_max=1 / 3, dtau_max=100.0))
     assert len(dtau) == 9 and io == 6
     assert np.allclose(dtau[:6], 1e-3 / 6, rtol=1e-13) and np.allclose(dtau[6:], 1e-3 / 3, rtol=1e-13)
+
+
+def test_velocity_count_single_precision_projection(orc):
+    # The single-precision decision projects the velocities rounded to single.
+    # Origin v = 0.7, forward neighbour v = 2.7000001586834803 (direction +x):
+    #   FP64: jump 2.00000015868... / (1/3) = 6.0000005 -> 7 parts;
+    #   single: fl32(2.70000016) - fl32(0.7) = 2.700000048 - 0.699999988 = 2.0 exactly,
+    #   and 2.0 / fl32(1/3) = 6.0 -> 6 parts.
+    # Rounding the FP64 jump instead gives fl32(2.00000016) = 2.00000024 -> 7 parts.
+    m = line_model(vel_a=0.7, vel_b=2.7000001586834803)
+    m["vel"][1, 0] = 0.7
+    om = orc.OracleModel(m, rays=np.zeros((3, 6), np.uint32))
+    ray = np.uint32(4)
+    assert om.vline_size(1, ray, orc.params(dv_max=1 / 3)) == (2 + 7, 1)
+    assert om.vline_size(1, ray, orc.params(dv_max=1 / 3, decide32=True)) == (2 + 6, 1)
+    # one sub-sample fewer is a discretisation change well above the FP32 budget
+    x = [orc.feautrier(*om.pair_line(1, ray, 0, 2, orc.params(dv_max=1 / 3, decide32=d))) for d in (False, True)]
+    assert abs(x[1] - x[0]) > 1e-3 * x[0]
 
 
 def _grid_closed_form(orc, m, om, params, origins):
