@@ -18,8 +18,11 @@ entry points (no arithmetic of the method here, only bookkeeping and statistics)
   seeds; the plain criterion's factors are scaled until it keeps the target
   fraction of the test mesh, and the network keeps as many points, either the
   top-ranked ones or by thinning weighted with its prediction.
+* `batch_throughput`, `model_throughput` -- solves/s of one graph-replayed
+  batched step over several models, and of the per-model entry point on one
+  large model (the 10^6-particle spiral).
 
-`python -m paper_2011_14998_gb300.experiments rays|reduction|learned|batch|batch64|octree` runs them
+`python -m paper_2011_14998_gb300.experiments rays|reduction|learned|batch|batch64|octree|spiral` runs them
 on the synthetic stand-ins and prints one JSON line each.
 """
 from __future__ import annotations
@@ -178,6 +181,44 @@ def batch_throughput(ctx, models, precision=MGX_FP32, reps=1):
                 plan_and_first_step_s=t_plan, step_s=dt, solves_per_s=solves / dt, all_finite=ok)
 
 
+def model_throughput(ctx, m, precision=MGX_FP32, reps=2):
+    """Solves/s of the per-model entry point (mgx_solve_J traces and solves the
+    origins in chunks that fit its arena) on one model, J left on the device;
+    the ingest with its ray set and the first solve are timed apart."""
+    import torch
+
+    t0 = time.perf_counter()
+    mid = ctx.load(m)
+    torch.cuda.synchronize()
+    t_load = time.perf_counter() - t0
+    try:
+        i = ctx.models[mid]
+        solves = i["n"] * i["npairs"] * i["L"] * i["F"]
+        out = torch.empty((i["n"], i["L"] * i["F"]), dtype=torch.float64, device=f"cuda:{ctx.device}")
+        t0 = time.perf_counter()
+        ctx.solve_J(mid, precision=precision, out=out)
+        torch.cuda.synchronize()
+        t_first = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.solve_J(mid, precision=precision, out=out)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        ok = bool(torch.isfinite(out).all())
+        ctx.profile(True)  # one more step, untimed, for the work counters and the kernel split
+        ctx.solve_J(mid, precision=precision, out=out)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+    finally:
+        ctx.free(mid)
+    return dict(points=int(i["n"]), pairs=int(i["npairs"]), solves_per_step=int(solves), load_s=t_load,
+                first_step_s=t_first, step_s=dt, solves_per_s=solves / dt, all_finite=ok,
+                samples_per_solve=prof["samples"] / solves, updates_per_solve=prof["updates"] / solves,
+                trace_points_per_half=prof["trace_points"] / (i["n"] * i["npairs"] * 2),
+                samples_per_s=prof["samples"] / dt, kernel_ms=prof["ms"])
+
+
 def learned_vs_plain(ctx, make_model, train_seeds, test_seed, table1, keep_fraction=0.2,
                      scales=(1.0, 1.5, 2.2), epochs=60, seed=11):
     """Reduced-mesh error of the learned and the plain criterion at one kept fraction."""
@@ -256,6 +297,15 @@ def main(argv):
             print(json.dumps(dict(experiment="batch_throughput", workload=m["name"], lines=2, bins_per_line=64,
                                   rays="adaptive l 0-3", generation_s=gen,
                                   **batch_throughput(ctx, [m], reps=3))), flush=True)
+        elif which == "spiral":
+            n = int(argv[2]) if len(argv) > 2 else 1_000_000
+            t0 = time.perf_counter()
+            m = synth.spiral_model(n, seed=4)
+            gen = time.perf_counter() - t0
+            print(json.dumps(dict(experiment="model_throughput", workload=m["name"], lines=1, bins_per_line=100,
+                                  rays="l = 2 (96 pairs)", generation_s=gen, **model_throughput(ctx, m))), flush=True)
+            print(json.dumps(dict(experiment="batch_throughput", workload=m["name"], lines=1, bins_per_line=100,
+                                  rays="l = 2 (96 pairs)", **batch_throughput(ctx, [m], reps=2))), flush=True)
         elif which == "batch64":
             n_max = int(argv[2]) if len(argv) > 2 else 200_000
             t0 = time.perf_counter()
