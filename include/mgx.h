@@ -173,7 +173,11 @@ mgx_status mgx_trace(mgx_ctx *ctx, int32_t model, int64_t o_begin, int64_t o_end
  *   J_out  [n][n_lines*n_freq] doubles, host or device per params->out_on_device
  * The call synchronises the stream (the tracer's total length sizes the
  * point-list arena; device-side checks are reported before returning).  Origins
- * are processed in chunks whose traced point ids fit a 16 GiB arena. */
+ * are processed in chunks whose traced point ids fit a 16 GiB arena.  The first
+ * call on a model counts the traced length of every half-ray and keeps the
+ * prefix sums with the model ((2 n npairs + 1) x 8 bytes of device memory)
+ * until mgx_set_rays or mgx_free_model; later calls trace and solve without
+ * the counting pass. */
 mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params, void *J_out);
 
 /* Mesh-reduction criterion of Section 2.2.2 with tracer f (Eqs. 6-8):

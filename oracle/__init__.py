@@ -160,6 +160,8 @@ class OracleModel:
             rays = rayset(self.pos, self.l_min, self.l_max, smp, threads)
         self.rays = np.ascontiguousarray(rays, np.uint32)
         n = len(self.pos)
+        if self.rays.shape != (n, rayset_npairs(self.l_min, self.l_max)):
+            raise ValueError(f"rays {self.rays.shape} do not match {n} points at levels {self.l_min}..{self.l_max}")
         self.s = Model(n, self.pos.ctypes.data, self.vel.ctypes.data, self.nbr_off.ctypes.data,
                        self.nbr_idx.ctypes.data, len(self.nu0), self.nu0.ctypes.data,
                        self.chi0.ctypes.data, self.eta0.ctypes.data, self.dvw.ctypes.data,

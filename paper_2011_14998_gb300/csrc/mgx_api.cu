@@ -44,6 +44,11 @@ struct Model {
     uint32_t *rays = nullptr;
     int32_t *sample = nullptr;  // device copy of the ray-set sample (adaptive sets)
     int64_t n_sample = 0;
+    // half-ray offsets of every origin, [2 n npairs + 1] on the device, and
+    // their values at origin boundaries, [n + 1] on the host: made by the first
+    // mgx_solve_J and kept until the ray set changes (the mesh never does)
+    int64_t *offs_all = nullptr;
+    std::vector<int64_t> obound;
 };
 
 // A batched solve kept for replay: its buffers and, in graph mode, the
@@ -338,6 +343,12 @@ void free_lines(mgx_ctx *ctx, Model &m) {
     m.has_lines = false;
 }
 
+void drop_offsets(mgx_ctx *ctx, Model &m) {
+    dfree(ctx, m.offs_all);
+    m.obound.clear();
+    m.obound.shrink_to_fit();
+}
+
 void free_model(mgx_ctx *ctx, Model &m) {
     dfree(ctx, m.x); dfree(ctx, m.y); dfree(ctx, m.z);
     dfree(ctx, m.vx); dfree(ctx, m.vy); dfree(ctx, m.vz);
@@ -347,6 +358,7 @@ void free_model(mgx_ctx *ctx, Model &m) {
     free_lines(ctx, m);
     dfree(ctx, m.rays);
     dfree(ctx, m.sample);
+    drop_offsets(ctx, m);
     m.has_rays = false;
     m.live = false;
 }
@@ -731,6 +743,7 @@ mgx_status mgx_set_rays(mgx_ctx *ctx, int32_t model, int32_t l_min, int32_t l_ma
     DeviceGuard g(ctx->device);
     mgx_status s = ensure_tables(ctx, l_max);
     if (s != MGX_OK) return s;
+    drop_offsets(ctx, *m);
     if (!m->rays || m->npairs != np) {
         dfree(ctx, m->rays);
         CK(dalloc(ctx, &m->rays, size_t(m->n) * size_t(np)));
@@ -838,19 +851,24 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         return fail(ctx, MGX_EINVAL, "solve_J: order must be 0, 2 or 4 (reserved 0)");
     DeviceGuard g(ctx->device);
     const int32_t n = m->n, np = m->npairs;
-    const int64_t n_half = int64_t(n) * np * 2;
-    int64_t *offs = nullptr;
-    mgx_status s = trace_offsets(ctx, *m, 0, n, &offs);
-    if (s != MGX_OK) return s;
-    // half-ray offsets at origin boundaries decide the chunks
-    std::vector<int64_t> obound(size_t(n) + 1);
-    CK(cudaMemcpy2DAsync(obound.data(), sizeof(int64_t), offs, size_t(2 * np) * sizeof(int64_t), sizeof(int64_t),
-                         size_t(n) + 1, cudaMemcpyDeviceToHost, ctx->stream));
-    s = sync_status(ctx);
-    if (s != MGX_OK) {
-        dfree(ctx, offs);
-        return s;
+    if (!m->offs_all) {
+        int64_t *offs = nullptr;
+        mgx_status s = trace_offsets(ctx, *m, 0, n, &offs);
+        if (s != MGX_OK) return s;
+        // half-ray offsets at origin boundaries decide the chunks
+        m->obound.assign(size_t(n) + 1, 0);
+        CK(cudaMemcpy2DAsync(m->obound.data(), sizeof(int64_t), offs, size_t(2 * np) * sizeof(int64_t),
+                             sizeof(int64_t), size_t(n) + 1, cudaMemcpyDeviceToHost, ctx->stream));
+        s = sync_status(ctx);
+        if (s != MGX_OK) {
+            dfree(ctx, offs);
+            m->obound.clear();
+            return s;
+        }
+        m->offs_all = offs;
     }
+    const int64_t *offs = m->offs_all;
+    const std::vector<int64_t> &obound = m->obound;
     const int64_t total = obound[size_t(n)];
     const int64_t budget = int64_t(ctx->arena_budget / sizeof(int32_t));
     std::vector<int32_t> cuts{0};
@@ -909,11 +927,9 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
         }
         CK(cudaGetLastError());
     }
-    (void)n_half;
     if (!p->out_on_device)
         CK(cudaMemcpyAsync(J_out, J, size_t(n) * size_t(NB) * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     dfree(ctx, aidx);
-    dfree(ctx, offs);
     if (!p->out_on_device) dfree(ctx, J);
     return sync_status(ctx);
 }

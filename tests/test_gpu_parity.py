@@ -168,6 +168,30 @@ def test_multiline_adaptive_J(ctx, orc, cloud_multi):
     assert r32 < FP32_TOL, r32
 
 
+def test_repeated_solve_and_new_ray_set(ctx, orc, wind_small):
+    """mgx_solve_J keeps the half-ray offsets of a model after its first call: a
+    second call gives the same J bit for bit, and a new ray set replaces them."""
+    import paper_2011_14998_gb300 as mgx
+
+    m = wind_small
+    mid = ctx.load(m)
+    J1 = ctx.solve_J(mid, precision=mgx.MGX_FP64)
+    J2 = ctx.solve_J(mid, precision=mgx.MGX_FP64)
+    assert np.array_equal(J1, J2)
+    n_pairs = ctx.models[mid]["npairs"]
+    ctx.set_rays(mid, 0, 2, m["sample"])  # adaptive levels 0-2 instead of the model's fixed level
+    rays = ctx.rays(mid)
+    J3 = ctx.solve_J(mid, precision=mgx.MGX_FP64)
+    ctx.set_rays(mid, m["l_min"], m["l_max"], m["sample"])
+    J4 = ctx.solve_J(mid, precision=mgx.MGX_FP64)
+    ctx.free(mid)
+    assert rays.shape[1] != n_pairs
+    assert np.array_equal(J4, J1)
+    o = np.arange(0, len(m["pos"]), 7)
+    Jo = _oracle(orc, m, rays=rays, l_min=0, l_max=2).solve_J(orc.params(), origins=o)
+    assert j_rel_err(J3[o], Jo)[0] < FP64_TOL
+
+
 def test_J_device_output_matches_host(ctx, wind_small):
     import torch
 
