@@ -28,6 +28,13 @@
  *                                       parity unpinned (conventions, not in the paper)
  *   reduction criterion .............. pinned (hand-computed graphs, Gf in [0,1],
  *                                       thinning rate)
+ *   Hermitian solve .................. pinned (uniform-grid Numerov system, exact
+ *                                       quadratics, third-order convergence)
+ *   per-ray u ........................ pinned (sum of 2 w u equals J)
+ *   analytic size field .............. pinned (exponential closed form, Gaussian
+ *                                       convergence, thinning rate)
+ *   single-precision decisions ....... pinned (a constructed velocity jump that rounds
+ *                                       to another count in single precision)
  */
 #include <math.h>
 #include <stdint.h>
