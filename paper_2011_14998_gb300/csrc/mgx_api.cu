@@ -391,7 +391,11 @@ mgx_status trace_offsets(mgx_ctx *ctx, Model &m, int32_t o0, int32_t o1, int64_t
     if (n_half > 0) {
         Timed t(ctx, MGX_K_SCAN);
         const mgx_status s = scan_i64(ctx, lens, offs + 1, n_half);
-        if (s != MGX_OK) return s;
+        if (s != MGX_OK) {
+            dfree(ctx, lens);
+            dfree(ctx, offs);
+            return s;
+        }
     }
     dfree(ctx, lens);
     *offs_out = offs;
