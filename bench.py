@@ -175,7 +175,7 @@ def run_reference(args):
     pr = oracle.params(dtau_max=0.5, dv_max=1.0 / 3.0)
     rng = np.random.default_rng(1)
     per_step = max(threads, 4 * threads)  # origins per step: bounded sample
-    for _ in range(args.warmup if args.warmup < 2 else 1):
+    for _ in range(args.warmup):  # untimed, one origin per thread each
         om.solve_J(pr, origins=rng.integers(0, len(m["pos"]), threads), threads=threads)
     times, solves = [], 0
     for _ in range(args.steps):
