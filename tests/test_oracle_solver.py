@@ -154,6 +154,25 @@ def test_velocity_sampling_counts(orc):
     assert np.allclose(dtau[:6], 1e-3 / 6, rtol=1e-13) and np.allclose(dtau[6:], 1e-3 / 3, rtol=1e-13)
 
 
+def test_static_medium_line_mapping(orc):
+    # No motion: the Doppler factor is exactly one, so the profile argument of a
+    # line at its own bins is the rounded x dv_o / dv, and velocity sampling
+    # inserts nothing (a pair line is the traced points plus the origin).
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        nu, x, dvo, dv = 115.2712018e9 * rng.uniform(0.5, 2), rng.uniform(-5, 5), rng.uniform(0.1, 3), rng.uniform(0.1, 3)
+        assert orc.profile_arg(nu, nu, x, dvo, 0.0, dv) == (x * dvo) / dv
+    import synth
+
+    m = synth.grid_model(6, level=1)
+    om = orc.OracleModel(m)
+    for o in (0, 43, 100, 215):
+        for ray in om.rays[o]:
+            d = orc.pix2vec(int(ray >> 28), int(ray & 0x0FFFFFFF))
+            nb, nf = len(om.trace_half(o, -d)[0]), len(om.trace_half(o, d)[0])
+            assert om.vline_size(o, ray, orc.params(dv_max=1 / 3)) == (nb + nf + 1, nb)
+
+
 def test_velocity_count_single_precision_projection(orc):
     # The single-precision decision projects the velocities rounded to single.
     # Origin v = 0.7, forward neighbour v = 2.7000001586834803 (direction +x):
