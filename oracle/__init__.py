@@ -46,7 +46,7 @@ class Model(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("dtau_max", C.c_double), ("dv_max", C.c_double), ("I_bdy", C.c_double),
-                ("decide32", C.c_int32), ("order", C.c_int32)]
+                ("order", C.c_int32)]
 
 
 def lib():
@@ -67,7 +67,7 @@ def lib():
                 "orc_trace_half": (i64, [vp, i64, vp, i64, vp, vp]),
                 "orc_profile_arg": (dbl, [dbl, dbl, dbl, dbl, dbl, dbl]),
                 "orc_bin_x": (dbl, [i32, dbl, i32]),
-                "orc_subdivide": (i64, [i64, vp, vp, vp, i64, dbl, i32, i64, vp, vp, vp]),
+                "orc_subdivide": (i64, [i64, vp, vp, vp, i64, dbl, i64, vp, vp, vp]),
                 "orc_feautrier": (dbl, [i64, vp, vp, i64, dbl, vp]),
                 "orc_feautrier4": (dbl, [i64, vp, vp, i64, dbl, vp]),
                 "orc_analytic_mesh": (i64, [i32, i32, i32, vp, dbl, dbl, dbl, C.c_uint64, vp, vp, vp]),
@@ -218,13 +218,11 @@ class OracleModel:
         return u
 
 
-def params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, decide32=False, order=2) -> Params:
-    """decide32: take the velocity-sample count and Eq. 2's n_inter in single
-    precision, the precision in which the single-precision kernel decides them.
-    order: 2 (second-order scheme) or 4 (Hermitian scheme, Section 2.1)."""
+def params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, order=2) -> Params:
+    """order: 2 (second-order scheme) or 4 (Hermitian scheme, Section 2.1)."""
     if order not in (2, 4):
         raise ValueError("order must be 2 or 4")
-    return Params(dtau_max, dv_max, I_bdy, int(bool(decide32)), int(order))
+    return Params(dtau_max, dv_max, I_bdy, int(order))
 
 
 def feautrier(dtau, S, io, I_bdy=0.0, all_rows=False, order=2):
@@ -237,15 +235,15 @@ def feautrier(dtau, S, io, I_bdy=0.0, all_rows=False, order=2):
     return u if all_rows else uo
 
 
-def subdivide(s, chi, eta, io, dtau_max, max_pts=1 << 20, decide32=False):
+def subdivide(s, chi, eta, io, dtau_max, max_pts=1 << 20):
     s = np.ascontiguousarray(s, np.float64)
     chi = np.ascontiguousarray(chi, np.float64)
     eta = np.ascontiguousarray(eta, np.float64)
     dtau = np.empty(max_pts)
     S = np.empty(max_pts + 1)
     ioo = C.c_int64(0)
-    M = lib().orc_subdivide(len(s), _p(s), _p(chi), _p(eta), int(io), float(dtau_max), int(decide32),
-                            max_pts, _p(dtau), _p(S), C.byref(ioo))
+    M = lib().orc_subdivide(len(s), _p(s), _p(chi), _p(eta), int(io), float(dtau_max), max_pts, _p(dtau),
+                            _p(S), C.byref(ioo))
     if M < 0:
         raise ValueError("too many sub-points")
     return dtau[:M].copy(), S[:M + 1].copy(), int(ioo.value)

@@ -33,8 +33,6 @@
  *   per-ray u ........................ pinned (sum of 2 w u equals J)
  *   analytic size field .............. pinned (exponential closed form, Gaussian
  *                                       convergence, thinning rate)
- *   single-precision decisions ....... pinned (a constructed velocity jump that rounds
- *                                       to another count in single precision)
  */
 #include <math.h>
 #include <stdint.h>
@@ -307,14 +305,6 @@ typedef struct {
     double dtau_max; /* Eq. 2 */
     double dv_max;   /* velocity step limit, in units of the smaller Doppler width (<= 0: off) */
     double I_bdy;    /* boundary intensity entering both ends of every ray    */
-    int32_t decide32; /* take the two integer decisions in single precision, as
-                         the single-precision form of the solver does: the
-                         velocity-sample count as ceil(|d delta| / limit), on
-                         delta projected in single precision from the
-                         velocities and direction rounded to single, and
-                         Eq. 2's n_inter as 1 unless chi_max > dtau_max / ds,
-                         else ceil((chi_max ds) fl32(1/dtau_max));
-                         everything else stays double */
     int32_t order;    /* 2: the second-order scheme with second-order boundary
                          conditions; 4: Auer's (1976) Hermitian fourth-order
                          scheme with third-order boundary conditions (Section 2.1) */
@@ -394,7 +384,6 @@ double orc_bin_x(int32_t n_freq, double x_span, int32_t k)
 typedef struct {
     double s, delta, dvw, chic, etac;
     double chi0[ORC_MAX_LINES], eta0[ORC_MAX_LINES];
-    float delta32; /* delta projected in single precision (base points only) */
 } orc_sample;
 
 typedef struct {
@@ -436,24 +425,10 @@ static void sample_lerp(int L, const orc_sample *a, const orc_sample *b, double 
     x->dvw = a->dvw + (b->dvw - a->dvw) * t;
     x->chic = a->chic + (b->chic - a->chic) * t;
     x->etac = a->etac + (b->etac - a->etac) * t;
-    x->delta32 = 0.0f;
     for (int l = 0; l < L; ++l) {
         x->chi0[l] = a->chi0[l] + (b->chi0[l] - a->chi0[l]) * t;
         x->eta0[l] = a->eta0[l] + (b->eta0[l] - a->eta0[l]) * t;
     }
-}
-
-/* (v_n - v_o).d in single precision: every operand rounded to single, the
- * components differenced, then (x + y) + z with each product and sum rounded
- * (the sources are compiled without contraction).  Only the decide32 form of
- * the velocity-sample count reads it. */
-static float delta_single(const double *vn, const double *vo, const double d[3])
-{
-    const float ux = (float)vn[0] - (float)vo[0];
-    const float uy = (float)vn[1] - (float)vo[1];
-    const float uz = (float)vn[2] - (float)vo[2];
-    const float px = ux * (float)d[0], py = uy * (float)d[1], pz = uz * (float)d[2];
-    return (px + py) + pz;
 }
 
 /* Build the velocity-sampled pair line of origin o along +-r.  The base points
@@ -490,28 +465,19 @@ static void build_vline(const orc_model *m, const orc_params *pr, int64_t o, con
             const double *vn = m->vel + 3 * id;
             const double de = ((vn[0] - vo[0]) * rm[0] + (vn[1] - vo[1]) * rm[1]) + (vn[2] - vo[2]) * rm[2];
             sample_of_point(m, id, -bz[nb - 1 - k], de, &cur);
-            cur.delta32 = delta_single(vn, vo, rm);
         } else if (k == nb) {
             sample_of_point(m, o, 0.0, 0.0, &cur);
-            cur.delta32 = 0.0f;
         } else {
             const int64_t id = fi[k - nb - 1];
             const double *vn = m->vel + 3 * id;
             const double de = ((vn[0] - vo[0]) * r[0] + (vn[1] - vo[1]) * r[1]) + (vn[2] - vo[2]) * r[2];
             sample_of_point(m, id, fz[k - nb - 1], de, &cur);
-            cur.delta32 = delta_single(vn, vo, r);
         }
         if (k > 0 && pr->dv_max > 0.0) {
             int64_t parts = 1;
-            if (pr->decide32) {
-                const float jump = fabsf(cur.delta32 - prev.delta32);
-                const float lim = (float)pr->dv_max * fminf((float)prev.dvw, (float)cur.dvw);
-                if (jump > lim) parts = (int64_t)ceilf(jump / lim);
-            } else {
-                const double jump = fabs(cur.delta - prev.delta);
-                const double lim = pr->dv_max * fmin(prev.dvw, cur.dvw);
-                if (jump > lim) parts = (int64_t)ceil(jump / lim);
-            }
+            const double jump = fabs(cur.delta - prev.delta);
+            const double lim = pr->dv_max * fmin(prev.dvw, cur.dvw);
+            if (jump > lim) parts = (int64_t)ceil(jump / lim);
             if (parts > 1) {
                 for (int64_t j = 1; j < parts; ++j) {
                     sample_lerp(L, &prev, &cur, (double)j / (double)parts, &mid);
@@ -554,8 +520,8 @@ static void line_optics(const orc_model *m, const orc_vline *v, double dv_o, int
  * sub-divided line, and the index of the origin.  Returns M, or -1 when the
  * line would exceed max_pts. */
 int64_t orc_subdivide(int64_t mv, const double *s, const double *chi, const double *eta,
-                      int64_t io, double dtau_max, int32_t decide32, int64_t max_pts, double *dtau,
-                      double *S, int64_t *io_out)
+                      int64_t io, double dtau_max, int64_t max_pts, double *dtau, double *S,
+                      int64_t *io_out)
 {
     int64_t M = 0;
     S[0] = eta[0] / chi[0];
@@ -563,16 +529,7 @@ int64_t orc_subdivide(int64_t mv, const double *s, const double *chi, const doub
     for (int64_t i = 0; i + 1 < mv; ++i) {
         const double ds = s[i + 1] - s[i];
         const double cmax = fmax(chi[i], chi[i + 1]);
-        /* Eq. 2.  In single precision the test "more than one part" is the
-         * equivalent inequality chi_max > dtau_max / ds, and the count is
-         * formed only when it holds. */
-        int64_t ni = 1;
-        if (decide32) {
-            const float cm = (float)cmax, dsf = (float)ds, dtm = (float)dtau_max;
-            if (cm > dtm / dsf) ni = (int64_t)ceilf((cm * dsf) * (float)(1.0 / dtau_max));
-        } else {
-            ni = (int64_t)ceil(cmax * ds / dtau_max);
-        }
+        int64_t ni = (int64_t)ceil(cmax * ds / dtau_max); /* Eq. 2 */
         if (ni < 1) ni = 1;
         if (M + ni > max_pts) return -1;
         const double h = ds / (double)ni;
@@ -602,7 +559,7 @@ static int64_t orc_subdivide_v(const orc_vline *v, const double *chi, const doub
 {
     double *s = (double *)malloc(sizeof(double) * (size_t)v->m);
     for (int64_t i = 0; i < v->m; ++i) s[i] = v->p[i].s;
-    const int64_t M = orc_subdivide(v->m, s, chi, eta, v->io, pr->dtau_max, pr->decide32, max_pts, dtau, S, io);
+    const int64_t M = orc_subdivide(v->m, s, chi, eta, v->io, pr->dtau_max, max_pts, dtau, S, io);
     free(s);
     return M;
 }

@@ -173,22 +173,22 @@ def test_static_medium_line_mapping(orc):
             assert om.vline_size(o, ray, orc.params(dv_max=1 / 3)) == (nb + nf + 1, nb)
 
 
-def test_velocity_count_single_precision_projection(orc):
-    # The single-precision decision projects the velocities rounded to single.
-    # Origin v = 0.7, forward neighbour v = 2.7000001586834803 (direction +x):
-    #   FP64: jump 2.00000015868... / (1/3) = 6.0000005 -> 7 parts;
-    #   single: fl32(2.70000016) - fl32(0.7) = 2.700000048 - 0.699999988 = 2.0 exactly,
-    #   and 2.0 / fl32(1/3) = 6.0 -> 6 parts.
-    # Rounding the FP64 jump instead gives fl32(2.00000016) = 2.00000024 -> 7 parts.
+def test_velocity_count_at_a_near_tie(orc):
+    # Section 2.1.1: an interval is split into ceil(|jump| / limit) parts.  Origin
+    # v = 0.7, forward neighbour v = 2.7000001586834803 (direction +x), limit
+    # 1/3 of the unit Doppler width: the jump is 2.00000015868... = 6.0000005
+    # limits, so 7 parts (6 interpolated samples), although the jump of the
+    # velocities rounded to single precision is exactly 6 limits.
     m = line_model(vel_a=0.7, vel_b=2.7000001586834803)
     m["vel"][1, 0] = 0.7
     om = orc.OracleModel(m, rays=np.zeros((3, 6), np.uint32))
     ray = np.uint32(4)
     assert om.vline_size(1, ray, orc.params(dv_max=1 / 3)) == (2 + 7, 1)
-    assert om.vline_size(1, ray, orc.params(dv_max=1 / 3, decide32=True)) == (2 + 6, 1)
-    # one sub-sample fewer is a discretisation change well above the FP32 budget
-    x = [orc.feautrier(*om.pair_line(1, ray, 0, 2, orc.params(dv_max=1 / 3, decide32=d))) for d in (False, True)]
-    assert abs(x[1] - x[0]) > 1e-3 * x[0]
+    # an exact multiple of the limit is not split further: jump 2.0 = 6 limits of 1/3
+    m2 = line_model(vel_a=0.7, vel_b=2.0 + 0.5)
+    m2["vel"][1, 0] = 0.5
+    om2 = orc.OracleModel(m2, rays=np.zeros((3, 6), np.uint32))
+    assert om2.vline_size(1, ray, orc.params(dv_max=0.25)) == (2 + 8, 1)
 
 
 def _grid_closed_form(orc, m, om, params, origins):
@@ -248,12 +248,16 @@ def test_J_weights_sum_to_one(orc):
     assert np.allclose(J, 0.5, rtol=1e-12)
 
 
-def test_decision_precision_flag(orc):
-    # chi (5 + 5e-10) * ds 0.2 / dtau_max 0.5 is just above 2 in double precision
-    # (3 sub-intervals) and exactly 2 in single precision (2 sub-intervals)
+def test_subdivision_count_at_the_ceiling(orc):
+    # Eq. 2: n_inter = ceil(chi_max ds / dtau_max).  chi (5 + 5e-10) ds 0.2 /
+    # dtau_max 0.5 is just above 2 in double precision -> 3 sub-intervals;
+    # chi = 5 gives exactly 2 -> 2 sub-intervals; the sub-interval optical
+    # depths sum to the trapezoid of the interval either way.
     s = np.array([0.0, 0.2])
-    chi = np.array([5.0 + 5e-10, 5.0 + 5e-10])
-    d64, _, _ = orc.subdivide(s, chi, chi, 0, 0.5)
-    d32, _, _ = orc.subdivide(s, chi, chi, 0, 0.5, decide32=True)
-    assert len(d64) == 3 and len(d32) == 2
-    assert d64.sum() == pytest.approx(d32.sum(), rel=1e-15)
+    chi_a = np.array([5.0 + 5e-10, 5.0 + 5e-10])
+    chi_b = np.array([5.0, 5.0])
+    da, _, _ = orc.subdivide(s, chi_a, chi_a, 0, 0.5)
+    db, _, _ = orc.subdivide(s, chi_b, chi_b, 0, 0.5)
+    assert len(da) == 3 and len(db) == 2
+    assert da.sum() == pytest.approx(0.2 * chi_a[0], rel=1e-15)
+    assert db.sum() == pytest.approx(0.2 * chi_b[0], rel=1e-15)
