@@ -7,8 +7,8 @@ device-resident inputs: ray set -> trace (padded rows + overflow) -> velocity
 and optical-depth sampling -> Feautrier solve of every (point, pair, bin) -> J.
 
 Metric: ray-pair x frequency Feautrier solves per second of the single-precision
-form (FP64 only for distance increments and the J sum); the FP64 plain form is
-timed beside it.  Under torchrun every rank solves its own replica of the
+form (FP64 for the distance increments, the integer decisions of Section 2.1.1
+and Eq. 2, and the J sum); the FP64 plain form is timed beside it.  Under torchrun every rank solves its own replica of the
 workload (independent models, no collective: weak scaling); value is the total
 over ranks divided by the slowest rank's time.
 
@@ -30,7 +30,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "ray-pair x frequency Feautrier solves/s (FP32 form, FP64 dtau/J-sum) on the 50k-point wind"
+METRIC = "ray-pair x frequency Feautrier solves/s (FP32 form; FP64 distance increments, decisions, J sum) on the 50k-point wind"
 UNIT = "solves/s"
 WORKLOAD = dict(workload="stellar wind, 50000 points, Delaunay neighbours, 1 line x 50 bins, nside 4 "
                          "(96 ray pairs/point), dtau_max 0.5, dv_max 1/3 Doppler width",
@@ -363,8 +363,12 @@ def run_mgx(args):
     flops = (FLOPS_PER_UPDATE * prof32["updates"] + FLOPS_PER_SAMPLE_LINE * len(m["nu0"]) * prof32["samples"])
     flops_per_launch = flops / max(1, prof32["launches"]["solve"])
     achieved = flops_per_launch / (ms_solve * 1e-3) / 1e12
-    arena_bytes = prof32["trace_points"] * 12 * ((NB + 31) // 32) + n * NB * 8  # point lists per tile + J
-    hbm_gbs = arena_bytes / max(1, prof32["launches"]["solve"]) / (ms_solve * 1e-3) / 1e9
+    # algorithmic bytes of the solve: a 4-byte point id per traced point and frequency tile (the tile is
+    # 32 x bins-per-lane bins), the point data once (positions and velocities in double and single precision,
+    # width, continuum and line data: 56 + 8 (L - 1) bytes) and 8 bytes of J per (point, bin)
+    tiles = -(-NB // (32 * int(tuning.get("bins_per_lane") or 2)))
+    solve_bytes = (prof32["trace_points"] // kb) * 4 * tiles + n * (56 + 8 * (len(m["nu0"]) - 1)) + n * NB * 8
+    hbm_gbs = solve_bytes / (ms_solve * 1e-3) / 1e9
     step_ms = {k: v / kb for k, v in prof32["ms"].items()}
     # own kernels per step: ray sets, padded trace, tail trace, the work-list kernels (three for the
     # cost-binned schedule, one for plain order), the solve (scans and the sort are CUB's)
@@ -393,11 +397,12 @@ def run_mgx(args):
         "work_per_step": {"solves": solves_per_step, "trace_points": prof32["trace_points"] // kb,
                           "updates": prof32["updates"] // kb, "samples": prof32["samples"] // kb,
                           "trace_steps": prof32["trace_steps"] // kb,
-                          "trace_steps_redone_fp64": prof32["trace_exact_steps"] // kb},
+                          "trace_steps_redone_fp64": prof32["trace_exact_steps"] // kb,
+                          "solve_decisions_redone_fp64": prof32["decisions_redone"] // kb},
         "roofline": {"kernel": "k_solve_queue<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",
-                     "hbm_algorithmic_gbs": hbm_gbs},
+                     "hbm_algorithmic_gbs": hbm_gbs, "hbm_algorithmic_bytes_per_launch": solve_bytes},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
@@ -416,12 +421,12 @@ SOLVE_SOURCES = ("k_solve_impl.cuh", "k_solve.cu")
 
 def hermitian_accuracy(m, rays, J32h, n=200):
     """Largest relative error of the FP32 Hermitian step against the oracle's
-    Hermitian solve (single-precision decisions) on n random origins."""
+    Hermitian solve on n random origins."""
     import oracle
 
     om = oracle.OracleModel(m, rays=rays)
     o = np.sort(np.random.default_rng(5).choice(len(m["pos"]), n, replace=False))
-    Jo = om.solve_J(oracle.params(dtau_max=0.5, dv_max=1.0 / 3.0, decide32=True, order=4), origins=o)
+    Jo = om.solve_J(oracle.params(dtau_max=0.5, dv_max=1.0 / 3.0, order=4), origins=o)
     mask = np.abs(Jo) > 1e-6 * np.abs(Jo).max(axis=1, keepdims=True)
     rel = np.abs(J32h[o] - Jo)[mask] / np.abs(Jo[mask])
     return {"fp32_max_rel": float(rel.max()), "fp32_p99_rel": float(np.quantile(rel, 0.99)), "origins": n}

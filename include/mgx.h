@@ -51,8 +51,12 @@ enum {
 /* arithmetic forms of the formal solution */
 enum {
     MGX_FP64 = 0, /* plain form: every step in double precision                    */
-    MGX_FP32 = 1  /* single-precision bulk; double only for the distance increments
-                     along the ray and the compensated J sum                        */
+    MGX_FP32 = 1  /* single-precision bulk; double for the distance increments along
+                     the ray and the compensated J sum.  The integer decisions (the
+                     velocity-sample count of Section 2.1.1, Eq. 2's n_inter) are
+                     the double-precision definition's: taken in single precision
+                     under a rigorous error bound, redone in double precision
+                     where the bound leaves the integer open                        */
 };
 
 /* Limits. */
@@ -316,10 +320,11 @@ mgx_status mgx_autotune(mgx_ctx *ctx, const int32_t *models, int32_t n_models, c
  * MGX_ERANGE when the ray set has too many pairs for the array or when one
  * origin's traced point lists alone do not fit (more than about 14 million
  * points).  No cudaMalloc, cudaFree or allocating library routine is called.
- * The first call on a device looks up the array's device address (set-up); make
- * that first call before any stream capture.  Every call shares the array:
- * calls that overlap on the GPU (other streams or contexts on the same device)
- * race on it.  The call synchronises the stream. */
+ * The first call on a device looks up the array's device address (set-up).
+ * The call cannot be captured in a CUDA graph: for every chunk it reads the
+ * traced total back to the host and synchronises the stream.  Every call
+ * shares the array: calls that overlap on the GPU (other streams or contexts
+ * on the same device) race on it. */
 mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params,
                                double *J_out);
 
@@ -364,6 +369,16 @@ mgx_status mgx_mlp_features(mgx_ctx *ctx, int32_t model, const double *rho, cons
 mgx_status mgx_reduce_mesh_learned(mgx_ctx *ctx, int32_t model, const float *X, double keep_fraction, uint8_t *keep,
                                    int64_t *n_kept);
 
+/* The approximate single-precision functions of the single-precision solve,
+ * for tests of the error bounds its integer decisions (velocity-sample counts,
+ * Eq. 2 sub-interval counts) are certified with; no counterpart in the paper.
+ * kind 0: y = 2^x as the solve evaluates exp(-a^2); kind 1: y = 1/x.  x, y [n]
+ * are device pointers on the context's device; the work is enqueued on the
+ * context's stream (no synchronisation).  *bound (may be NULL) receives the
+ * largest relative error the solve assumes for that function.  MGX_EINVAL for
+ * another kind, n < 0, or null arrays with n > 0. */
+mgx_status mgx_eval_approx(mgx_ctx *ctx, int32_t kind, const float *x, int64_t n, float *y, float *bound);
+
 /* Kernel-level profiling.  While enabled, every kernel launch of the context is
  * bracketed by CUDA events on the context's stream and the work counters below
  * are accumulated on the device; mgx_profile_read synchronises the stream and
@@ -388,6 +403,9 @@ typedef struct {
     int64_t trace_steps;           /* tracer steps of the counting pass               */
     int64_t trace_exact_steps;     /* of those, steps the single-precision screen could
                                       not decide, redone in double precision          */
+    int64_t decisions_redone;      /* integer decisions of the single-precision solve (velocity-
+                                      sample counts, Eq. 2 sub-interval counts) that its error
+                                      bound left open, redone in double precision     */
 } mgx_profile;
 
 /* enable != 0 starts (and resets) profiling; 0 stops it. */

@@ -29,7 +29,7 @@ ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs
                "mgx_solve_J_noalloc", "mgx_solve_J_batch", "mgx_mlp_set_params", "mgx_mlp_get_params",
                "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned",
                "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune", "mgx_analytic_mesh", "mgx_solve_u",
-               "mgx_pix2vec", "mgx_antipode", "mgx_reduce_mesh_learned_weighted")
+               "mgx_pix2vec", "mgx_antipode", "mgx_reduce_mesh_learned_weighted", "mgx_eval_approx")
 MGX_MLP_NPARAM = 4801
 MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
@@ -50,7 +50,7 @@ class SolveParams(C.Structure):
 class Profile(C.Structure):
     _fields_ = [("ms", C.c_double * 6), ("launches", C.c_int64 * 6), ("trace_points", C.c_int64),
                 ("solves", C.c_int64), ("updates", C.c_int64), ("samples", C.c_int64),
-                ("trace_steps", C.c_int64), ("trace_exact_steps", C.c_int64)]
+                ("trace_steps", C.c_int64), ("trace_exact_steps", C.c_int64), ("decisions_redone", C.c_int64)]
 
 
 class Tuning(C.Structure):
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH):
         "mgx_reduce_mesh_learned": (i32, [vp, i32, vp, dbl, vp, C.POINTER(i64)]),
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
+        "mgx_eval_approx": (i32, [vp, i32, vp, i64, vp, C.POINTER(C.c_float)]),
         "mgx_set_tuning": (i32, [vp, C.POINTER(Tuning)]),
         "mgx_pix2vec": (i32, [i32, i64, vp]),
         "mgx_reduce_mesh_learned_weighted": (i32, [vp, i32, vp, dbl, dbl, u64, vp, C.POINTER(i64),
@@ -201,12 +202,15 @@ def mgx_get_rays(ctx, model, n, npairs) -> np.ndarray:
     return out
 
 
-def mgx_trace(ctx, model, o_begin, o_end, npairs, with_delta=False):
-    """Returns (off [n_half+1], idx, Z, delta-or-None)."""
+def mgx_trace(ctx, model, o_begin, o_end, npairs, with_delta=False, ids=True):
+    """Returns (off [n_half+1], idx, Z, delta-or-None); with ids=False only the
+    offsets are traced and (off, None, None, None) is returned."""
     n_half = (o_end - o_begin) * npairs * 2
     off = np.empty(n_half + 1, np.int64)
     L = load_library()
     _check(ctx, L.mgx_trace(ctx, int(model), int(o_begin), int(o_end), _ptr(off), None, None, None, 0))
+    if not ids:
+        return off, None, None, None
     tot = int(off[-1])
     idx = np.empty(max(tot, 1), np.int32)
     Z = np.empty(max(tot, 1), np.float64)
@@ -363,6 +367,15 @@ def mgx_reduce_mesh(ctx, model, f, f_small, f_large, G_thres, seed):
     return Gf, L_, ell, keep, int(nk.value)
 
 
+def mgx_eval_approx(ctx, kind: int, x, y) -> float:
+    """y = 2^x (kind 0) or 1/x (kind 1) by the solve's approximate single-precision
+    functions; x, y float32 device tensors of the same size.  Returns the relative
+    error bound the solve assumes for that function."""
+    b = C.c_float(0.0)
+    _check(ctx, load_library().mgx_eval_approx(ctx, int(kind), _ptr(x), int(x.numel()), _ptr(y), C.byref(b)))
+    return float(b.value)
+
+
 def mgx_profile_enable(ctx, enable: bool = True) -> None:
     _check(ctx, load_library().mgx_profile_enable(ctx, int(bool(enable))))
 
@@ -374,7 +387,7 @@ def mgx_profile_read(ctx) -> dict:
                 launches={k: int(p.launches[i]) for i, k in enumerate(KERNEL_CLASSES)},
                 trace_points=int(p.trace_points), solves=int(p.solves), updates=int(p.updates),
                 samples=int(p.samples), trace_steps=int(p.trace_steps),
-                trace_exact_steps=int(p.trace_exact_steps))
+                trace_exact_steps=int(p.trace_exact_steps), decisions_redone=int(p.decisions_redone))
 
 
 def solve_params(dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, precision=MGX_FP64, out_on_device=False, order=2):
@@ -428,9 +441,9 @@ class Context:
         i = self.models[mid]
         return mgx_get_rays(self.ptr, mid, i["n"], i["npairs"])
 
-    def trace(self, mid, o_begin=0, o_end=None, with_delta=False):
+    def trace(self, mid, o_begin=0, o_end=None, with_delta=False, ids=True):
         i = self.models[mid]
-        return mgx_trace(self.ptr, mid, o_begin, i["n"] if o_end is None else o_end, i["npairs"], with_delta)
+        return mgx_trace(self.ptr, mid, o_begin, i["n"] if o_end is None else o_end, i["npairs"], with_delta, ids)
 
     def solve_J(self, mid, precision=MGX_FP64, dtau_max=0.5, dv_max=1.0 / 3.0, I_bdy=0.0, out=None, order=2):
         """J [n, L*F] float64; `out` may be a CUDA float64 tensor (device output)."""

@@ -21,6 +21,8 @@ using namespace mgx;
 
 namespace {
 
+constexpr int kCounters = 8;  // device work counters of a context (see mgx_ctx::d_counters)
+
 struct Model {
     bool live = false;
     int32_t n = 0;
@@ -101,7 +103,8 @@ struct mgx_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[MGX_K_COUNT];
     int64_t launches[MGX_K_COUNT] = {};
     std::vector<cudaEvent_t> event_pool;
-    unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples, [2] trace steps, [3] redone
+    unsigned long long *d_counters = nullptr;  // [0] updates, [1] samples, [2] trace steps, [3] redone,
+                                               // [4] solve decisions redone in double, [5..7] spare
     int64_t trace_points = 0, solves = 0;
     BatchPlan plan;
     mgx_tuning tune{};  // launch parameters of the batched solve (zero: automatic)
@@ -234,7 +237,7 @@ void reset_profile(mgx_ctx *c) {
     for (auto &l : c->launches) l = 0;
     c->trace_points = 0;
     c->solves = 0;
-    if (c->d_counters) cudaMemsetAsync(c->d_counters, 0, 4 * sizeof(unsigned long long), c->stream);
+    if (c->d_counters) cudaMemsetAsync(c->d_counters, 0, kCounters * sizeof(unsigned long long), c->stream);
 }
 
 Model *get_model(mgx_ctx *ctx, int32_t id) {
@@ -551,8 +554,8 @@ mgx_status mgx_create(int device, void *stream, mgx_ctx **out) {
     CK(cudaMalloc(&c->d_status, sizeof(int)));
     CK(cudaMemset(c->d_status, 0, sizeof(int)));
     CK(cudaMallocHost(&c->h_status, sizeof(int)));
-    CK(cudaMalloc(&c->d_counters, 4 * sizeof(unsigned long long)));
-    CK(cudaMemset(c->d_counters, 0, 4 * sizeof(unsigned long long)));
+    CK(cudaMalloc(&c->d_counters, kCounters * sizeof(unsigned long long)));
+    CK(cudaMemset(c->d_counters, 0, kCounters * sizeof(unsigned long long)));
     *out = c.release();
     return MGX_OK;
 }
@@ -1033,7 +1036,7 @@ mgx_status mgx_solve_u(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, i
     a.J = J;
     a.u_out = u;
     a.status = ctx->d_status;
-    a.counters = nullptr;
+    a.counters = ctx->prof ? ctx->d_counters : nullptr;
     fill_pair_weights(a);
     {
         Timed t(ctx, MGX_K_SOLVE);
@@ -1692,6 +1695,18 @@ mgx_status mgx_reduce_mesh_learned_weighted(mgx_ctx *ctx, int32_t model, const f
     return MGX_OK;
 }
 
+mgx_status mgx_eval_approx(mgx_ctx *ctx, int32_t kind, const float *x, int64_t n, float *y, float *bound) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (kind != 0 && kind != 1) return fail(ctx, MGX_EINVAL, "eval_approx: kind must be 0 or 1");
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(ctx, MGX_EINVAL, "eval_approx: bad arrays");
+    if (bound) *bound = approx_bound(kind);
+    DeviceGuard g(ctx->device);
+    launch_eval_approx(kind, x, n, y, ctx->stream);
+    CK(cudaGetLastError());
+    return MGX_OK;
+}
+
 mgx_status mgx_profile_enable(mgx_ctx *ctx, int32_t enable) {
     if (!ctx) return MGX_EINVAL;
     ctx->err.clear();
@@ -1706,7 +1721,7 @@ mgx_status mgx_profile_read(mgx_ctx *ctx, mgx_profile *out) {
     if (!ctx || !out) return MGX_EINVAL;
     ctx->err.clear();
     DeviceGuard g(ctx->device);
-    unsigned long long cnt[4] = {0, 0, 0, 0};
+    unsigned long long cnt[kCounters] = {};
     CK(cudaMemcpyAsync(cnt, ctx->d_counters, sizeof cnt, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     std::memset(out, 0, sizeof *out);
@@ -1726,6 +1741,7 @@ mgx_status mgx_profile_read(mgx_ctx *ctx, mgx_profile *out) {
     out->samples = int64_t(cnt[1]);
     out->trace_steps = int64_t(cnt[2]);
     out->trace_exact_steps = int64_t(cnt[3]);
+    out->decisions_redone = int64_t(cnt[4]);
     return MGX_OK;
 }
 

@@ -237,6 +237,12 @@ void launch_mlp_features(const DevMesh &m, const float *chi0, int32_t L, const f
 void launch_select_top(const float *score, int64_t n, int64_t k, int32_t *ids, float *score_sorted,
                        int32_t *ids_sorted, uint8_t *keep, cudaStream_t st);
 
+// ---- approximate single-precision functions of the solve (k_approx.cu):
+// kind 0: 2^x (ex2.approx.ftz.f32), kind 1: 1/x (rcp.approx.ftz.f32); and the
+// relative error bound the solve's decisions take for each
+void launch_eval_approx(int kind, const float *x, int64_t n, float *y, cudaStream_t st);
+float approx_bound(int kind);
+
 // ---- host HEALPix tables (hpx_host.cpp)
 int64_t hpx_npix(int l);
 void hpx_pix2vec(int l, int64_t p, double v[3]);

@@ -52,9 +52,8 @@ def test_hermitian_fp64_and_fp32(ctx, orc, name):
     ctx.free(mid)
     om = orc.OracleModel(m, rays=rays)
     Jo = om.solve_J(orc.params(order=4, **kw), origins=origins)
-    Jo32 = om.solve_J(orc.params(order=4, decide32=True, **kw), origins=origins)
     assert j_rel_err(J64[origins], Jo)[0] < FP64_TOL
-    assert j_rel_err(J32[origins], Jo32)[0] < FP32_TOL
+    assert j_rel_err(J32[origins], Jo)[0] < FP32_TOL
     assert not np.array_equal(J64, J2)  # the order parameter reaches the kernel
 
 
@@ -107,8 +106,8 @@ def test_hermitian_batched_graph_and_noalloc(ctx, orc):
         ctx.free(k)
     om = orc.OracleModel(models[1], rays=rays)
     o = np.arange(0, len(models[1]["pos"]), 11)
-    Jo32 = om.solve_J(orc.params(order=4, decide32=True), origins=o)
-    assert j_rel_err(outs[1].cpu().numpy()[o], Jo32)[0] < FP32_TOL
+    Jo = om.solve_J(orc.params(order=4), origins=o)
+    assert j_rel_err(outs[1].cpu().numpy()[o], Jo)[0] < FP32_TOL
 
 
 def test_invalid_order_rejected(ctx):

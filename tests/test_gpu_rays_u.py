@@ -40,10 +40,9 @@ def test_solve_u_parity_and_J(ctx, orc, order):
     om = orc.OracleModel(m, rays=rays)
     o = np.arange(o0, o1)
     uo = om.solve_u(orc.params(order=order, I_bdy=0.1), o)
-    uo32 = om.solve_u(orc.params(order=order, I_bdy=0.1, decide32=True), o)
     assert u64.shape == uo.shape == (o1 - o0, rays.shape[1], 22)
     assert j_rel_err(u64.reshape(-1, 22), uo.reshape(-1, 22))[0] < 1e-10
-    assert j_rel_err(u32.reshape(-1, 22), uo32.reshape(-1, 22))[0] < 1e-4
+    assert j_rel_err(u32.reshape(-1, 22), uo.reshape(-1, 22))[0] < 1e-4
     w2 = 2.0 / (12.0 * 4.0 ** (rays[o0:o1] >> 28))
     assert np.allclose((w2[:, :, None] * u64).sum(1), J64[o0:o1], rtol=1e-13, atol=0)
 

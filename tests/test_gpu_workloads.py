@@ -8,7 +8,8 @@
   four of them against the oracle;
 * the 50,000-point wind at full size in the launch configuration that the
   benchmark times (batched FP32, ray sets rebuilt inside the graph) -- sampled
-  origins against the oracle, and the traced lists bit-exact."""
+  origins against the oracle, the traced lists bit-exact, and every origin's
+  FP32 J within 1e-4 of the FP64 form."""
 import numpy as np
 import pytest
 
@@ -51,10 +52,9 @@ def test_octree_adaptive_two_lines(ctx, orc):
     origins = _sample(len(m["pos"]), 300, 1)
     om = orc.OracleModel(m, rays=rays)
     Jo = om.solve_J(orc.params(), origins=origins)
-    Jo32 = om.solve_J(orc.params(decide32=True), origins=origins)
     assert j_rel_err(J64[origins], Jo)[0] < FP64_TOL
-    assert j_rel_err(J32[origins], Jo32)[0] < FP32_TOL
-    assert j_rel_err(Jb32.cpu().numpy()[origins], Jo32)[0] < FP32_TOL
+    assert j_rel_err(J32[origins], Jo)[0] < FP32_TOL
+    assert j_rel_err(Jb32.cpu().numpy()[origins], Jo)[0] < FP32_TOL
 
 
 def test_mixed_batch_four_lines(ctx, orc):
@@ -75,9 +75,8 @@ def test_mixed_batch_four_lines(ctx, orc):
         origins = _sample(len(m["pos"]), 60, 2 + j)
         om = orc.OracleModel(m, rays=rays[j])
         Jo = om.solve_J(orc.params(), origins=origins)
-        Jo32 = om.solve_J(orc.params(decide32=True), origins=origins)
         assert j_rel_err(out64[j].cpu().numpy()[origins], Jo)[0] < FP64_TOL, m["name"]
-        assert j_rel_err(out32[j].cpu().numpy()[origins], Jo32)[0] < FP32_TOL, m["name"]
+        assert j_rel_err(out32[j].cpu().numpy()[origins], Jo)[0] < FP32_TOL, m["name"]
 
 
 def test_wind_full_size_bench_configuration(ctx, orc):
@@ -107,7 +106,11 @@ def test_wind_full_size_bench_configuration(ctx, orc):
             assert np.array_equal(idx[off[h]:off[h + 1]], ri)
             assert np.array_equal(Z[off[h]:off[h + 1]], rz)
     assert np.all(np.isfinite(J32)) and J32.min() >= 0
-    Jo32 = om.solve_J(orc.params(decide32=True), origins=origins)
-    assert j_rel_err(J32[origins], Jo32)[0] < FP32_TOL
-    Jo = om.solve_J(orc.params(), origins=o64)
-    assert j_rel_err(J64[o64], Jo)[0] < FP64_TOL
+    Jo = om.solve_J(orc.params(), origins=origins)
+    assert j_rel_err(J32[origins], Jo)[0] < FP32_TOL
+    assert j_rel_err(J64[o64], Jo[:40])[0] < FP64_TOL
+    # every origin: the single-precision form within the budget of the FP64 form
+    # (itself oracle-verified above), both taking the definition's integer decisions
+    r_all, _ = j_rel_err(J32, J64)
+    print(f"50k wind, all origins: FP32 vs FP64 max rel err {r_all:.3e}")
+    assert r_all < FP32_TOL
