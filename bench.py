@@ -234,6 +234,13 @@ def run_mgx(args):
         ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32h],
                           flags=batched, order=4)
 
+    out32d = torch.empty((n, NB), dtype=torch.float64, device="cuda")
+
+    def step32d():
+        # the batched step with the optical-depth increments and the elimination pivots in FP64
+        ctx.solve_J_batch([mid], precision=mgx.MGX_FP32_DT64, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32d],
+                          flags=batched)
+
     def step32_profiled():
         ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32],
                           flags=mgx.MGX_BATCH_RAYS)
@@ -267,6 +274,8 @@ def run_mgx(args):
             ctx.profile(False)
         return sum(a.elapsed_time(b) for a, b in ev) / 1e3, prof
 
+    # measured throughput of the arithmetic pipes (the solve's roofline denominators), untimed
+    alu = mgx.mgx_alu_peaks(ctx.ptr, 3)
     # launch parameters of the batched step from the autotuner (untimed; results do not depend on them)
     trials, _ = ctx.autotune([mid], precision=mgx.MGX_FP32, dtau_max=0.5, dv_max=1.0 / 3.0, outs=[out32],
                              flags=batched, reps=3)
@@ -283,6 +292,8 @@ def run_mgx(args):
     value = job_throughput(ws, solves_per_step, args.steps, t32)
     kh = max(1, min(args.steps, 5))
     t32h, _ = timed(step32h, kh, max(3, min(args.warmup, 3)), False)
+    kd = max(1, min(args.steps, 3))
+    t32d, _ = timed(step32d, kd, 1, False)
     # per-kernel CUDA-event breakdown of the same step, launched without the graph
     kb = max(1, min(args.steps, 3))
     tb, prof32 = timed(step32_profiled, kb, 1, True)
@@ -338,6 +349,8 @@ def run_mgx(args):
     mx = np.abs(J64).max(axis=1, keepdims=True)
     mask = np.abs(J64) > 1e-6 * mx
     rel32_64 = np.abs(J32 - J64)[mask] / np.abs(J64[mask])
+    J32d = out32d.cpu().numpy()
+    rel32d_64 = np.abs(J32d - J64)[mask] / np.abs(J64[mask])
     cpu = None
     acc_oracle = None
     acc_herm = None
@@ -358,11 +371,14 @@ def run_mgx(args):
     except (OSError, ValueError):
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA counted as 2
+    fp32_derived = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA counted as 2
+    fp32_peak = alu["fp32_fma_tflops"]
     ms_solve = prof32["ms"]["solve"] / max(1, prof32["launches"]["solve"])
     flops = (FLOPS_PER_UPDATE * prof32["updates"] + FLOPS_PER_SAMPLE_LINE * len(m["nu0"]) * prof32["samples"])
     flops_per_launch = flops / max(1, prof32["launches"]["solve"])
     achieved = flops_per_launch / (ms_solve * 1e-3) / 1e12
+    # special-function operations of the solve: one exp2 per (sample, bin, line), one reciprocal per update
+    mufu_ops = (len(m["nu0"]) * prof32["samples"] + prof32["updates"]) / max(1, prof32["launches"]["solve"])
     # algorithmic bytes of the solve: a 4-byte point id per traced point and frequency tile (the tile is
     # 32 x bins-per-lane bins), the point data once (positions and velocities in double and single precision,
     # width, continuum and line data: 56 + 8 (L - 1) bytes) and 8 bytes of J per (point, bin)
@@ -389,6 +405,10 @@ def run_mgx(args):
         "hermitian_fp32": {"value": solves_per_step * kh / t32h, "unit": UNIT, "ms_per_step": 1e3 * t32h / kh,
                            "cost_vs_second_order": (t32h / kh) / (t32 / args.steps),
                            "oracle_sample": acc_herm},
+        "fp32_dt64": {"value": solves_per_step * kd / t32d, "unit": UNIT, "ms_per_step": 1e3 * t32d / kd,
+                      "cost_vs_fp32": (t32d / kd) / (t32 / args.steps),
+                      "vs_fp64_max_rel": float(rel32d_64.max()),
+                      "vs_fp64_p99_rel": float(np.quantile(rel32d_64, 0.99))},
         "accuracy": {"fp32_vs_fp64_max_rel": float(rel32_64.max()),
                      "fp32_vs_fp64_p99_rel": float(np.quantile(rel32_64, 0.99)),
                      "oracle_sample": acc_oracle},
@@ -401,7 +421,12 @@ def run_mgx(args):
                           "solve_decisions_redone_fp64": prof32["decisions_redone"] // kb},
         "roofline": {"kernel": "k_solve_queue<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                     "peak_source": f"FP32 FMA: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz (derived)",
+                     "peak_source": "measured: FP32 FMA chains on every SM (mgx_alu_peaks), of measured",
+                     "derived_peak": fp32_derived, "frac_of_derived": achieved / fp32_derived,
+                     "mufu": {"ops_per_launch": mufu_ops, "achieved_gops": mufu_ops / (ms_solve * 1e-3) / 1e9,
+                              "peak_gops": alu["ex2_gops"],
+                              "frac": mufu_ops / (ms_solve * 1e-3) / 1e9 / alu["ex2_gops"]},
+                     "measured_alu_peaks": alu,
                      "hbm_algorithmic_gbs": hbm_gbs, "hbm_algorithmic_bytes_per_launch": solve_bytes},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -51,12 +51,16 @@ enum {
 /* arithmetic forms of the formal solution */
 enum {
     MGX_FP64 = 0, /* plain form: every step in double precision                    */
-    MGX_FP32 = 1  /* single-precision bulk; double for the distance increments along
+    MGX_FP32 = 1, /* single-precision bulk; double for the distance increments along
                      the ray and the compensated J sum.  The integer decisions (the
                      velocity-sample count of Section 2.1.1, Eq. 2's n_inter) are
                      the double-precision definition's: taken in single precision
                      under a rigorous error bound, redone in double precision
                      where the bound leaves the integer open                        */
+    MGX_FP32_DT64 = 2 /* MGX_FP32 with the optical-depth increments and the pivot
+                     recurrence of the elimination (Fh and D of the scaled 1+B form)
+                     also in double precision, z and S in single precision; second-
+                     order scheme only (order 4 gives MGX_EINVAL)                    */
 };
 
 /* Limits. */
@@ -378,6 +382,16 @@ mgx_status mgx_reduce_mesh_learned(mgx_ctx *ctx, int32_t model, const float *X, 
  * largest relative error the solve assumes for that function.  MGX_EINVAL for
  * another kind, n < 0, or null arrays with n > 0. */
 mgx_status mgx_eval_approx(mgx_ctx *ctx, int32_t kind, const float *x, int64_t n, float *y, float *bound);
+
+/* Measured throughput of the arithmetic pipes the formal solution runs on (no
+ * counterpart in the paper; the denominators of its roofline): out[0] FP32
+ * fused multiply-add TFLOP/s (two flops each), out[1] FP64 fused multiply-add
+ * TFLOP/s, out[2] approximate exp2 and out[3] approximate reciprocal, each in
+ * Gop/s; every figure is the best of `reps` (1..100) timed launches of eight
+ * independent dependency chains per thread on every SM (CUDA events on the
+ * context's stream).  Allocates and frees a small device buffer; synchronises
+ * the stream.  Takes about a second. */
+mgx_status mgx_alu_peaks(mgx_ctx *ctx, int32_t reps, double *out);
 
 /* Kernel-level profiling.  While enabled, every kernel launch of the context is
  * bracketed by CUDA events on the context's stream and the work counters below

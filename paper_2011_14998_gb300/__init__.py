@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmgx.so")
 
 MGX_OK, MGX_EINVAL, MGX_ENOMEM, MGX_ECUDA, MGX_ESTATE, MGX_ERANGE = 0, -1, -2, -3, -4, -6
-MGX_FP64, MGX_FP32 = 0, 1
+MGX_FP64, MGX_FP32, MGX_FP32_DT64 = 0, 1, 2
 MGX_MAX_LINES = 8
 
 # every symbol the header declares
@@ -29,7 +29,7 @@ ABI_SYMBOLS = ("mgx_create", "mgx_destroy", "mgx_last_error", "mgx_rayset_npairs
                "mgx_solve_J_noalloc", "mgx_solve_J_batch", "mgx_mlp_set_params", "mgx_mlp_get_params",
                "mgx_mlp_forward", "mgx_mlp_grad", "mgx_mlp_train", "mgx_mlp_features", "mgx_reduce_mesh_learned",
                "mgx_set_tuning", "mgx_get_tuning", "mgx_autotune", "mgx_analytic_mesh", "mgx_solve_u",
-               "mgx_pix2vec", "mgx_antipode", "mgx_reduce_mesh_learned_weighted", "mgx_eval_approx")
+               "mgx_pix2vec", "mgx_antipode", "mgx_reduce_mesh_learned_weighted", "mgx_eval_approx", "mgx_alu_peaks")
 MGX_MLP_NPARAM = 4801
 MGX_BATCH_GRAPH, MGX_BATCH_RAYS = 1, 2
 KERNEL_CLASSES = ("rays", "trace_count", "scan", "trace_emit", "solve", "other")
@@ -108,6 +108,7 @@ def load_library(path: str = LIB_PATH):
         "mgx_profile_enable": (i32, [vp, i32]),
         "mgx_profile_read": (i32, [vp, C.POINTER(Profile)]),
         "mgx_eval_approx": (i32, [vp, i32, vp, i64, vp, C.POINTER(C.c_float)]),
+        "mgx_alu_peaks": (i32, [vp, i32, vp]),
         "mgx_set_tuning": (i32, [vp, C.POINTER(Tuning)]),
         "mgx_pix2vec": (i32, [i32, i64, vp]),
         "mgx_reduce_mesh_learned_weighted": (i32, [vp, i32, vp, dbl, dbl, u64, vp, C.POINTER(i64),
@@ -374,6 +375,14 @@ def mgx_eval_approx(ctx, kind: int, x, y) -> float:
     b = C.c_float(0.0)
     _check(ctx, load_library().mgx_eval_approx(ctx, int(kind), _ptr(x), int(x.numel()), _ptr(y), C.byref(b)))
     return float(b.value)
+
+
+def mgx_alu_peaks(ctx, reps: int = 3) -> dict:
+    """Measured pipe throughputs: FP32 and FP64 FMA TFLOP/s, exp2 and rcp Gop/s."""
+    out = np.zeros(4)
+    _check(ctx, load_library().mgx_alu_peaks(ctx, int(reps), _ptr(out)))
+    return {"fp32_fma_tflops": float(out[0]), "fp64_fma_tflops": float(out[1]), "ex2_gops": float(out[2]),
+            "rcp_gops": float(out[3])}
 
 
 def mgx_profile_enable(ctx, enable: bool = True) -> None:

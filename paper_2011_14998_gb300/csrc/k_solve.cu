@@ -8,7 +8,7 @@ namespace mgx {
 // Bins per lane of the single-precision kernel: 2 when there are more bins than
 // lanes (the frequency-independent work is then shared by two bins), else 1.
 int solve_bins_per_lane(int precision, int32_t n_bins) {
-    if (precision != MGX_FP32) return 1;
+    if (precision != MGX_FP32 && precision != MGX_FP32_DT64) return 1;
     return n_bins > 32 ? 2 : 1;
 }
 

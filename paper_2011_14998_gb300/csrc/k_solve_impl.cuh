@@ -163,11 +163,16 @@ __device__ __forceinline__ void optics(R delta, R rdv, R cc, R ec, const R *ce, 
 // The Hermitian scheme (ORD 4) also carries the source function of the last
 // eliminated row (Sp) and of the current sample (Sc), the last increment (hp,
 // negative before the first row) and its reciprocal (rh).
-template <typename R>
+//
+// P is the precision of the pivot recurrence (Fh, D and the increments dt):
+// R, or double with R = float (the form with double-precision optical-depth
+// increments and pivots, second-order scheme only).
+template <typename R, typename P = R>
 struct Sweep {
-    R Fh, Dm, zh, dtp;  // scaled 1+B quantities of the last eliminated row, half its dtau
-    R chi, eta;         // optics of the current (not yet eliminated) sample
-    R Sp, Sc, hp, rh;   // Hermitian scheme only
+    P Fh, Dm, dtp;  // scaled 1+B quantities of the last eliminated row, half its dtau
+    R zh;
+    R chi, eta;     // optics of the current (not yet eliminated) sample
+    R Sp, Sc, hp, rh;  // Hermitian scheme only
 };
 
 // Eliminate the row of the current sub-point (optics chi, eta) once the
@@ -192,16 +197,25 @@ struct Sweep {
 //   Fh = (1 + h/2) / (1 - h^2/6),  zh = D (h S_i / 3 + h S_{i+1} / 6 + I) / (1 - h^2/6).
 constexpr double kHermRatio = 64.0;
 
-template <int ORD, typename R>
-__device__ __forceinline__ void row(Sweep<R> &w, R chi, R eta, R dt, R Si, R Sn) {
+template <int ORD, typename R, typename P>
+__device__ __forceinline__ void row(Sweep<R, P> &w, R chi, R eta, P dt, R Si, R Sn) {
     if constexpr (ORD == 2) {
-        const R dtb = fma(dt, R(0.5), w.dtp);
+        const P dtb = fma(dt, P(0.5), w.dtp);
         w.Fh = dtb + w.Dm * w.Fh;
-        const R rr = Ar<R>::rcp(chi * (R(1) + dt * w.Fh));
-        w.Dm = chi * rr;
-        w.zh = w.Dm * w.zh + dtb * (eta * rr);
-        w.dtp = dt * R(0.5);
+        if constexpr (sizeof(P) == sizeof(R)) {
+            const R rr = Ar<R>::rcp(chi * (R(1) + dt * w.Fh));
+            w.Dm = chi * rr;
+            w.zh = w.Dm * w.zh + dtb * (eta * rr);
+        } else {
+            // pivots in double precision: D = 1 / (1 + dt Fh); z in single
+            // precision from D and S = eta / chi
+            const P D = P(1) / (P(1) + dt * w.Fh);
+            w.Dm = D;
+            w.zh = R(D) * w.zh + R(dtb * D) * (eta * Ar<R>::rcp(chi));
+        }
+        w.dtp = dt * P(0.5);
     } else {
+        static_assert(sizeof(P) == sizeof(R), "the Hermitian scheme keeps its pivots in the form's precision");
         const R rh = Ar<R>::rcp(dt);
         if (w.hp < R(0)) {  // boundary row
             const R k = Ar<R>::rcp(R(1) - dt * dt * R(1.0 / 6.0));
@@ -233,10 +247,10 @@ __device__ __forceinline__ void row(Sweep<R> &w, R chi, R eta, R dt, R Si, R Sn)
 // last eliminated rows of both halves; no back substitution is needed).
 // Second order: u_o = (dtbar S_o + zh- + zh+) / (dtbar + D- Fh- + D+ Fh+), an
 // empty half contributing (D Fh, zh) = (1, I) through its initial state.
-template <typename R>
-__device__ __forceinline__ R origin_u2(const Sweep<R> &b, const Sweep<R> &f, R So) {
-    const R dtb = b.dtp + f.dtp;  // the halves of the two last increments
-    return (dtb * So + b.zh + f.zh) / (dtb + b.Dm * b.Fh + f.Dm * f.Fh);
+template <typename R, typename P>
+__device__ __forceinline__ R origin_u2(const Sweep<R, P> &b, const Sweep<R, P> &f, R So) {
+    const P dtb = b.dtp + f.dtp;  // the halves of the two last increments
+    return R((dtb * P(So) + P(b.zh) + P(f.zh)) / (dtb + b.Dm * b.Fh + f.Dm * f.Fh));
 }
 
 // Hermitian scheme: with h- (h+) the last increment of the backward (forward)
@@ -245,11 +259,11 @@ __device__ __forceinline__ R origin_u2(const Sweep<R> &b, const Sweep<R> &f, R S
 // with one half empty the origin row is the third-order boundary row,
 //   u_o = (h S_o/3 + h S_1/6 + I + (1 - h^2/6) zh) / (1 + h/2 + (1 - h^2/6) D Fh);
 // with both empty u_o = I.
-template <typename R>
-__device__ __forceinline__ R origin_u4(const Sweep<R> &b, const Sweep<R> &f, R So, R I) {
+template <typename R, typename P>
+__device__ __forceinline__ R origin_u4(const Sweep<R, P> &b, const Sweep<R, P> &f, R So, R I) {
     if (b.hp < R(0) && f.hp < R(0)) return I;
     if (b.hp < R(0) || f.hp < R(0)) {
-        const Sweep<R> &w = b.hp < R(0) ? f : b;
+        const Sweep<R, P> &w = b.hp < R(0) ? f : b;
         const R h = w.hp, k1 = R(1) - h * h * R(1.0 / 6.0);
         return (h * (So * R(1.0 / 3.0) + w.Sp * R(1.0 / 6.0)) + I + k1 * w.zh) / (fma(h, R(0.5), R(1)) + k1 * w.Dm * w.Fh);
     }
@@ -339,14 +353,16 @@ __device__ __forceinline__ int32_t lane_bin(const St &sg, int i, int lane) {
 // elimination state of each of the lane's (at most two) bins (D and Fh enter
 // every step only as their product, which is what is kept), the running
 // maximum of chi, the compensated J sums, the origin's source function, and
-// the backward half's coupling to the origin row (second order: D Fh, zh,
-// dtb/2; Hermitian: also hp, Sp, rh).
-template <typename R, int ORD>
+// the backward half's coupling to the origin row.  The pivot quantities
+// (D Fh, dtb/2) are kept in the pivot precision P.
+template <typename R, int ORD, typename P = R>
 struct Lane {
-    static constexpr int kW = ORD == 4 ? 9 : 5;
-    static constexpr int kC = ORD == 4 ? 6 : 3;
-    R ws[kW][2][32];
-    R cp[kC][2][32];
+    static constexpr int kWR = ORD == 4 ? 7 : 3;  // zh, chi, eta (Hermitian: + Sp, Sc, hp, rh)
+    static constexpr int kCR = ORD == 4 ? 4 : 1;  // zh (Hermitian: + hp, Sp, rh)
+    P wp[2][2][32];                              // D Fh, dtb/2
+    R wr[kWR][2][32];
+    P cpp[2][2][32];                             // backward half: D Fh, dtb/2
+    R cpr[kCR][2][32];
     R cm[32];
     R So[2][32];
     double js[2][32], jc[2][32];
@@ -724,10 +740,10 @@ __device__ __noinline__ void resolve_n_inter(Stage<R, NL> &sg, const DevMesh &m,
 // with nothing changed, when a single-precision count is left open somewhere
 // in the warp (sg.fix marks it); once it has been redone the sample is
 // stepped again with `fixed` set, taking the counts from sg.fix.
-template <typename R, int NL, int BPL, int ORD>
+template <typename R, int NL, int BPL, int ORD, typename P>
 __device__ __forceinline__ bool sample_step(const R (&v)[Stage<R, NL>::kS], int s, bool fixed, Stage<R, NL> &sg,
                                             const SolveArgs &a, R &cmax, const Bin<R, NL> (&f)[BPL],
-                                            const bool (&act)[BPL], Sweep<R> (&w)[BPL]) {
+                                            const bool (&act)[BPL], Sweep<R, P> (&w)[BPL]) {
     const R dl = v[0], rdv = v[1], hq = v[4], thr = v[5];
     R chi_q[BPL], eta_q[BPL];
 #pragma unroll
@@ -747,7 +763,7 @@ __device__ __forceinline__ bool sample_step(const R (&v)[Stage<R, NL>::kS], int 
         for (int i = 0; i < BPL; ++i) {
             R Sq = R(0);
             if constexpr (ORD == 4) Sq = Ar<R>::src(eta_q[i], chi_q[i]);
-            row<ORD>(w[i], w[i].chi, w[i].eta, hq * (w[i].chi + chi_q[i]), w[i].Sc, Sq);
+            row<ORD>(w[i], w[i].chi, w[i].eta, P(hq) * (P(w[i].chi) + P(chi_q[i])), w[i].Sc, Sq);
             w[i].chi = chi_q[i];
             w[i].eta = eta_q[i];
             w[i].Sc = Sq;
@@ -789,14 +805,14 @@ __device__ __forceinline__ bool sample_step(const R (&v)[Stage<R, NL>::kS], int 
             const R ck = c0 + dchi * R(k), ek = e0 + deta * R(k);
             R Sk = R(0);
             if constexpr (ORD == 4) Sk = Ar<R>::src(ek, ck);
-            row<ORD>(w[i], cprev, eprev, hh * (cprev + ck), Sprev, Sk);
+            row<ORD>(w[i], cprev, eprev, P(hh) * (P(cprev) + P(ck)), Sprev, Sk);
             cprev = ck;
             eprev = ek;
             Sprev = Sk;
         }
         R Sq = R(0);
         if constexpr (ORD == 4) Sq = Ar<R>::src(eta_q[i], chi_q[i]);
-        row<ORD>(w[i], cprev, eprev, hh * (cprev + chi_q[i]), Sprev, Sq);
+        row<ORD>(w[i], cprev, eprev, P(hh) * (P(cprev) + P(chi_q[i])), Sprev, Sq);
         w[i].chi = chi_q[i];
         w[i].eta = eta_q[i];
         w[i].Sc = Sq;
@@ -808,39 +824,39 @@ __device__ __forceinline__ bool sample_step(const R (&v)[Stage<R, NL>::kS], int 
 
 // The lane's sweep state to and from shared memory (D Fh kept as one value,
 // read back as Fh = D Fh, D = 1).
-template <typename R, int BPL, int ORD>
-__device__ __forceinline__ void put_sweep(Lane<R, ORD> &ln, const Sweep<R> (&w)[BPL], int lane) {
+template <typename R, int BPL, int ORD, typename P>
+__device__ __forceinline__ void put_sweep(Lane<R, ORD, P> &ln, const Sweep<R, P> (&w)[BPL], int lane) {
 #pragma unroll
     for (int i = 0; i < BPL; ++i) {
-        ln.ws[0][i][lane] = w[i].Dm * w[i].Fh;
-        ln.ws[1][i][lane] = w[i].zh;
-        ln.ws[2][i][lane] = w[i].dtp;
-        ln.ws[3][i][lane] = w[i].chi;
-        ln.ws[4][i][lane] = w[i].eta;
+        ln.wp[0][i][lane] = w[i].Dm * w[i].Fh;
+        ln.wp[1][i][lane] = w[i].dtp;
+        ln.wr[0][i][lane] = w[i].zh;
+        ln.wr[1][i][lane] = w[i].chi;
+        ln.wr[2][i][lane] = w[i].eta;
         if constexpr (ORD == 4) {
-            ln.ws[5][i][lane] = w[i].Sp;
-            ln.ws[6][i][lane] = w[i].Sc;
-            ln.ws[7][i][lane] = w[i].hp;
-            ln.ws[8][i][lane] = w[i].rh;
+            ln.wr[3][i][lane] = w[i].Sp;
+            ln.wr[4][i][lane] = w[i].Sc;
+            ln.wr[5][i][lane] = w[i].hp;
+            ln.wr[6][i][lane] = w[i].rh;
         }
     }
 }
 
-template <typename R, int BPL, int ORD>
-__device__ __forceinline__ void get_sweep(const Lane<R, ORD> &ln, Sweep<R> (&w)[BPL], int lane) {
+template <typename R, int BPL, int ORD, typename P>
+__device__ __forceinline__ void get_sweep(const Lane<R, ORD, P> &ln, Sweep<R, P> (&w)[BPL], int lane) {
 #pragma unroll
     for (int i = 0; i < BPL; ++i) {
-        w[i].Fh = ln.ws[0][i][lane];
-        w[i].Dm = R(1);
-        w[i].zh = ln.ws[1][i][lane];
-        w[i].dtp = ln.ws[2][i][lane];
-        w[i].chi = ln.ws[3][i][lane];
-        w[i].eta = ln.ws[4][i][lane];
+        w[i].Fh = ln.wp[0][i][lane];
+        w[i].Dm = P(1);
+        w[i].dtp = ln.wp[1][i][lane];
+        w[i].zh = ln.wr[0][i][lane];
+        w[i].chi = ln.wr[1][i][lane];
+        w[i].eta = ln.wr[2][i][lane];
         if constexpr (ORD == 4) {
-            w[i].Sp = ln.ws[5][i][lane];
-            w[i].Sc = ln.ws[6][i][lane];
-            w[i].hp = ln.ws[7][i][lane];
-            w[i].rh = ln.ws[8][i][lane];
+            w[i].Sp = ln.wr[3][i][lane];
+            w[i].Sc = ln.wr[4][i][lane];
+            w[i].hp = ln.wr[5][i][lane];
+            w[i].rh = ln.wr[6][i][lane];
         } else {
             w[i].Sp = w[i].Sc = w[i].hp = w[i].rh = R(0);
         }
@@ -869,15 +885,15 @@ __device__ __forceinline__ void get_bins(const Stage<R, NL> &sg, Bin<R, NL> (&f)
 // (one call per chunk): its loop then gets a register allocation of its own,
 // unaffected by the calls of the code around it.  pend: a sample whose open
 // counts have been redone into sg.fix (-1: none).
-template <typename R, int NL, int BPL, int ORD>
-__device__ __noinline__ int consume_chunk(Stage<R, NL> &sg, Lane<R, ORD> &ln, const SolveArgs &a, int total,
+template <typename R, int NL, int BPL, int ORD, typename P>
+__device__ __noinline__ int consume_chunk(Stage<R, NL> &sg, Lane<R, ORD, P> &ln, const SolveArgs &a, int total,
                                           int nch, int sign, int pos, int pend, bool fresh) {
     constexpr int kS = Stage<R, NL>::kS, kCap = Stage<R, NL>::kCap;
     const int lane = threadIdx.x & 31;
-    Sweep<R> w[BPL];
+    Sweep<R, P> w[BPL];
     Bin<R, NL> f[BPL];
     bool act[BPL];
-    get_sweep<R, BPL, ORD>(ln, w, lane);
+    get_sweep<R, BPL, ORD, P>(ln, w, lane);
     get_bins<R, NL, BPL>(sg, f, act, lane);
     R cmax = ln.cm[lane];
     int r0 = pos / kCap * kCap, s = pos - r0;
@@ -893,12 +909,12 @@ __device__ __noinline__ int consume_chunk(Stage<R, NL> &sg, Lane<R, ORD> &ln, co
         for (; s < nr; ++s) {
             R v[kS];
             load_rec<R, NL>(sg.rec + s * kS, v);
-            if (!sample_step<R, NL, BPL, ORD>(v, s, r0 + s == pend, sg, a, cmax, f, act, w)) break;
+            if (!sample_step<R, NL, BPL, ORD, P>(v, s, r0 + s == pend, sg, a, cmax, f, act, w)) break;
         }
         if (s < nr) break;
         __syncwarp();
     }
-    put_sweep<R, BPL, ORD>(ln, w, lane);
+    put_sweep<R, BPL, ORD, P>(ln, w, lane);
     ln.cm[lane] = cmax;
     __syncwarp();
     return r0 < total ? r0 + s : total;
@@ -954,23 +970,23 @@ __device__ __noinline__ int stage_chunk(const DevMesh &m, const DevLines &Ln, co
 // Eliminate one half of a pair line (direction sign r) from its far end up to
 // (excluding) the origin row.  Leaves the origin row's coupling (D Fh, zh)
 // and the last optical-depth increment in the lane's sweep state.
-template <typename R, int NL, int BPL, int ORD>
+template <typename R, int NL, int BPL, int ORD, typename P>
 __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs &a, Stage<R, NL> &sg,
-                           Lane<R, ORD> &ln, int sign) {
+                           Lane<R, ORD, P> &ln, int sign) {
     constexpr int kCap = Stage<R, NL>::kCap;
     const int lane = threadIdx.x & 31;
     {
-        Sweep<R> w[BPL];
+        Sweep<R, P> w[BPL];
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
-            w[i].Fh = R(1);
-            w[i].Dm = R(1);
+            w[i].Fh = P(1);
+            w[i].Dm = P(1);
             w[i].zh = R(a.I_bdy);
-            w[i].dtp = R(0);
+            w[i].dtp = P(0);
             w[i].hp = R(-1);  // no row yet (Hermitian scheme)
             w[i].Sp = w[i].Sc = w[i].rh = w[i].chi = w[i].eta = R(0);
         }
-        put_sweep<R, BPL, ORD>(ln, w, lane);
+        put_sweep<R, BPL, ORD, P>(ln, w, lane);
     }
     const int32_t cnt = sg.hl.cnt;
     __syncwarp();
@@ -992,9 +1008,9 @@ __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs
             for (int i = 0; i < BPL; ++i) {
                 R chi, eta;
                 optics<R, NL>(sg.d[1], rdv, sg.cc[1], sg.ec[1], ce, f[i], chi, eta);
-                ln.ws[3][i][lane] = chi;
-                ln.ws[4][i][lane] = eta;
-                if constexpr (ORD == 4) ln.ws[6][i][lane] = Ar<R>::src(eta, chi);
+                ln.wr[1][i][lane] = chi;
+                ln.wr[2][i][lane] = eta;
+                if constexpr (ORD == 4) ln.wr[4][i][lane] = Ar<R>::src(eta, chi);
                 cmax = i == 0 ? chi : fmax(cmax, chi);
             }
             ln.cm[lane] = cmax;
@@ -1004,7 +1020,7 @@ __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs
         bool fresh = true;
 #pragma unroll 1
         for (;;) {
-            pos = consume_chunk<R, NL, BPL, ORD>(sg, ln, a, total, nch, sign, pos, pend, fresh);
+            pos = consume_chunk<R, NL, BPL, ORD, P>(sg, ln, a, total, nch, sign, pos, pend, fresh);
             if (pos >= total) break;
             resolve_n_inter<R, NL>(sg, m, Ln, a, sign, pos % kCap, lane_bin<BPL>(sg, 0, lane),
                                    lane_bin<BPL>(sg, BPL - 1, lane));
@@ -1020,18 +1036,19 @@ __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs
 // large); the minimum resident CTAs per SM caps the registers
 // (65536 / (threads x CTAs)).  One line: 7 CTAs (72 registers; the shared
 // staging of 7 CTAs just fits 228 KB), measured 9 % faster than 6 on GB300.
-template <typename R, int NL, int BPL>
+template <typename R, int NL, int BPL, typename P = R>
 struct Occ {
     static constexpr int kWarps = sizeof(R) == 8 ? 2 : 4;
     static constexpr int kThreads = 32 * kWarps;
-    static constexpr int kMinBlocks = sizeof(R) == 8 ? 1 : (NL == 1 ? 7 : NL <= 4 ? 4 : 3);
+    static constexpr int kMinBlocks =
+        sizeof(R) == 8 ? 1 : sizeof(P) == 8 ? (NL == 1 ? 4 : 2) : (NL == 1 ? 7 : NL <= 4 ? 4 : 3);
 };
 
 // J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
-template <typename R, int NL, int BPL, int ORD>
+template <typename R, int NL, int BPL, int ORD, typename P>
 __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln, const DevRays &Rs,
                                            const SolveArgs &a, int32_t oc, int32_t tile, Stage<R, NL> &sg,
-                                           Lane<R, ORD> &ln, int lane) {
+                                           Lane<R, ORD, P> &ln, int lane) {
     static_assert(BPL <= 2, "the shared per-lane state holds two bins");
     const int32_t o = a.o_begin + oc;
     const int32_t L = Ln.L, F = Ln.F, NB = L * F;
@@ -1113,35 +1130,35 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
         if (lane < 3) sg.r[lane] = Rs.dir[3 * (level_offset(lev) + (ray & 0x0FFFFFFFu)) + lane];
         if (lane == 0) sg.hl = half_list(a, hb);
         __syncwarp();
-        half_sweep<R, NL, BPL, ORD>(m, Ln, a, sg, ln, -1);
+        half_sweep<R, NL, BPL, ORD, P>(m, Ln, a, sg, ln, -1);
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {  // the backward half's coupling to the origin row
-            ln.cp[0][i][lane] = ln.ws[0][i][lane];  // D Fh
-            ln.cp[1][i][lane] = ln.ws[1][i][lane];  // zh
-            ln.cp[2][i][lane] = ln.ws[2][i][lane];  // dtb / 2
+            ln.cpp[0][i][lane] = ln.wp[0][i][lane];  // D Fh
+            ln.cpp[1][i][lane] = ln.wp[1][i][lane];  // dtb / 2
+            ln.cpr[0][i][lane] = ln.wr[0][i][lane];  // zh
             if constexpr (ORD == 4) {
-                ln.cp[3][i][lane] = ln.ws[7][i][lane];  // hp
-                ln.cp[4][i][lane] = ln.ws[5][i][lane];  // Sp
-                ln.cp[5][i][lane] = ln.ws[8][i][lane];  // rh
+                ln.cpr[1][i][lane] = ln.wr[5][i][lane];  // hp
+                ln.cpr[2][i][lane] = ln.wr[3][i][lane];  // Sp
+                ln.cpr[3][i][lane] = ln.wr[6][i][lane];  // rh
             }
         }
         if (lane == 0) sg.hl = half_list(a, hb + 1);
         __syncwarp();
-        half_sweep<R, NL, BPL, ORD>(m, Ln, a, sg, ln, 1);
+        half_sweep<R, NL, BPL, ORD, P>(m, Ln, a, sg, ln, 1);
         const double w2 = a.w2[lev];
-        Sweep<R> wf[BPL];
-        get_sweep<R, BPL, ORD>(ln, wf, lane);
+        Sweep<R, P> wf[BPL];
+        get_sweep<R, BPL, ORD, P>(ln, wf, lane);
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
-            Sweep<R> wb;
-            wb.Fh = ln.cp[0][i][lane];
-            wb.Dm = R(1);
-            wb.zh = ln.cp[1][i][lane];
-            wb.dtp = ln.cp[2][i][lane];
+            Sweep<R, P> wb;
+            wb.Fh = ln.cpp[0][i][lane];
+            wb.Dm = P(1);
+            wb.dtp = ln.cpp[1][i][lane];
+            wb.zh = ln.cpr[0][i][lane];
             if constexpr (ORD == 4) {
-                wb.hp = ln.cp[3][i][lane];
-                wb.Sp = ln.cp[4][i][lane];
-                wb.rh = ln.cp[5][i][lane];
+                wb.hp = ln.cpr[1][i][lane];
+                wb.Sp = ln.cpr[2][i][lane];
+                wb.rh = ln.cpr[3][i][lane];
             }
             const R So = ln.So[i][lane];
             const R u = ORD == 4 ? origin_u4(wb, wf[i], So, R(a.I_bdy)) : origin_u2(wb, wf[i], So);
@@ -1182,29 +1199,29 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
 }
 
 // Grid-mapped launch: warp w of the grid solves item w = oc * n_tiles + tile.
-template <typename R, int NL, int BPL, int ORD>
-__global__ void __launch_bounds__(Occ<R, NL, BPL>::kThreads, (Occ<R, NL, BPL>::kMinBlocks))
+template <typename R, int NL, int BPL, int ORD, typename P>
+__global__ void __launch_bounds__(Occ<R, NL, BPL, P>::kThreads, (Occ<R, NL, BPL, P>::kMinBlocks))
 k_solve(const __grid_constant__ DevMesh m, const __grid_constant__ DevLines Ln, const __grid_constant__ DevRays Rs,
         const __grid_constant__ SolveArgs a) {
-    __shared__ Stage<R, NL> stage[Occ<R, NL, BPL>::kWarps];  // one per warp
-    __shared__ Lane<R, ORD> lanes[Occ<R, NL, BPL>::kWarps];
+    __shared__ Stage<R, NL> stage[Occ<R, NL, BPL, P>::kWarps];  // one per warp
+    __shared__ Lane<R, ORD, P> lanes[Occ<R, NL, BPL, P>::kWarps];
     const int lane = threadIdx.x & 31;
     const int64_t item = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
     const int64_t n_items = int64_t(a.o_end - a.o_begin) * a.n_tiles;
     if (item >= n_items) return;
-    solve_item<R, NL, BPL, ORD>(m, Ln, Rs, a, int32_t(item / a.n_tiles), int32_t(item % a.n_tiles),
+    solve_item<R, NL, BPL, ORD, P>(m, Ln, Rs, a, int32_t(item / a.n_tiles), int32_t(item % a.n_tiles),
                                 stage[threadIdx.x >> 5], lanes[threadIdx.x >> 5], lane);
 }
 
 // Persistent launch over a work list of (model, origin, tile) items of many
 // models: each warp takes the next item from a global counter until the list
 // is exhausted.
-template <typename R, int NL, int BPL, int ORD>
-__global__ void __launch_bounds__(Occ<R, NL, BPL>::kThreads, (Occ<R, NL, BPL>::kMinBlocks))
+template <typename R, int NL, int BPL, int ORD, typename P>
+__global__ void __launch_bounds__(Occ<R, NL, BPL, P>::kThreads, (Occ<R, NL, BPL, P>::kMinBlocks))
 k_solve_queue(const BatchSlot *__restrict__ slots, const uint2 *__restrict__ work, int64_t n_work,
               unsigned long long *__restrict__ next) {
-    __shared__ Stage<R, NL> stage[Occ<R, NL, BPL>::kWarps];
-    __shared__ Lane<R, ORD> lanes[Occ<R, NL, BPL>::kWarps];
+    __shared__ Stage<R, NL> stage[Occ<R, NL, BPL, P>::kWarps];
+    __shared__ Lane<R, ORD, P> lanes[Occ<R, NL, BPL, P>::kWarps];
     const int lane = threadIdx.x & 31;
     for (;;) {
         unsigned long long it = 0;
@@ -1213,7 +1230,7 @@ k_solve_queue(const BatchSlot *__restrict__ slots, const uint2 *__restrict__ wor
         if (it >= (unsigned long long)n_work) return;
         const uint2 w = work[it];  // x = model << 16 | tile, y = origin
         const BatchSlot &s = slots[w.x >> 16];
-        solve_item<R, NL, BPL, ORD>(s.m, s.Ln, s.R, s.a, int32_t(w.y), int32_t(w.x & 0xffffu), stage[threadIdx.x >> 5],
+        solve_item<R, NL, BPL, ORD, P>(s.m, s.Ln, s.R, s.a, int32_t(w.y), int32_t(w.x & 0xffffu), stage[threadIdx.x >> 5],
                                     lanes[threadIdx.x >> 5], lane);
         __syncwarp();
     }
@@ -1230,51 +1247,51 @@ void prefer_shared(K kernel) {
     }
 }
 
-template <typename R, int BPL, int ORD>
+template <typename R, int BPL, int ORD, typename P = R>
 void launch_RB(const DevMesh &m, const DevLines &Ln, const DevRays &R_, const SolveArgs &a, cudaStream_t st) {
     const int64_t n_items = int64_t(a.o_end - a.o_begin) * a.n_tiles;
     if (n_items == 0) return;
-    constexpr int tb = Occ<R, 1, BPL>::kThreads;
+    constexpr int tb = Occ<R, 1, BPL, P>::kThreads;
     const unsigned grid = unsigned((n_items * 32 + tb - 1) / tb);
     if (Ln.L <= 1) {
-        prefer_shared(k_solve<R, 1, BPL, ORD>);
-        k_solve<R, 1, BPL, ORD><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+        prefer_shared(k_solve<R, 1, BPL, ORD, P>);
+        k_solve<R, 1, BPL, ORD, P><<<grid, tb, 0, st>>>(m, Ln, R_, a);
     } else if (Ln.L <= 2) {
-        prefer_shared(k_solve<R, 2, BPL, ORD>);
-        k_solve<R, 2, BPL, ORD><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+        prefer_shared(k_solve<R, 2, BPL, ORD, P>);
+        k_solve<R, 2, BPL, ORD, P><<<grid, tb, 0, st>>>(m, Ln, R_, a);
     } else if (Ln.L <= 4) {
-        prefer_shared(k_solve<R, 4, BPL, ORD>);
-        k_solve<R, 4, BPL, ORD><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+        prefer_shared(k_solve<R, 4, BPL, ORD, P>);
+        k_solve<R, 4, BPL, ORD, P><<<grid, tb, 0, st>>>(m, Ln, R_, a);
     } else {
-        prefer_shared(k_solve<R, 8, BPL, ORD>);
-        k_solve<R, 8, BPL, ORD><<<grid, tb, 0, st>>>(m, Ln, R_, a);
+        prefer_shared(k_solve<R, 8, BPL, ORD, P>);
+        k_solve<R, 8, BPL, ORD, P><<<grid, tb, 0, st>>>(m, Ln, R_, a);
     }
 }
 
-template <typename R, int BPL, int NL, int ORD>
+template <typename R, int BPL, int NL, int ORD, typename P = R>
 void launch_queue_NL(const BatchSlot *slots, const uint2 *work, int64_t n_work, unsigned long long *next,
                      cudaStream_t st) {
     int dev = 0, sms = 152, per_sm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    constexpr int tb = Occ<R, NL, BPL>::kThreads, nw = Occ<R, NL, BPL>::kWarps;
-    prefer_shared(k_solve_queue<R, NL, BPL, ORD>);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_queue<R, NL, BPL, ORD>, tb, 0);
+    constexpr int tb = Occ<R, NL, BPL, P>::kThreads, nw = Occ<R, NL, BPL, P>::kWarps;
+    prefer_shared(k_solve_queue<R, NL, BPL, ORD, P>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_queue<R, NL, BPL, ORD, P>, tb, 0);
     if (per_sm < 1) per_sm = 1;
     int64_t grid = int64_t(sms) * per_sm;
     const int64_t need = (n_work + nw - 1) / nw;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    k_solve_queue<R, NL, BPL, ORD><<<unsigned(grid), tb, 0, st>>>(slots, work, n_work, next);
+    k_solve_queue<R, NL, BPL, ORD, P><<<unsigned(grid), tb, 0, st>>>(slots, work, n_work, next);
 }
 
-template <typename R, int BPL, int ORD>
+template <typename R, int BPL, int ORD, typename P = R>
 void launch_queue_RB(int max_lines, const BatchSlot *slots, const uint2 *work, int64_t n_work,
                      unsigned long long *next, cudaStream_t st) {
-    if (max_lines <= 1) launch_queue_NL<R, BPL, 1, ORD>(slots, work, n_work, next, st);
-    else if (max_lines <= 2) launch_queue_NL<R, BPL, 2, ORD>(slots, work, n_work, next, st);
-    else if (max_lines <= 4) launch_queue_NL<R, BPL, 4, ORD>(slots, work, n_work, next, st);
-    else launch_queue_NL<R, BPL, 8, ORD>(slots, work, n_work, next, st);
+    if (max_lines <= 1) launch_queue_NL<R, BPL, 1, ORD, P>(slots, work, n_work, next, st);
+    else if (max_lines <= 2) launch_queue_NL<R, BPL, 2, ORD, P>(slots, work, n_work, next, st);
+    else if (max_lines <= 4) launch_queue_NL<R, BPL, 4, ORD, P>(slots, work, n_work, next, st);
+    else launch_queue_NL<R, BPL, 8, ORD, P>(slots, work, n_work, next, st);
 }
 
 }  // namespace
@@ -1284,6 +1301,7 @@ void launch_solve_ord(const DevMesh &m, const DevLines &Ln, const DevRays &R, co
                       cudaStream_t st) {
     const int bpl = solve_bins_per_lane(precision, Ln.L * Ln.F);
     if (precision == MGX_FP64) launch_RB<double, 1, ORD>(m, Ln, R, a, st);
+    else if (precision == MGX_FP32_DT64) launch_solve_dt64(m, Ln, R, a, bpl, st);
     else if (bpl == 2) launch_RB<float, 2, ORD>(m, Ln, R, a, st);
     else launch_RB<float, 1, ORD>(m, Ln, R, a, st);
 }
@@ -1293,6 +1311,8 @@ void launch_solve_queue_ord(int precision, int bins_per_lane, int max_lines, con
                             const uint2 *work, int64_t n_work, unsigned long long *next, cudaStream_t st) {
     if (n_work == 0) return;
     if (precision == MGX_FP64) launch_queue_RB<double, 1, ORD>(max_lines, slots, work, n_work, next, st);
+    else if (precision == MGX_FP32_DT64)
+        launch_solve_queue_dt64(bins_per_lane, max_lines, slots, work, n_work, next, st);
     else if (bins_per_lane == 2) launch_queue_RB<float, 2, ORD>(max_lines, slots, work, n_work, next, st);
     else launch_queue_RB<float, 1, ORD>(max_lines, slots, work, n_work, next, st);
 }

@@ -853,7 +853,10 @@ mgx_status mgx_solve_J(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, v
     if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0)) return fail(ctx, MGX_EINVAL, "solve_J: dtau_max must be > 0");
     if (!std::isfinite(p->dv_max)) return fail(ctx, MGX_EINVAL, "solve_J: dv_max must be finite");
     if (!std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J: I_bdy must be finite");
-    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J: unknown precision");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32 && p->precision != MGX_FP32_DT64)
+        return fail(ctx, MGX_EINVAL, "solve_J: unknown precision");
+    if (p->precision == MGX_FP32_DT64 && p->order == 4)
+        return fail(ctx, MGX_EINVAL, "solve_J: MGX_FP32_DT64 exists for the second-order scheme only");
     if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
         return fail(ctx, MGX_EINVAL, "solve_J: order must be 0, 2 or 4 (reserved 0)");
     DeviceGuard g(ctx->device);
@@ -992,7 +995,10 @@ mgx_status mgx_solve_u(mgx_ctx *ctx, int32_t model, const mgx_solve_params *p, i
     if (!m->has_lines || !m->has_rays) return fail(ctx, MGX_ESTATE, "solve_u: set_lines / set_rays not called");
     if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0) || !std::isfinite(p->dv_max) || !std::isfinite(p->I_bdy))
         return fail(ctx, MGX_EINVAL, "solve_u: dtau_max must be > 0, dv_max and I_bdy finite");
-    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_u: unknown precision");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32 && p->precision != MGX_FP32_DT64)
+        return fail(ctx, MGX_EINVAL, "solve_u: unknown precision");
+    if (p->precision == MGX_FP32_DT64 && p->order == 4)
+        return fail(ctx, MGX_EINVAL, "solve_u: MGX_FP32_DT64 exists for the second-order scheme only");
     if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
         return fail(ctx, MGX_EINVAL, "solve_u: order must be 0, 2 or 4 (reserved 0)");
     if (o_begin < 0 || o_end > m->n || o_begin > o_end) return fail(ctx, MGX_EINVAL, "solve_u: bad origin range");
@@ -1103,7 +1109,10 @@ mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_para
     if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: dtau_max must be > 0");
     if (!std::isfinite(p->dv_max)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: dv_max must be finite");
     if (!std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: I_bdy must be finite");
-    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J_noalloc: unknown precision");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32 && p->precision != MGX_FP32_DT64)
+        return fail(ctx, MGX_EINVAL, "solve_J_noalloc: unknown precision");
+    if (p->precision == MGX_FP32_DT64 && p->order == 4)
+        return fail(ctx, MGX_EINVAL, "solve_J_noalloc: MGX_FP32_DT64 exists for the second-order scheme only");
     if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
         return fail(ctx, MGX_EINVAL, "solve_J_noalloc: order must be 0, 2 or 4 (reserved 0)");
     cudaPointerAttributes attr;
@@ -1134,7 +1143,10 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         return fail(ctx, MGX_EINVAL, "solve_J_batch: bad model list, params or outputs");
     if (!std::isfinite(p->dtau_max) || !(p->dtau_max > 0.0)) return fail(ctx, MGX_EINVAL, "solve_J_batch: dtau_max must be > 0");
     if (!std::isfinite(p->dv_max) || !std::isfinite(p->I_bdy)) return fail(ctx, MGX_EINVAL, "solve_J_batch: dv_max, I_bdy must be finite");
-    if (p->precision != MGX_FP64 && p->precision != MGX_FP32) return fail(ctx, MGX_EINVAL, "solve_J_batch: unknown precision");
+    if (p->precision != MGX_FP64 && p->precision != MGX_FP32 && p->precision != MGX_FP32_DT64)
+        return fail(ctx, MGX_EINVAL, "solve_J_batch: unknown precision");
+    if (p->precision == MGX_FP32_DT64 && p->order == 4)
+        return fail(ctx, MGX_EINVAL, "solve_J_batch: MGX_FP32_DT64 exists for the second-order scheme only");
     if ((p->order != 0 && p->order != 2 && p->order != 4) || p->reserved != 0)
         return fail(ctx, MGX_EINVAL, "solve_J_batch: order must be 0, 2 or 4 (reserved 0)");
     if (flags & ~(MGX_BATCH_GRAPH | MGX_BATCH_RAYS)) return fail(ctx, MGX_EINVAL, "solve_J_batch: unknown flags");
@@ -1175,7 +1187,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         pl.max_lines = std::max(pl.max_lines, int(m->L));
     }
     pl.bpl = solve_bins_per_lane(p->precision, int32_t(max_nb));
-    if (p->precision == MGX_FP32 && pl.tune.bins_per_lane > 0) pl.bpl = pl.tune.bins_per_lane;
+    if (p->precision != MGX_FP64 && pl.tune.bins_per_lane > 0) pl.bpl = pl.tune.bins_per_lane;
     std::vector<BatchGeom> geo(static_cast<size_t>(n_models));
     std::vector<int64_t> obase(static_cast<size_t>(n_models));
     pl.total_half = pl.n_origins = pl.n_work = 0;
@@ -1384,14 +1396,14 @@ mgx_status mgx_autotune(mgx_ctx *ctx, const int32_t *models, int32_t n_models, c
     };
     // start from the current tuning with its automatic fields made explicit
     mgx_tuning best = saved;
-    if (best.bins_per_lane == 0 && p->precision == MGX_FP32) best.bins_per_lane = solve_bins_per_lane(MGX_FP32, int32_t(max_nb));
+    if (best.bins_per_lane == 0 && p->precision != MGX_FP64) best.bins_per_lane = solve_bins_per_lane(MGX_FP32, int32_t(max_nb));
     if (best.trace_ctas_per_sm == 0) best.trace_ctas_per_sm = 8;
     if (best.tail_permille == 0) best.tail_permille = 20;
     double best_ms = 0.0;
     mgx_status s = time_one(best, &best_ms);
     const int32_t bpl_c[] = {1, 2}, trace_c[] = {4, 6, 8}, tail_c[] = {5, 20, 80}, sched_c[] = {0, 1};
     for (int dim = 0; dim < 4 && s == MGX_OK; ++dim) {
-        if (dim == 0 && p->precision != MGX_FP32) continue;
+        if (dim == 0 && p->precision == MGX_FP64) continue;
         const int32_t *cand = dim == 0 ? bpl_c : dim == 1 ? trace_c : dim == 2 ? tail_c : sched_c;
         const int nc = (dim == 0 || dim == 3) ? 2 : 3;
         const mgx_tuning base = best;
@@ -1704,6 +1716,15 @@ mgx_status mgx_eval_approx(mgx_ctx *ctx, int32_t kind, const float *x, int64_t n
     DeviceGuard g(ctx->device);
     launch_eval_approx(kind, x, n, y, ctx->stream);
     CK(cudaGetLastError());
+    return MGX_OK;
+}
+
+mgx_status mgx_alu_peaks(mgx_ctx *ctx, int32_t reps, double *out) {
+    if (!ctx) return MGX_EINVAL;
+    ctx->err.clear();
+    if (!out || reps < 1 || reps > 100) return fail(ctx, MGX_EINVAL, "alu_peaks: null output or reps outside 1..100");
+    DeviceGuard g(ctx->device);
+    CK(alu_peaks(ctx->stream, reps, out));
     return MGX_OK;
 }
 

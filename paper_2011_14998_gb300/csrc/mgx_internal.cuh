@@ -177,6 +177,12 @@ void launch_solve(const DevMesh &m, const DevLines &Ln, const DevRays &R, const 
 // persistent launch over a work list (x = model << 16 | tile, y = origin); next: zeroed counter
 void launch_solve_queue(int precision, int order, int bins_per_lane, int max_lines, const BatchSlot *slots,
                         const uint2 *work, int64_t n_work, unsigned long long *next, cudaStream_t st);
+// the single-precision form with double-precision increments and pivots
+// (MGX_FP32_DT64, second-order scheme; k_solve_mix.cu)
+void launch_solve_dt64(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a, int bins_per_lane,
+                       cudaStream_t st);
+void launch_solve_queue_dt64(int bins_per_lane, int max_lines, const BatchSlot *slots, const uint2 *work,
+                             int64_t n_work, unsigned long long *next, cudaStream_t st);
 // the two instantiations (k_solve.cu, k_solve_herm.cu)
 template <int ORD>
 void launch_solve_ord(const DevMesh &m, const DevLines &Ln, const DevRays &R, const SolveArgs &a, int precision,
@@ -242,6 +248,9 @@ void launch_select_top(const float *score, int64_t n, int64_t k, int32_t *ids, f
 // relative error bound the solve's decisions take for each
 void launch_eval_approx(int kind, const float *x, int64_t n, float *y, cudaStream_t st);
 float approx_bound(int kind);
+
+// ---- arithmetic-pipe throughput microbenchmarks (k_peaks.cu)
+cudaError_t alu_peaks(cudaStream_t st, int reps, double out[4]);
 
 // ---- host HEALPix tables (hpx_host.cpp)
 int64_t hpx_npix(int l);

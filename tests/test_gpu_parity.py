@@ -147,6 +147,26 @@ def test_wind_J_fp64_and_fp32(ctx, orc, wind_small, dv_max):
     assert r32 < FP32_TOL, r32
 
 
+def test_wind_double_pivot_form(ctx, orc, wind_small):
+    """MGX_FP32_DT64 (optical-depth increments and the pivot recurrence in
+    double precision, the rest single) against the FP64 oracle; the Hermitian
+    scheme is refused in that form."""
+    import paper_2011_14998_gb300 as mgx
+
+    m = wind_small
+    mid = ctx.load(m)
+    J = ctx.solve_J(mid, precision=mgx.MGX_FP32_DT64)
+    Jb = ctx.solve_J_batch([mid], precision=mgx.MGX_FP32_DT64)[0].cpu().numpy()
+    rays = ctx.rays(mid)
+    with pytest.raises(mgx.MgxError):
+        ctx.solve_J(mid, precision=mgx.MGX_FP32_DT64, order=4)
+    ctx.free(mid)
+    origins = np.arange(0, len(m["pos"]), 5)
+    Jo = _oracle(orc, m, rays=rays).solve_J(orc.params(), origins=origins)
+    assert j_rel_err(J[origins], Jo)[0] < FP32_TOL
+    assert j_rel_err(Jb[origins], Jo)[0] < FP32_TOL
+
+
 def test_multiline_adaptive_J(ctx, orc, cloud_multi):
     import paper_2011_14998_gb300 as mgx
 
