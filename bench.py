@@ -391,7 +391,7 @@ def run_mgx(args):
     lp = prof32["launches"]
     wl = 3 if tuning.get("schedule", 0) == 0 else 1
     launches = args.steps * (lp["rays"] + lp["trace_count"] + lp["trace_emit"] + wl * lp["other"] + lp["solve"]) // kb
-    traffic = solve_traffic()
+    traffic = solve_traffic(prof32["trace_points"] // kb)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t32 / args.steps, "higher_is_better": True,
@@ -422,6 +422,8 @@ def run_mgx(args):
         "roofline": {"kernel": "k_solve_queue<float>", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                      "peak_source": "measured: FP32 FMA chains on every SM (mgx_alu_peaks), of measured",
+                     "traffic_source": "ncu capture of the 20 000-point case (profiles/k_solve_queue_wind20k.md) "
+                                       "scaled by traced points per launch; null once the solve source changed",
                      "derived_peak": fp32_derived, "frac_of_derived": achieved / fp32_derived,
                      "mufu": {"ops_per_launch": mufu_ops, "achieved_gops": mufu_ops / (ms_solve * 1e-3) / 1e9,
                               "peak_gops": alu["ex2_gops"],
@@ -440,7 +442,7 @@ def run_mgx(args):
         torch.distributed.destroy_process_group()
 
 
-SOLVE_PROFILE = os.path.join(ROOT, "profiles", "k_solve_queue_wind50k.md")
+SOLVE_PROFILE = os.path.join(ROOT, "profiles", "k_solve_queue_wind20k.md")
 SOLVE_SOURCES = ("k_solve_impl.cuh", "k_solve.cu")
 
 
@@ -457,21 +459,24 @@ def hermitian_accuracy(m, rays, J32h, n=200):
     return {"fp32_max_rel": float(rel.max()), "fp32_p99_rel": float(np.quantile(rel, 0.99)), "origins": n}
 
 
-def solve_traffic():
-    """DRAM bytes per launch of the solve kernel from its committed ncu summary,
-    or None when the kernel source has changed since the counters were taken
-    (the summary records the SHA-256 of the solve's sources, concatenated in
-    the order of SOLVE_SOURCES, it was measured with)."""
+def solve_traffic(trace_points_per_launch):
+    """DRAM bytes of one solve launch: the committed ncu summary's capture of the
+    20 000-point case scaled by traced points per launch, or None when the
+    kernel source has changed since the counters were taken (the summary
+    records the SHA-256 of the solve's sources, concatenated in the order of
+    SOLVE_SOURCES)."""
     import hashlib
 
     try:
-        kv = dict(l.split(":", 1) for l in open(SOLVE_PROFILE).read().splitlines() if l.startswith("dram_") or
-                  l.startswith("k_solve_sha256"))
+        kv = dict(l.strip().split(":", 1) for l in open(SOLVE_PROFILE).read().splitlines()
+                  if l.strip().startswith(("dram_", "k_solve_sha256", "trace_points_per_launch")))
         src = b"".join(open(os.path.join(ROOT, "paper_2011_14998_gb300", "csrc", f), "rb").read()
                        for f in SOLVE_SOURCES)
         if hashlib.sha256(src).hexdigest() != kv["k_solve_sha256"].strip():
             return None
-        return int(kv["dram_bytes_read"]) + int(kv["dram_bytes_write"])
+        per_point = (int(kv["dram_bytes_read_20k"]) + int(kv["dram_bytes_write_20k"])) / int(
+            kv["trace_points_per_launch_20k"])
+        return int(per_point * trace_points_per_launch)
     except (OSError, KeyError, ValueError):
         return None
 

@@ -136,6 +136,20 @@ def rayset(pos, l_min, l_max, sample=None, threads=None) -> np.ndarray:
     return out
 
 
+def rayset_at(pos, origins, l_min, l_max, sample=None) -> np.ndarray:
+    """Ray sets of the given origins only: [len(origins)][npairs]."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    sample = np.zeros(0, np.int32) if sample is None else np.ascontiguousarray(sample, np.int32)
+    npairs = rayset_npairs(l_min, l_max)
+    out = np.zeros((len(origins), npairs), dtype=np.uint32)
+    for q, o in enumerate(origins):
+        row = np.zeros(npairs, np.uint32)
+        if lib().orc_rayset_one(len(pos), _p(pos), int(o), len(sample), _p(sample), l_min, l_max, _p(row)) != 0:
+            raise ValueError("oracle ray set failed")
+        out[q] = row
+    return out
+
+
 # ---------------------------------------------------------------- model
 class OracleModel:
     """Holds contiguous FP64 copies of a model and the oracle's own ray set."""

@@ -86,6 +86,28 @@ def loss_and_grad(theta, X, t, bf=False):
     return L, pack(g)
 
 
+def grad_magnitudes(theta, X, t, bf=False):
+    """For every gradient element, the sum of the magnitudes of the terms that
+    loss_and_grad adds up for it (|h|^T |d| for a weight, sum |d| for a bias):
+    the scale against which the rounding of a differently ordered or
+    differently rounded evaluation of the same sums is measured."""
+    p = unpack(theta)
+    y, c = forward(theta, X, bf)
+    t = np.asarray(t, np.float64)
+    n = len(t)
+    ady = np.abs(2.0 * (y - t) / n)
+    g = {}
+    g["b3"] = np.array([ady.sum()])
+    g["W3"] = np.abs(c["h2"]).T @ ady
+    adh2 = np.outer(ady, np.abs(p["W3"])) * (c["h2"] > 0)
+    g["b2"] = adh2.sum(0)
+    g["W2"] = np.abs(c["h1"]).T @ adh2
+    adh1 = (adh2 @ np.abs(c["W2"]).T) * (c["h1"] > 0)
+    g["b1"] = adh1.sum(0)
+    g["W1"] = np.abs(c["X"]).T @ adh1
+    return pack(g)
+
+
 def init(seed: int) -> np.ndarray:
     """He-normal weights, zero biases."""
     rng = np.random.default_rng(seed)

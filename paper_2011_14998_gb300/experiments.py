@@ -116,6 +116,62 @@ def reduction_speedup(ctx, m: dict, f_small, f_large, G_thres, seed=1, precision
                 frac_below_10pct=float((err < 0.1).mean()))
 
 
+def error_cdf(err: np.ndarray, bins: int = 1000, lo: float = -8.0, hi: float = 1.0):
+    """Cumulative distribution of per-point relative errors over `bins` bins
+    uniform in log10(error) on [lo, hi] (errors below 10^lo in the first bin):
+    (bin upper edges, fraction of points at or below each edge)."""
+    e = np.log10(np.maximum(np.asarray(err, np.float64), 10.0 ** lo))
+    edges = np.linspace(lo, hi, bins + 1)[1:]
+    h = np.histogram(np.minimum(e, hi), bins=bins, range=(lo, hi))[0]
+    return edges, np.cumsum(h) / max(len(e), 1)
+
+
+def reduction_sweep(ctx, m: dict, table1, scales=(1.0, 1.4, 2.0), seed=1, precision=MGX_FP32, reps=3,
+                    std=None, alpha=2.0):
+    """Solve-time speed-up against reduction factor (Table 2 shape, Fig. 6): the
+    plain criterion with Table 1's factors scaled by each of `scales`, and, when
+    a trained network's feature standardiser `std` is given, the weighted learned
+    thinning at the same kept fraction.  Per run: reduction factor, speed-up of
+    the reduced solve, mean and p90 per-point error, and its CDF (1000 bins)."""
+    import torch
+
+    from . import learned
+
+    def timed_solve(model):
+        mid = ctx.load(model)
+        ctx.solve_J(mid, precision=precision)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            J = ctx.solve_J(mid, precision=precision)
+        torch.cuda.synchronize()
+        return mid, J, (time.perf_counter() - t0) / reps
+
+    f_small, f_large, g_thres = table1
+    mid, J_full, t_full = timed_solve(m)
+    runs = []
+    try:
+        for k in scales:
+            keeps = {"plain": ctx.reduce_mesh(mid, m["rho"], f_small * k, f_large * k, g_thres, seed)[3]}
+            if std is not None:
+                keeps["learned_weighted"] = learned.reduce_learned_weighted(ctx, mid, m, std,
+                                                                            float(keeps["plain"].mean()), alpha, seed)
+            for crit, keep in keeps.items():
+                r = learned.remesh(m, keep)
+                mr, J_red, t_red = timed_solve(r)
+                ctx.free(mr)
+                err = learned.point_errors(J_full, learned.interpolate(r["pos"], J_red, m["pos"]))
+                edges, cdf = error_cdf(err)
+                runs.append(dict(criterion=crit, scale=k, n_reduced=len(r["pos"]),
+                                 reduction=len(m["pos"]) / len(r["pos"]), t_reduced_s=t_red,
+                                 speedup=t_full / t_red, mean_rel_err=float(err.mean()),
+                                 p90_rel_err=float(np.quantile(err, 0.9)), cdf_log10_edges=edges.tolist(),
+                                 cdf=cdf.tolist()))
+    finally:
+        ctx.free(mid)
+    return dict(n_original=len(m["pos"]), t_full_s=t_full, runs=runs)
+
+
 def batch_schedule(ctx, models, precision=MGX_FP32, reps=3):
     """Step time of one batched solve over `models` with the cost-binned and the plain work list."""
     import torch
@@ -270,6 +326,60 @@ def learned_vs_plain(ctx, make_model, train_seeds, test_seed, table1, keep_fract
                 frac_below_1pct_learned=float((e_mlp < 0.01).mean()), weighted=weighted)
 
 
+def learned_reduction_study(ctx, make_train, train_seeds, test_model, table1, fractions=(0.2, 0.1),
+                            scales=(1.0, 1.5, 2.2), alphas=(1.0, 2.0), epochs=40, seed=11):
+    """Train the reduction network once on J errors of plain reductions of the
+    training models, then compare the plain criterion, the top-ranked points and
+    the weighted thinning at each kept fraction of the test model (same number
+    of points kept): mean and p90 of the per-point J error after re-meshing and
+    barycentric interpolation back to the full mesh."""
+    from . import learned
+
+    f_small, f_large, g_thres = table1
+    t0 = time.perf_counter()
+    Xs, ys = [], []
+    for s_ in train_seeds:
+        m = make_train(s_)
+        reds = [(f_small * k, f_large * k, g_thres, 1000 + 10 * s_ + j) for j, k in enumerate(scales)]
+        X, y = learned.training_samples(ctx, m, reds)
+        Xs.append(X)
+        ys.append(y)
+        del m
+    X, y = np.concatenate(Xs), np.concatenate(ys)
+    std, losses, _ = learned.train_network(ctx, X, y, epochs=epochs, seed=1)
+    t_train = time.perf_counter() - t0
+    test = test_model
+    mid = ctx.load(test)
+    rows = []
+    try:
+        J_full = ctx.solve_J(mid, precision=MGX_FP32)
+        for frac in fractions:
+            lo, hi = 0.25, 16.0
+            for _ in range(40):
+                k = np.sqrt(lo * hi)
+                keep = ctx.reduce_mesh(mid, test["rho"], f_small * k, f_large * k, g_thres, seed)[3]
+                if keep.mean() > frac:
+                    lo = k
+                else:
+                    hi = k
+                if hi / lo < 1.001:
+                    break
+            keeps = {"plain": ctx.reduce_mesh(mid, test["rho"], f_small * hi, f_large * hi, g_thres, seed)[3]}
+            kf = float(keeps["plain"].mean())
+            keeps["top_k"] = learned.reduce_learned(ctx, mid, test, std, kf)
+            for a in alphas:
+                keeps[f"weighted_alpha_{a}"] = learned.reduce_learned_weighted(ctx, mid, test, std, kf, a, seed)
+            for name, kp in keeps.items():
+                e = learned.reduction_error(ctx, test, J_full, kp)
+                rows.append(dict(target_fraction=frac, criterion=name, kept_fraction=float(kp.mean()),
+                                 reduction=float(1.0 / kp.mean()), mean_rel_err=float(e.mean()),
+                                 p90=float(np.quantile(e, 0.9)), frac_below_1pct=float((e < 0.01).mean())))
+    finally:
+        ctx.free(mid)
+    return dict(n_test=len(test["pos"]), train_seeds=list(train_seeds), train_samples=int(len(y)),
+                train_s=t_train, loss_first=float(losses[0]), loss_last=float(losses[-1]), rows=rows)
+
+
 def main(argv):
     import synth
 
@@ -314,6 +424,46 @@ def main(argv):
             print(json.dumps(dict(experiment="batch_throughput", n_max=n_max, lines=4, bins_per_line=100,
                                   rays="adaptive l 0-3", generation_s=gen,
                                   **batch_throughput(ctx, models))), flush=True)
+        elif which == "sweep":
+            # f3: speed-up against reduction factor on the two synthetic stand-ins, plain and learned
+            n = int(argv[2]) if len(argv) > 2 else 200_000
+            out_path = argv[3] if len(argv) > 3 else None
+            cases = [("AMR (clump octree)",
+                      lambda s_, n_: synth.octree_model(n_, seed=s_, n_lines=1, n_freq=50, l_min=2, l_max=2),
+                      (0.90, 2.10, 0.10), 3),
+                     ("SPH (binary-wind spiral)", lambda s_, n_: synth.spiral_model(n_, seed=s_, n_freq=50),
+                      (1.00, 2.15, 0.21), 4)]
+            from . import learned
+            allres = []
+            for name, mk, t1, test_seed in cases:
+                Xs, ys = [], []
+                for s_ in (100, 101):
+                    mt = mk(s_, n // 2)
+                    X, y = learned.training_samples(ctx, mt, [(t1[0] * k, t1[1] * k, t1[2], 1000 + 10 * s_ + j)
+                                                              for j, k in enumerate((1.0, 1.5, 2.2))])
+                    Xs.append(X)
+                    ys.append(y)
+                std, _, _ = learned.train_network(ctx, np.concatenate(Xs), np.concatenate(ys), epochs=40, seed=1)
+                res = reduction_sweep(ctx, mk(test_seed, n), t1, scales=(1.0, 1.3, 1.7, 2.2, 3.0), std=std)
+                res.update(experiment="reduction_sweep", model=name, table1=t1)
+                allres.append(res)
+                print(json.dumps({k: v for k, v in res.items() if k != "runs"} | {"runs": [
+                    {k: v for k, v in r.items() if not k.startswith("cdf")} for r in res["runs"]]}), flush=True)
+            if out_path:
+                with open(out_path, "w") as f:
+                    json.dump(allres, f)
+        elif which == "learned4":
+            # the binary-wind spiral: training seeds 100-103 at n_train points, the
+            # test seed 4 at n_test particles (1 line x 100 bins, l = 2)
+            n_test = int(argv[2]) if len(argv) > 2 else 1_000_000
+            n_train = int(argv[3]) if len(argv) > 3 else 150_000
+            t0 = time.perf_counter()
+            test = synth.spiral_model(n_test, seed=4)
+            gen = time.perf_counter() - t0
+            res = learned_reduction_study(ctx, lambda s_: synth.spiral_model(n_train, seed=s_),
+                                          (100, 101, 102, 103), test, (1.00, 2.15, 0.21))
+            print(json.dumps(dict(experiment="learned_reduction_study", model="SPH (binary-wind spiral)",
+                                  n_train=n_train, generation_s=gen, **res)), flush=True)
         elif which == "learned":
             n = int(argv[2]) if len(argv) > 2 else 20000
 

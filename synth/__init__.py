@@ -171,7 +171,8 @@ def spiral_model(n: int = 1_000_000, seed: int = 4, n_freq: int = 100, x_span: f
     spiral r = r0 + arm_spacing phi / 2 pi in the orbital plane (arm half-width
     8 AU, scale height 30 AU), in a box of `box` AU; equal-mass particles
     (positions drawn with probability ~ rho), Delaunay neighbours, a 15 km/s
-    radial wind with 1 km/s noise, T = 2000 K (r / 10 AU)^-0.7."""
+    radial wind plus a smooth random field of 64 Fourier modes (1 km/s rms per
+    component), T = 2000 K (r / 10 AU)^-0.7."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5B]))
     r_in, r_out = 10.0, box / 2.0
 
@@ -198,7 +199,7 @@ def spiral_model(n: int = 1_000_000, seed: int = 4, n_freq: int = 100, x_span: f
     off, nbr = delaunay_csr(pos)
     r = np.sqrt((pos ** 2).sum(1))
     rhat = pos / r[:, None]
-    vel = 15.0 * rhat + rng.normal(0.0, 1.0, (n, 3))
+    vel = 15.0 * rhat + _fourier_velocity(pos, rng, 64, 1.0, box)
     rho = (r / r_in) ** -2.0 * (1 + (contrast - 1) * arm(pos))
     T = 2000.0 * (r / r_in) ** -0.7
     k = tau_radial / (r_in * (1 - r_in / r_out))  # radial line-centre depth of the smooth r^-2 part
@@ -353,14 +354,17 @@ def with_lines(m: dict, n_lines: int, n_freq: int, line_ratio: float = 0.5) -> d
 
 
 def batch_models(n_models: int = 64, seed: int = 5, n_min: int = 10_000, n_max: int = 200_000, n_lines: int = 4,
-                 n_freq: int = 100, l_min: int = 0, l_max: int = 3):
+                 n_freq: int = 100, l_min: int = 0, l_max: int = 3, only=None):
     """Independent models with seeded sizes log-uniform in [n_min, n_max], the
     generators taken in turn (Cartesian grid, stellar wind, clump octree), each
-    with n_lines separated lines of n_freq bins and adaptive rays l_min..l_max."""
+    with n_lines separated lines of n_freq bins and adaptive rays l_min..l_max.
+    `only` (indices) builds just those members of the same draw."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA]))
     sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_models)).astype(np.int64)
     out = []
     for k, n in enumerate(sizes):
+        if only is not None and k not in only:
+            continue
         s = seed * 1000 + k
         kind = k % 3
         if kind == 0:

@@ -49,10 +49,16 @@ def test_gradient_matches_oracle(ctx):
     g, loss = mgx.mgx_mlp_grad(ctx.ptr, X, t)
     Lo, go = mlp.loss_and_grad(mgx.mgx_mlp_get_params(ctx.ptr).astype(np.float64), X, t, bf=True)
     assert loss == pytest.approx(Lo, rel=5e-3)
-    gl, gol = _layers(g), _layers(go)
+    # element by element: every gradient entry within 2^-6 (two bfloat16 units) of the sum of the
+    # magnitudes of the terms it adds up; a transposed or shifted block fails this
+    mag = mlp.grad_magnitudes(mgx.mgx_mlp_get_params(ctx.ptr).astype(np.float64), X, t, bf=True)
+    gl, gol, ml = _layers(g), _layers(go), _layers(mag)
     for name in gl:
-        err = np.linalg.norm(gl[name] - gol[name]) / max(np.linalg.norm(gol[name]), 1e-12)
-        assert err < 1e-2, (name, err)
+        bad = np.abs(gl[name] - gol[name]) > 2.0 ** -6 * ml[name] + 1e-9
+        assert not bad.any(), (name, int(bad.sum()), float(np.abs(gl[name] - gol[name]).max()))
+    # the bound is tight enough to see a transposed W2 block
+    W2 = gol["W2"]
+    assert (np.abs(W2.T - W2) > 2.0 ** -6 * ml["W2"] + 1e-9).any()
 
 
 def test_training_reduces_loss(ctx):

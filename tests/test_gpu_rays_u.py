@@ -74,3 +74,23 @@ def test_reduction_speedup_experiment(ctx):
     assert res["n_reduced"] < res["n_original"]
     assert res["speedup"] > 1.0
     assert np.isfinite(res["mean_rel_err"])
+
+
+def test_reduction_sweep_speedup_grows(ctx):
+    """Table 2 / Fig. 6 shape on the clump octree: stronger plain reductions give
+    larger solve speed-ups, and the per-point error CDF is a distribution."""
+    import synth
+
+    from paper_2011_14998_gb300 import experiments
+
+    m = synth.octree_model(20000, seed=12, hi_level=7, n_lines=1, n_freq=20, l_min=1, l_max=1)
+    res = experiments.reduction_sweep(ctx, m, (0.90, 2.10, 0.10), scales=(1.0, 1.6, 2.6), reps=3)
+    runs = res["runs"]
+    red = [r["reduction"] for r in runs]
+    spd = [r["speedup"] for r in runs]
+    assert red[0] < red[1] < red[2]
+    assert spd[0] < spd[1] < spd[2], spd
+    for r in runs:
+        c = np.asarray(r["cdf"])
+        assert len(c) == 1000 and np.all(np.diff(c) >= 0) and abs(c[-1] - 1.0) < 1e-12
+        assert np.isfinite(r["mean_rel_err"])

@@ -48,3 +48,28 @@ def test_bf16_rounding():
     assert mlp.bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6
     x = np.random.default_rng(3).normal(size=1000)
     assert np.all(np.abs(mlp.bf16(x) - x) <= np.abs(x) * 2 ** -8)
+
+
+def test_features_by_hand():
+    """The eight features on a hand-built 4-point graph: a path 0-1-2 along x
+    (unit spacing) plus an isolated point 3."""
+    from oracle import mlp
+
+    pos = np.array([[1.0, 0, 0], [2.0, 0, 0], [3.0, 0, 0], [0.0, 0, 5.0]])
+    vel = np.array([[0.0, 0, 0], [3.0, 4.0, 0], [0.0, 0, 0], [1.0, 1, 1]])
+    off = np.array([0, 1, 3, 4, 4])
+    nbr = np.array([1, 0, 2, 1], np.int32)
+    rho = np.array([1.0, np.e, np.e ** 3, 2.0])
+    T = np.array([100.0, 200.0, 300.0, 400.0])
+    dvw = np.array([0.5, 1.0, 2.0, 4.0])
+    chi0 = np.array([2.0, 3.0, 4.0, 5.0])
+    X = mlp.features(pos, vel, off, nbr, rho, T, dvw, chi0)
+    # point 0: one neighbour (1) at distance 1, log rho contrast 1, |dv| = 5 over width 0.5
+    assert X[0] == pytest.approx([0.0, 1.0, 10.0, np.log(100.0), 0.0, 1.0, 0.0, np.log(2.0)])
+    # point 1: neighbours 0 and 2 at distance 1, contrasts 1 and 2, |dv| = 5 to both over width 1
+    assert X[1] == pytest.approx([1.0, 2.0, 5.0, np.log(200.0), 0.0, 2.0, np.log(2.0), np.log(3.0)])
+    # point 2: neighbour 1, contrast 2, |dv| = 5 over width 2
+    assert X[2] == pytest.approx([3.0, 2.0, 2.5, np.log(300.0), 0.0, 1.0, np.log(3.0), np.log(4.0)])
+    # point 3: no neighbours (mean distance 0, so log L and log(chi0 L) take the 1e-30 floor)
+    assert X[3] == pytest.approx([np.log(2.0), 0.0, 0.0, np.log(400.0), np.log(1e-30), 0.0, np.log(5.0),
+                                  np.log(1e-30)])
