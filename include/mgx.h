@@ -261,7 +261,11 @@ enum {
  * without a long tail.  Launch parameters come from the context's tuning
  * (mgx_set_tuning / mgx_autotune).
  *   models  [n_models] distinct model handles (1..65535), lines and rays set
- *   J_out   [n_models] device pointers, J_out[k] of size [n_k][n_lines_k*n_freq_k]
+ *   J_out   [n_models] outputs, J_out[k] of size [n_k][n_lines_k*n_freq_k]: device
+ *           memory of the context's device, or host memory (pageable or pinned),
+ *           which the call stages in device memory that the plan owns and
+ *           copies back (one copy per model, on the context's stream) after
+ *           each step; a graph replay then copies too
  *   flags   MGX_BATCH_RAYS: the step starts by rebuilding the ray sets;
  *           MGX_BATCH_GRAPH: the first call plans the layout (one host
  *           synchronisation), runs the step and captures it as a CUDA graph;

@@ -231,7 +231,8 @@ def mgx_solve_J_noalloc(ctx, model, params: SolveParams, J_out) -> None:
 
 
 def mgx_solve_J_batch(ctx, models, params: SolveParams, J_outs, flags: int = 0) -> None:
-    """Batched solve of several models into CUDA float64 tensors J_outs[k] (see include/mgx.h)."""
+    """Batched solve of several models into contiguous float64 tensors J_outs[k], on the context's
+    device or in host memory (see include/mgx.h)."""
     ids = np.ascontiguousarray(models, np.int32)
     ptrs = (C.c_void_p * len(J_outs))(*[t.data_ptr() for t in J_outs])
     _check(ctx, load_library().mgx_solve_J_batch(ctx, _ptr(ids), len(ids), C.byref(params), ptrs, int(flags)))

@@ -10,16 +10,19 @@
 //
 // GB300 executes double precision at a small fraction of its single-precision
 // rate, so each step first screens the neighbours in single precision: each
-// CSR edge carries its neighbour's position rounded to float, the offset
-// x_n - x_o, Z and q are formed in float, and each gets a rigorous bound on its
-// distance from the double-precision value (derived from the unit roundoff
-// u = 2^-24 and the positions' own rounding; see step_screen).
-// A neighbour is surely (not) forward when Z32 - Z_c clears eZ plus the
-// rounding of Z_c; the step is decided in single precision when one surely
-// forward neighbour's interval [q32 - eq, q32 + eq] lies strictly below the
-// intervals of every other candidate.  Otherwise (near-ties, exact ties of
-// lattice meshes, ambiguous forward tests) the step is redone exactly in
-// double precision.  The winner's Z is always computed exactly in double.
+// CSR edge carries its neighbour's position rounded to float.  The screen
+// works relative to the current point c rather than to the origin: with
+// Delta = x_n - x_c, the increment Z_n - Z_c = Delta.d and the lateral offset
+// e_n = e_c + Delta - (Delta.d) d (q_n = |e_n|^2) involve only differences of
+// neighbouring points, so their rounding scales with the spacing of the mesh
+// and the positions' own rounding, not with the distance from the origin.  The
+// walk carries e_c in float with a rigorous bound on its error; each quantity
+// gets such a bound (from the unit roundoff u = 2^-24; see step_screen).
+// A neighbour is surely (not) forward when Delta.d clears its bound; the step
+// is decided in single precision when one surely forward neighbour's interval
+// [q32 - eq, q32 + eq] lies strictly below the intervals of every other
+// candidate.  Otherwise (near-ties, exact ties of lattice meshes, ambiguous
+// forward tests) the step is redone exactly in double precision.
 //
 // An undecided step is decided by the whole warp at once (step_exact_warp):
 // every neighbour of the current point is evaluated in double precision, one
@@ -27,10 +30,10 @@
 // one another only at these steps, and for a few tens of cycles rather than a
 // serial double-precision pass over the neighbour list.
 //
-// The fast path carries the winner's single-precision Z and its error bound
-// into the next step's forward test, so it executes no double-precision
-// operation at all; the exact Z is formed only on undecided steps (and for
-// the inspection output of mgx_trace).
+// The fast path carries the winner's lateral offset and position into the
+// next step, so it executes no double-precision operation at all; exact values
+// are formed only on undecided steps, when a tail walk resumes (its lateral
+// offset), and for the inspection output of mgx_trace.
 //
 // The walk serves three layouts of the traced lists (the solver re-forms each
 // point's exact Z from its position, so only point ids are stored):
@@ -65,40 +68,71 @@ __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t c, double xo
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2));
 }
 
-struct FStep {
-    int32_t next;  // -1: the half-ray ends; -2: undecided
-    float z32;     // single-precision Z of next; when undecided, the smallest upper bound of q
-    float ez;      // bound on |z32 - Z(next)|, Z the double-precision value
+// State of one lane's current walk.  It holds the direction in float only
+// (the rounded table entry, negated for a backward half, which equals the
+// rounded negation); the double direction is read from the table on the rare
+// steps that need it, so setting up a walk executes no double-precision
+// operation.
+struct Walk {
+    int64_t h, w;             // half-ray, write base of its entries
+    float4 hc;                // position of the current point (float; w = its |x|_1)
+    float f0, f1, f2;         // direction (float)
+    float ecx, ecy, ecz, eec; // lateral offset of the current point from the ray (float) and its bound
+    int32_t o, c, k, expect;
+    int32_t pix;           // table index of the pair direction
+    bool back;             // backward half (direction negated)
 };
+
 
 // Single-precision screen of one step over the neighbour records of c (the
 // float position of each neighbour stored next to its id, read sequentially).
-// zc32 approximates the double Z of the current point within ezc; Xo is
-// |x_o|_1 in float.  With hi-only positions the bounds carry the rounding of
-// both positions: eZ = 3u (X_n + X_o) + 12u S + g0, eq = 32u (X_n + X_o) S +
-// 128u S^2 + 32 g0 S (about 2.5 to 3 times the worst case).  Returns
-// next = -2 when it cannot decide.
-__device__ __forceinline__ FStep step_screen(const DevMesh &m, int32_t c, float4 oh, float Xo, float f0, float f1,
-                                             float f2, float zc32, float ezc) {
-    const float zcm = ezc + 4.0f * kU * fabsf(zc32);
-    int32_t best = -1, lo1_id = -1;
-    float hib = INFINITY, lo1 = INFINITY, lo2 = INFINITY, zb = 0.0f, ezb = 0.0f;
+// The walk holds c's float position hc (w = |hc|_1), (ecx, ecy, ecz)
+// approximating c's lateral offset e_c = (x_c - x_o) - Z_c d componentwise
+// within eec, and the direction f rounded to float.  Bounds, with a_i = |hn_i| + |hc_i|,
+// S = |Delta32|_1, X = |hn|_1 + |hc|_1 <= 2 Xc + 1.01 S (Xc = |hc|_1) and
+// E1 = |e32|_1 (positions round to float within u |x|, d to f within u |d|):
+//   |Delta32_i - Delta_i| <= u (|Delta32_i| + a_i) (1 + 2u)
+//   |dZ32 - dZ| <= 5.01u S + 1.01u X <= 6.04u S + 2.02u Xc       (used: 8u S + 4u Xc)
+//   |e32_i - e_i| <= eec + 1.01 |dZ32 - dZ| + 1.01u (4.1 S + X + E1)
+//                 <= eec + u (13.4 S + 6.2 Xc + 1.01 E1)   (used: de = eec + u (15 S + 8 Xc + 2 E1))
+//   |q32 - q| <= 2 E1 de + 3 de^2 + 3.01u q32     (used: 2.02 E1 de + 3.03 de^2 + 6u q32,
+//                                                  the margin covering the rounding of the bounds)
+// The definition's own double rounding adds at most g0 to a Z difference
+// (16 u64 max|x|_1 against g0 = 32 u^2 max|x|_1) and g0 (E1 + de) + g0^2 to q
+// (16.2 u64 |x_n - x_o|_1 |e|_1 + 3.01 u64 q + 197 u64^2 |x_n - x_o|_1^2).
+// Returns the next point (-1: the half-ray ends; -2: undecided); when it
+// decides a next point it moves the walk's position and lateral offset to it.
+__device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
+    const int32_t c = wk.c;
+    const float4 hc = wk.hc;
+    const float f0 = wk.f0, f1 = wk.f1, f2 = wk.f2, ecx = wk.ecx, ecy = wk.ecy, ecz = wk.ecz, eec = wk.eec;
+    int32_t best = -1, lo1_id = -1, be = 0;
+    float hib = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+    const float g02 = m.g0 * m.g0;
     const int32_t e1 = m.off[c + 1];
+    // the screen of neighbour record e (the same arithmetic for the loop and the winner)
+    const float bz = fmaf(4.0f * kU, hc.w, m.g0), be0 = fmaf(8.0f * kU, hc.w, eec);
+    auto screen = [&](const float4 &rec, float &dZ, float &edZ, float &ex, float &ey, float &ez, float &S) {
+        const float dx = rec.x - hc.x, dy = rec.y - hc.y, dz = rec.z - hc.z;
+        S = fabsf(dx) + fabsf(dy) + fabsf(dz);
+        dZ = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
+        edZ = fmaf(8.0f * kU, S, bz);
+        ex = ecx + fmaf(-dZ, f0, dx);
+        ey = ecy + fmaf(-dZ, f1, dy);
+        ez = ecz + fmaf(-dZ, f2, dz);
+    };
+    auto bound = [&](float S, float E1) { return fmaf(15.0f * kU, S, fmaf(2.0f * kU, E1, be0)); };
     for (int32_t e = m.off[c]; e < e1; ++e) {
         const float4 rec = __ldg(m.nrec + e);
-        const int32_t nb = __float_as_int(rec.w);
-        const float dx = rec.x - oh.x, dy = rec.y - oh.y, dz = rec.z - oh.z;
-        const float S = fabsf(dx) + fabsf(dy) + fabsf(dz);
-        const float XS = fabsf(rec.x) + fabsf(rec.y) + fabsf(rec.z) + Xo;
-        const float z32 = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
-        const float ez = fmaf(3.0f * kU, XS, fmaf(12.0f * kU, S, m.g0));
-        const float diff = z32 - zc32;
-        const float E = ez + zcm + 4.0f * kU * fabsf(diff);
-        if (diff < -E) continue;  // surely not forward
-        const float ex = fmaf(-z32, f0, dx), ey = fmaf(-z32, f1, dy), ez2 = fmaf(-z32, f2, dz);
-        const float q = fmaf(ez2, ez2, fmaf(ey, ey, ex * ex));
-        const float eq = fmaf(fmaf(32.0f * kU, XS, 128.0f * kU * S), S, fmaf(32.0f * m.g0, S, 1e-37f));
+        float dZ, edZ, ex, ey, ez, S;
+        screen(rec, dZ, edZ, ex, ey, ez, S);
+        if (dZ < -edZ) continue;  // surely not forward
+        const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
+        const float q = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
+        const float de = bound(S, E1);
+        const float eq = fmaf(fmaf(2.02f, E1, 3.03f * de), de, fmaf(6.0f * kU, q, fmaf(m.g0, E1 + de, g02)));
         const float lo = q - eq, hi = q + eq;
+        const int32_t nb = __float_as_int(rec.w);
         if (lo < lo1) {
             lo2 = lo1;
             lo1 = lo;
@@ -106,38 +140,43 @@ __device__ __forceinline__ FStep step_screen(const DevMesh &m, int32_t c, float4
         } else if (lo < lo2) {
             lo2 = lo;
         }
-        if (diff > E && hi < hib) {  // surely forward
+        if (dZ > edZ && hi < hib) {  // surely forward
             hib = hi;
             best = nb;
-            zb = z32;
-            ezb = ez;
+            be = e;
         }
     }
-    if (lo1_id < 0) return FStep{-1, 0.0f, 0.0f};  // no neighbour can be forward
-    if (best >= 0 && best == lo1_id && hib < lo2) return FStep{best, zb, ezb};
-    return FStep{-2, hib, 0.0f};
+    if (lo1_id < 0) return -1;  // no neighbour can be forward: the half-ray ends
+    if (best < 0 || best != lo1_id || !(hib < lo2)) return -2;
+    // the winner's offset and bound, formed again from its record as in the loop
+    const float4 rec = __ldg(m.nrec + be);
+    float dZ, edZ, ex, ey, ez, S;
+    screen(rec, dZ, edZ, ex, ey, ez, S);
+    const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
+    wk.eec = bound(S, E1) * (1.0f + 8.0f * kU);  // with the rounding of the bound itself
+    wk.hc = make_float4(rec.x, rec.y, rec.z, fabsf(rec.x) + fabsf(rec.y) + fabsf(rec.z));
+    wk.ecx = ex;
+    wk.ecy = ey;
+    wk.ecz = ez;
+    return best;
 }
-
-// State of one lane's current walk.  It holds the direction in float only
-// (the rounded table entry, negated for a backward half, which equals the
-// rounded negation); the double direction is read from the table on the rare
-// steps that need it, so setting up a walk executes no double-precision
-// operation.
-struct Walk {
-    int64_t h, w;          // half-ray, write base of its entries
-    float4 oh;             // origin position (float)
-    float f0, f1, f2, Xo;  // direction (float), |x_o|_1
-    float zc32, ezc;       // Z of the current point (float) and its bound
-    int32_t o, c, k, expect;
-    int32_t pix;           // table index of the pair direction
-    bool back;             // backward half (direction negated)
-};
 
 __device__ __forceinline__ void walk_dir(const DevRays &R, const Walk &wk, double &d0, double &d1, double &d2) {
     const double *r = R.dir + 3 * int64_t(wk.pix);
     d0 = wk.back ? -r[0] : r[0];
     d1 = wk.back ? -r[1] : r[1];
     d2 = wk.back ? -r[2] : r[2];
+}
+
+// The lateral offset of the walk's current point c (exact Z given) in
+// double, rounded to float, with its error bound (the float rounding plus g0).
+__device__ __forceinline__ void lateral(const DevMesh &m, Walk &wk, double Z, double d0, double d1, double d2,
+                                        double xo, double yo, double zo) {
+    const int32_t c = wk.c;
+    wk.ecx = __double2float_rn(__dsub_rn(__dsub_rn(m.x[c], xo), __dmul_rn(Z, d0)));
+    wk.ecy = __double2float_rn(__dsub_rn(__dsub_rn(m.y[c], yo), __dmul_rn(Z, d1)));
+    wk.ecz = __double2float_rn(__dsub_rn(__dsub_rn(m.z[c], zo), __dmul_rn(Z, d2)));
+    wk.eec = fmaf(1.01f * kU, fmaxf(fabsf(wk.ecx), fmaxf(fabsf(wk.ecy), fabsf(wk.ecz))), m.g0);
 }
 
 // Set up the walk of half-ray h; false when h needs no walk (MODE 4: no
@@ -162,8 +201,6 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
     wk.f0 = wk.back ? -df.x : df.x;
     wk.f1 = wk.back ? -df.y : df.y;
     wk.f2 = wk.back ? -df.z : df.z;
-    wk.oh = m.phi[wk.o];
-    wk.Xo = fabsf(wk.oh.x) + fabsf(wk.oh.y) + fabsf(wk.oh.z);
     wk.w = 0;
     wk.expect = 0;
     if (MODE == 1 || MODE == 2) {
@@ -185,19 +222,24 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
     }
     wk.c = wk.o;
     wk.k = 0;
-    wk.zc32 = 0.0f;  // Z of the origin is exactly 0
-    wk.ezc = 0.0f;
+    wk.ecx = wk.ecy = wk.ecz = wk.eec = 0.0f;  // the origin lies on the ray
     if (MODE == 4) {  // resume after the row's last entry
-        const int4 rs = resume[h];
-        wk.c = rs.x;
-        wk.zc32 = __int_as_float(rs.y);
-        wk.ezc = __int_as_float(rs.z);
+        wk.c = resume[h].x;
         wk.k = pad;
         if (wk.c < 0 || wk.c >= m.n) {
             dev_fail(status, kDevTraceMismatch);
             return false;
         }
+        // the lateral offset of the current point, formed in double: each
+        // component within 8.1 u64 |x_c - x_o|_1 (<= g0) of the exact value
+        double d0, d1, d2;
+        walk_dir(R, wk, d0, d1, d2);
+        const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
+        const double Z = exact_Z(m, wk.c, xo, yo, zo, d0, d1, d2);
+        lateral(m, wk, Z, d0, d1, d2, xo, yo, zo);
     }
+    wk.hc = m.phi[wk.c];
+    wk.hc.w = fabsf(wk.hc.x) + fabsf(wk.hc.y) + fabsf(wk.hc.z);
     return true;
 }
 
@@ -264,7 +306,7 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         unsigned long long *__restrict__ counters, int32_t pad, int64_t *__restrict__ excess,
         int4 *__restrict__ resume) {
     const int64_t T = int64_t(gridDim.x) * blockDim.x;
-    unsigned long long n_steps = 0, n_exact = 0;
+    unsigned n_steps = 0, n_exact = 0;
     Walk wk;
     int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     bool live = false;
@@ -274,14 +316,14 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
     // every lane stays in the loop until the whole warp is done, so that undecided
     // steps can be resolved by the warp together
     while (__any_sync(0xffffffffu, live)) {
-        FStep s{-1, 0.0f, 0.0f};
+        int32_t next = -1;
         if (live) {
-            s = step_screen(m, wk.c, wk.oh, wk.Xo, wk.f0, wk.f1, wk.f2, wk.zc32, wk.ezc);
+            next = step_screen(m, wk);
             ++n_steps;
         }
         double zexact = 0.0;
         bool have_exact = false;
-        unsigned todo = __ballot_sync(0xffffffffu, live && s.next == -2);
+        unsigned todo = __ballot_sync(0xffffffffu, live && next == -2);
         while (todo) {  // undecided in single precision: decided exactly, one lane's step at a time
             const int L = __ffs(todo) - 1;
             todo &= todo - 1;
@@ -294,37 +336,43 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
             d2 = __shfl_sync(0xffffffffu, d2, L);
             const Step x = step_exact_warp(m, c, o, d0, d1, d2, lane);
             if (lane == L) {
-                s.next = x.next;
+                next = x.next;
                 zexact = x.Z;
                 ++n_exact;
                 have_exact = true;
-                s.z32 = __double2float_rn(x.Z);
-                s.ez = 2.0f * kU * fabsf(s.z32);
+                if (x.next >= 0) {
+                    // the next point's position and lateral offset (exact Z known)
+                    wk.c = x.next;
+                    lateral(m, wk, x.Z, d0, d1, d2, m.x[o], m.y[o], m.z[o]);
+                    wk.c = c;
+                    wk.hc = m.phi[x.next];
+                    wk.hc.w = fabsf(wk.hc.x) + fabsf(wk.hc.y) + fabsf(wk.hc.z);
+                }
             }
         }
         if (!live) continue;
-        bool ended = s.next < 0, failed = false;
+        bool ended = next < 0, failed = false;
         if (!ended) {
             const int32_t k = wk.k;
             if (MODE == 3) {
-                if (k < pad) idx_out[wk.w + k] = s.next;
+                if (k < pad) idx_out[wk.w + k] = next;
             } else if (MODE == 4) {
                 if (k >= wk.expect) failed = true;
-                else idx_out[wk.w + k] = s.next;  // k >= pad here
+                else idx_out[wk.w + k] = next;  // k >= pad here
             } else if (MODE > 0) {
                 if (k >= wk.expect) {
                     failed = true;
                 } else {
-                    idx_out[wk.w + k] = s.next;
+                    idx_out[wk.w + k] = next;
                     if (MODE == 2) {
                         const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
                         double d0, d1, d2;
                         walk_dir(R, wk, d0, d1, d2);
-                        Z_out[wk.w + k] = have_exact ? zexact : exact_Z(m, s.next, xo, yo, zo, d0, d1, d2);
+                        Z_out[wk.w + k] = have_exact ? zexact : exact_Z(m, next, xo, yo, zo, d0, d1, d2);
                         if (delta_out) {
-                            const double ux = __dsub_rn(m.vx[s.next], m.vx[wk.o]);
-                            const double uy = __dsub_rn(m.vy[s.next], m.vy[wk.o]);
-                            const double uz = __dsub_rn(m.vz[s.next], m.vz[wk.o]);
+                            const double ux = __dsub_rn(m.vx[next], m.vx[wk.o]);
+                            const double uy = __dsub_rn(m.vy[next], m.vy[wk.o]);
+                            const double uz = __dsub_rn(m.vz[next], m.vz[wk.o]);
                             delta_out[wk.w + k] =
                                 __dadd_rn(__dadd_rn(__dmul_rn(ux, d0), __dmul_rn(uy, d1)), __dmul_rn(uz, d2));
                         }
@@ -336,11 +384,8 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
                 ended = true;
             } else {
                 wk.k = k + 1;
-                wk.c = s.next;
-                wk.zc32 = s.z32;
-                wk.ezc = s.ez;
-                if (MODE == 3 && wk.k == pad)
-                    resume[wk.h] = make_int4(wk.c, __float_as_int(wk.zc32), __float_as_int(wk.ezc), 0);
+                wk.c = next;
+                if (MODE == 3 && wk.k == pad) resume[wk.h] = make_int4(wk.c, 0, 0, 0);
                 if (wk.k > m.n) {  // Z increases strictly, so this cannot happen
                     dev_fail(status, kDevTraceGuard);
                     ended = true;
@@ -363,8 +408,8 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         }
     }
     if (counters) {
-        atomicAdd(counters + 2, n_steps);
-        atomicAdd(counters + 3, n_exact);
+        atomicAdd(counters + 2, (unsigned long long)n_steps);
+        atomicAdd(counters + 3, (unsigned long long)n_exact);
     }
 }
 

@@ -61,6 +61,8 @@ struct BatchPlan {
     bool valid = false;
     std::vector<int32_t> models;
     std::vector<double *> J;
+    std::vector<double *> Jdev;   // device staging of an output in host memory (null: J[k] is device memory)
+    std::vector<size_t> Jbytes;
     mgx_solve_params p{};
     int32_t flags = 0;
     int64_t total_half = 0, n_origins = 0, n_work = 0, tail_cap = 0, total_points = 0;
@@ -411,6 +413,9 @@ void free_plan(mgx_ctx *ctx, BatchPlan &pl) {
     if (pl.graph) cudaGraphDestroy(pl.graph);
     pl.exec = nullptr;
     pl.graph = nullptr;
+    for (double *&q : pl.Jdev) dfree(ctx, q);
+    pl.Jdev.clear();
+    pl.Jbytes.clear();
     dfree(ctx, pl.lens);
     dfree(ctx, pl.excess);
     dfree(ctx, pl.offs);
@@ -493,6 +498,14 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
     }
     CK(cudaGetLastError());
     return MGX_OK;
+}
+
+// Copy the staged outputs of a batched step to their host buffers (one copy
+// per model, after the step on the same stream) and wait for the stream.
+mgx_status finish_batch_step(mgx_ctx *ctx, BatchPlan &pl) {
+    for (size_t k = 0; k < pl.Jdev.size(); ++k)
+        if (pl.Jdev[k]) CK(cudaMemcpyAsync(pl.J[k], pl.Jdev[k], pl.Jbytes[k], cudaMemcpyDeviceToHost, ctx->stream));
+    return sync_status(ctx);
 }
 
 // Row width of the padded layout: the narrowest power of two that leaves at
@@ -1158,9 +1171,11 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         for (int32_t j = 0; j < k; ++j)
             if (models[j] == models[k]) return fail(ctx, MGX_EINVAL, "solve_J_batch: model %d listed twice", models[k]);
         cudaPointerAttributes attr;
-        if (!J_out[k] || cudaPointerGetAttributes(&attr, J_out[k]) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        if (!J_out[k] || cudaPointerGetAttributes(&attr, J_out[k]) != cudaSuccess ||
+            (attr.type == cudaMemoryTypeDevice && attr.device != ctx->device)) {
             cudaGetLastError();
-            return fail(ctx, MGX_EINVAL, "solve_J_batch: J_out[%d] must be device memory", k);
+            return fail(ctx, MGX_EINVAL, "solve_J_batch: J_out[%d] must be host memory or device memory of device %d",
+                        k, ctx->device);
         }
         ms.push_back(m);
     }
@@ -1170,7 +1185,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     if (graph && plan_matches(pl, models, n_models, p, J_out, flags, ctx->tune) && pl.exec) {
         CK(cudaGraphLaunch(pl.exec, ctx->stream));
         ctx->launches[MGX_K_SOLVE] += 1;
-        const mgx_status s = sync_status(ctx);
+        const mgx_status s = finish_batch_step(ctx, pl);
         if (s != MGX_OK) free_plan(ctx, pl);
         return s;
     }
@@ -1203,6 +1218,17 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         geo[size_t(k)].work_base = pl.n_work;
         pl.n_work += int64_t(m.n) * geo[size_t(k)].n_tiles;
         if (geo[size_t(k)].n_tiles > 65535) return fail(ctx, MGX_ERANGE, "solve_J_batch: too many frequency tiles");
+    }
+    // outputs in host memory are staged on the device and copied back after each step
+    pl.Jdev.assign(size_t(n_models), nullptr);
+    pl.Jbytes.assign(size_t(n_models), 0);
+    for (int32_t k = 0; k < n_models; ++k) {
+        cudaPointerAttributes attr;
+        CK(cudaPointerGetAttributes(&attr, J_out[k]));
+        if (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged) continue;
+        const Model &m = *ms[size_t(k)];
+        pl.Jbytes[size_t(k)] = size_t(m.n) * size_t(m.L) * size_t(m.F) * sizeof(double);
+        CK(dalloc(ctx, &pl.Jdev[size_t(k)], size_t(m.n) * size_t(m.L) * size_t(m.F)));
     }
     CK(dalloc(ctx, &pl.lens, size_t(pl.total_half)));
     CK(dalloc(ctx, &pl.excess, size_t(pl.total_half)));
@@ -1275,7 +1301,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         a.pad = pl.pad;
         a.lens = pl.lens + geo[size_t(k)].half_base;
         a.tail = pl.tail;
-        a.J = J_out[k];
+        a.J = pl.Jdev[size_t(k)] ? pl.Jdev[size_t(k)] : J_out[k];
         a.status = ctx->d_status;
         a.counters = ctx->prof ? ctx->d_counters : nullptr;
         fill_pair_weights(a);
@@ -1288,7 +1314,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         free_plan(ctx, pl);
         return s;
     }
-    s = sync_status(ctx);
+    s = finish_batch_step(ctx, pl);
     if (s != MGX_OK) {
         free_plan(ctx, pl);
         return s;

@@ -72,8 +72,32 @@ def test_batch_rejects_bad_arguments(setup):
     out = torch.empty((900, 50), dtype=torch.float64, device="cuda")
     with pytest.raises(mgx.MgxError):  # a model twice
         mgx.mgx_solve_J_batch(ctx.ptr, [mids[0], mids[0]], mgx.solve_params(), [out, out])
-    with pytest.raises(mgx.MgxError):  # host output
-        mgx.mgx_solve_J_batch(ctx.ptr, [mids[0]], mgx.solve_params(), [torch.empty((900, 50), dtype=torch.float64)])
+
+
+def test_batch_host_outputs(setup):
+    """Outputs in host memory (pageable and pinned, mixed with device memory)
+    receive the same J as device outputs, in the eager step and in graph replays."""
+    import torch
+
+    import paper_2011_14998_gb300 as mgx
+
+    ctx, models, mids = setup
+    ref = [o.cpu().numpy() for o in ctx.solve_J_batch(mids, precision=1)]
+    outs = []
+    for k, o in enumerate(ref):
+        if k % 3 == 0:
+            outs.append(torch.full(o.shape, -1.0, dtype=torch.float64))
+        elif k % 3 == 1:
+            outs.append(torch.full(o.shape, -1.0, dtype=torch.float64).pin_memory())
+        else:
+            outs.append(torch.full(o.shape, -1.0, dtype=torch.float64, device="cuda"))
+    params = mgx.solve_params(precision=mgx.MGX_FP32)
+    for flags in (0, mgx.MGX_BATCH_GRAPH, mgx.MGX_BATCH_GRAPH):  # eager, plan + capture, replay
+        for o in outs:
+            o.fill_(-1.0)
+        mgx.mgx_solve_J_batch(ctx.ptr, mids, params, outs, flags)
+        for o, r in zip(outs, ref):
+            assert np.array_equal(o.cpu().numpy(), r)
 
 
 def test_tuning_changes_speed_not_results(setup):
