@@ -284,7 +284,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
  * the compilers' fused multiply-adds differ), never beyond that. */
 typedef struct {
     int32_t bins_per_lane;     /* single-precision frequency bins per lane: 0 automatic (2 above 32 bins), 1, 2 */
-    int32_t trace_ctas_per_sm; /* resident tracer CTAs of 128 threads per SM: 0 = 8, else 1..32 (capped at
+    int32_t trace_ctas_per_sm; /* resident tracer CTAs of 128 threads per SM: 0 = 7, else 1..32 (capped at
                                   what fits) */
     int32_t tail_permille;     /* row width of the traced lists: the narrowest power of two leaving at most this
                                   share of the points (per mille) to the overflow pass; 0 = 20, else 1..1000 */

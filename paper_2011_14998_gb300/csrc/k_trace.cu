@@ -68,19 +68,18 @@ __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t c, double xo
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, d0), __dmul_rn(dy, d1)), __dmul_rn(dz, d2));
 }
 
-// State of one lane's current walk.  It holds the direction in float only
-// (the rounded table entry, negated for a backward half, which equals the
-// rounded negation); the double direction is read from the table on the rare
-// steps that need it, so setting up a walk executes no double-precision
-// operation.
+// State of one lane's current walk (the half-ray index h is the walking
+// loop's own variable).  It holds the direction in float only (the rounded
+// table entry, negated for a backward half, which equals the rounded
+// negation); the origin and the double direction are formed again from h on
+// the rare steps that need them, so the walk keeps few registers and setting
+// it up executes no double-precision operation.
 struct Walk {
-    int64_t h, w;             // half-ray, write base of its entries
+    int64_t w;                // write base of the entries (not kept by the padded pass: h * pad)
     float4 hc;                // position of the current point (float; w = its |x|_1)
     float f0, f1, f2;         // direction (float)
     float ecx, ecy, ecz, eec; // lateral offset of the current point from the ray (float) and its bound
-    int32_t o, c, k, expect;
-    int32_t pix;           // table index of the pair direction
-    bool back;             // backward half (direction negated)
+    int32_t c, k, expect;
 };
 
 
@@ -161,11 +160,25 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     return best;
 }
 
-__device__ __forceinline__ void walk_dir(const DevRays &R, const Walk &wk, double &d0, double &d1, double &d2) {
-    const double *r = R.dir + 3 * int64_t(wk.pix);
-    d0 = wk.back ? -r[0] : r[0];
-    d1 = wk.back ? -r[1] : r[1];
-    d2 = wk.back ? -r[2] : r[2];
+// Origin of half-ray h (two halves per pair, npairs pairs per origin).
+__device__ __forceinline__ int32_t walk_origin(const DevRays &R, int32_t o_begin, int64_t h) {
+    return o_begin + int32_t((h >> 1) / R.npairs);
+}
+
+// Table index of half-ray h's pair direction.
+__device__ __forceinline__ int32_t walk_pix(const DevRays &R, int32_t o, int64_t h) {
+    const uint32_t ray = R.rays[int64_t(o) * R.npairs + ((h >> 1) % R.npairs)];
+    return int32_t(level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
+}
+
+// The double direction of half-ray h (a backward half, h even, negated).
+__device__ __forceinline__ void walk_dir(const DevRays &R, int32_t o_begin, int64_t h, double &d0, double &d1,
+                                         double &d2) {
+    const double *r = R.dir + 3 * int64_t(walk_pix(R, walk_origin(R, o_begin, h), h));
+    const bool back = (h & 1) == 0;
+    d0 = back ? -r[0] : r[0];
+    d1 = back ? -r[1] : r[1];
+    d2 = back ? -r[2] : r[2];
 }
 
 // The lateral offset of the walk's current point c (exact Z given) in
@@ -192,15 +205,12 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
         if (expect_len <= pad) return false;
     }
     const int64_t pr = h >> 1;
-    wk.h = h;
-    wk.o = o_begin + int32_t(pr / R.npairs);
-    const uint32_t ray = R.rays[int64_t(wk.o) * R.npairs + (pr % R.npairs)];
-    wk.pix = int32_t(level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
-    wk.back = (h & 1) == 0;  // backward half: exact negation of the pair direction
-    const float4 df = R.dirf[wk.pix];
-    wk.f0 = wk.back ? -df.x : df.x;
-    wk.f1 = wk.back ? -df.y : df.y;
-    wk.f2 = wk.back ? -df.z : df.z;
+    const int32_t o = o_begin + int32_t(pr / R.npairs);
+    const float4 df = R.dirf[walk_pix(R, o, h)];
+    const bool back = (h & 1) == 0;  // backward half: exact negation of the pair direction
+    wk.f0 = back ? -df.x : df.x;
+    wk.f1 = back ? -df.y : df.y;
+    wk.f2 = back ? -df.z : df.z;
     wk.w = 0;
     wk.expect = 0;
     if (MODE == 1 || MODE == 2) {
@@ -210,8 +220,6 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
             dev_fail(status, kDevArenaOverflow);
             return false;
         }
-    } else if (MODE == 3) {
-        wk.w = h * int64_t(pad);
     } else if (MODE == 4) {
         wk.w = offs[h] - base - pad;  // entry k >= pad goes to w + k
         wk.expect = int32_t(expect_len);
@@ -220,7 +228,7 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
             return false;
         }
     }
-    wk.c = wk.o;
+    wk.c = o;
     wk.k = 0;
     wk.ecx = wk.ecy = wk.ecz = wk.eec = 0.0f;  // the origin lies on the ray
     if (MODE == 4) {  // resume after the row's last entry
@@ -233,8 +241,8 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
         // the lateral offset of the current point, formed in double: each
         // component within 8.1 u64 |x_c - x_o|_1 (<= g0) of the exact value
         double d0, d1, d2;
-        walk_dir(R, wk, d0, d1, d2);
-        const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
+        walk_dir(R, o_begin, h, d0, d1, d2);
+        const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
         const double Z = exact_Z(m, wk.c, xo, yo, zo, d0, d1, d2);
         lateral(m, wk, Z, d0, d1, d2, xo, yo, zo);
     }
@@ -299,7 +307,7 @@ __device__ Step step_exact_warp(const DevMesh &m, int32_t c, int32_t o, double d
 // sets up its next half-ray inside the iteration, so the lanes of a warp stay
 // busy although the half-rays they trace differ widely in length.
 template <int MODE>
-__global__ void __launch_bounds__(128, 8)
+__global__ void __launch_bounds__(128, 7)
 k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restrict__ lens,
         const int64_t *__restrict__ offs, int64_t base, int64_t cap, int32_t *__restrict__ idx_out,
         double *__restrict__ Z_out, double *__restrict__ delta_out, int *status,
@@ -308,10 +316,11 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
     const int64_t T = int64_t(gridDim.x) * blockDim.x;
     unsigned n_steps = 0, n_exact = 0;
     Walk wk;
+    // h: the lane's current half-ray while live
     int64_t h = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     bool live = false;
-    for (; h < n_half && !live; h += T) live = begin_walk<MODE>(m, R, o_begin, h, lens, offs, base, cap, pad, resume,
-                                                                status, wk);
+    for (; h < n_half; h += T)
+        if ((live = begin_walk<MODE>(m, R, o_begin, h, lens, offs, base, cap, pad, resume, status, wk))) break;
     const int lane = threadIdx.x & 31;
     // every lane stays in the loop until the whole warp is done, so that undecided
     // steps can be resolved by the warp together
@@ -328,9 +337,10 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
             const int L = __ffs(todo) - 1;
             todo &= todo - 1;
             const int32_t c = __shfl_sync(0xffffffffu, wk.c, L);
-            const int32_t o = __shfl_sync(0xffffffffu, wk.o, L);
+            const int64_t hL = __shfl_sync(0xffffffffu, h, L);
+            const int32_t o = walk_origin(R, o_begin, hL);
             double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-            if (lane == L) walk_dir(R, wk, d0, d1, d2);
+            if (lane == L) walk_dir(R, o_begin, h, d0, d1, d2);
             d0 = __shfl_sync(0xffffffffu, d0, L);
             d1 = __shfl_sync(0xffffffffu, d1, L);
             d2 = __shfl_sync(0xffffffffu, d2, L);
@@ -355,7 +365,7 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         if (!ended) {
             const int32_t k = wk.k;
             if (MODE == 3) {
-                if (k < pad) idx_out[wk.w + k] = next;
+                if (k < pad) idx_out[h * int64_t(pad) + k] = next;
             } else if (MODE == 4) {
                 if (k >= wk.expect) failed = true;
                 else idx_out[wk.w + k] = next;  // k >= pad here
@@ -365,14 +375,15 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
                 } else {
                     idx_out[wk.w + k] = next;
                     if (MODE == 2) {
-                        const double xo = m.x[wk.o], yo = m.y[wk.o], zo = m.z[wk.o];
+                        const int32_t o = walk_origin(R, o_begin, h);
+                        const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
                         double d0, d1, d2;
-                        walk_dir(R, wk, d0, d1, d2);
+                        walk_dir(R, o_begin, h, d0, d1, d2);
                         Z_out[wk.w + k] = have_exact ? zexact : exact_Z(m, next, xo, yo, zo, d0, d1, d2);
                         if (delta_out) {
-                            const double ux = __dsub_rn(m.vx[next], m.vx[wk.o]);
-                            const double uy = __dsub_rn(m.vy[next], m.vy[wk.o]);
-                            const double uz = __dsub_rn(m.vz[next], m.vz[wk.o]);
+                            const double ux = __dsub_rn(m.vx[next], m.vx[o]);
+                            const double uy = __dsub_rn(m.vy[next], m.vy[o]);
+                            const double uz = __dsub_rn(m.vz[next], m.vz[o]);
                             delta_out[wk.w + k] =
                                 __dadd_rn(__dadd_rn(__dmul_rn(ux, d0), __dmul_rn(uy, d1)), __dmul_rn(uz, d2));
                         }
@@ -385,7 +396,7 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
             } else {
                 wk.k = k + 1;
                 wk.c = next;
-                if (MODE == 3 && wk.k == pad) resume[wk.h] = make_int4(wk.c, 0, 0, 0);
+                if (MODE == 3 && wk.k == pad) resume[h] = make_int4(wk.c, 0, 0, 0);
                 if (wk.k > m.n) {  // Z increases strictly, so this cannot happen
                     dev_fail(status, kDevTraceGuard);
                     ended = true;
@@ -395,16 +406,16 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         }
         if (ended) {
             if (MODE == 0) {
-                lens[wk.h] = wk.k;
+                lens[h] = wk.k;
             } else if (MODE == 3) {
-                lens[wk.h] = wk.k;
-                excess[wk.h] = wk.k > pad ? wk.k - pad : 0;
+                lens[h] = wk.k;
+                excess[h] = wk.k > pad ? wk.k - pad : 0;
             } else if (!failed && wk.k != wk.expect) {
                 dev_fail(status, kDevTraceMismatch);
             }
             live = false;
-            for (; h < n_half && !live; h += T)
-                live = begin_walk<MODE>(m, R, o_begin, h, lens, offs, base, cap, pad, resume, status, wk);
+            for (h += T; h < n_half; h += T)
+                if ((live = begin_walk<MODE>(m, R, o_begin, h, lens, offs, base, cap, pad, resume, status, wk))) break;
         }
     }
     if (counters) {
@@ -413,16 +424,16 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
     }
 }
 
-// Grid of the strided walk: ctas_per_sm CTAs of 128 threads per SM (8 when
-// not positive), at most as many as can be resident at once (so the whole
+// Grid of the strided walk: ctas_per_sm CTAs of 128 threads per SM (7, the
+// register cap's limit, when not positive), at most as many as can be resident at once (so the whole
 // grid is one wave and every lane's share of half-rays runs concurrently),
 // fewer when there are fewer half-rays.
 template <int MODE>
 unsigned trace_grid(int64_t n_half, int ctas_per_sm = 0) {
-    int dev = 0, sms = 152, fit = 8;
+    int dev = 0, sms = 152, fit = 7;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, k_trace<MODE>, 128, 0) != cudaSuccess || fit < 1) fit = 1;
-    int per = ctas_per_sm > 0 ? ctas_per_sm : 8;
+    int per = ctas_per_sm > 0 ? ctas_per_sm : 7;
     if (per > fit) per = fit;
     const int64_t want = (n_half + 127) / 128;
     const int64_t cap = int64_t(sms) * per;

@@ -1423,11 +1423,11 @@ mgx_status mgx_autotune(mgx_ctx *ctx, const int32_t *models, int32_t n_models, c
     // start from the current tuning with its automatic fields made explicit
     mgx_tuning best = saved;
     if (best.bins_per_lane == 0 && p->precision != MGX_FP64) best.bins_per_lane = solve_bins_per_lane(MGX_FP32, int32_t(max_nb));
-    if (best.trace_ctas_per_sm == 0) best.trace_ctas_per_sm = 8;
+    if (best.trace_ctas_per_sm == 0) best.trace_ctas_per_sm = 7;
     if (best.tail_permille == 0) best.tail_permille = 20;
     double best_ms = 0.0;
     mgx_status s = time_one(best, &best_ms);
-    const int32_t bpl_c[] = {1, 2}, trace_c[] = {4, 6, 8}, tail_c[] = {5, 20, 80}, sched_c[] = {0, 1};
+    const int32_t bpl_c[] = {1, 2}, trace_c[] = {4, 5, 7}, tail_c[] = {5, 20, 80}, sched_c[] = {0, 1};
     for (int dim = 0; dim < 4 && s == MGX_OK; ++dim) {
         if (dim == 0 && p->precision == MGX_FP64) continue;
         const int32_t *cand = dim == 0 ? bpl_c : dim == 1 ? trace_c : dim == 2 ? tail_c : sched_c;
