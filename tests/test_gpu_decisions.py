@@ -55,6 +55,24 @@ def test_approximation_error_bounds(ctx):
         mgx.mgx_eval_approx(ctx.ptr, 2, xd, yd)
 
 
+def test_ex2_flushes_far_wings_to_zero(ctx):
+    """2^x as the solve evaluates it is exactly +0 for every x <= -128 (a
+    subnormal result, flushed): the single-precision solve skips the profile of
+    samples whose every bin has a'^2 >= 128 and takes the continuum alone,
+    which is then the same value bit for bit."""
+    import torch
+
+    import paper_2011_14998_gb300 as mgx
+
+    x = np.concatenate([-np.linspace(128.0, 1000.0, 1 << 20), [-128.0, -np.inf, -3.0e38]]).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.full_like(xd, 1.0)
+    mgx.mgx_eval_approx(ctx.ptr, 0, xd, yd)
+    torch.cuda.synchronize()
+    y = yd.cpu().numpy()
+    assert np.all(y == 0.0) and not np.any(np.signbit(y))
+
+
 def test_eq2_near_ties_take_the_definitions_count(ctx, orc):
     """A dense two-point medium whose opacity puts Eq. 2's ratio within a few
     units of single-precision rounding of an integer on many bins: J of the
