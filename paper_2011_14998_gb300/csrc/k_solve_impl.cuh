@@ -340,6 +340,8 @@ struct Stage {
     int fix[2][32];                         // Eq. 2 counts of a sample whose single-precision decision was
                                             // left open (-1: to redo in double precision; 0: not open)
     R fA[NL][2][32], fB[NL][2][32];         // profile constants of each lane's bins (Bin)
+    float wa[2], wb[2];                     // single precision, one line: A, B of the tile's first and last bin
+    int wing;                               // the far-wing test of the records is on
 };
 
 // Bin i of the lane in the warp's tile (>= NB: beyond the last, inactive).
@@ -365,7 +367,6 @@ struct Lane {
     R cpr[kCR][2][32];
     R cm[32];
     R So[2][32];
-    double js[2][32], jc[2][32];
 };
 
 // Projected distance Z = (x_n - x_o).d exactly as the tracer and its
@@ -628,6 +629,21 @@ __device__ __forceinline__ void gen_sample(Stage<R, NL> &sg, int s_abs, int s_re
             for (int c = 0; c < 2 * NL; ++c) o[6 + c] = fmaf(sg.ce[c][k] - sg.ce[c][pa], t, sg.ce[c][pa]);
         }
         o[1] = Ar<float>::rcp(wv);
+        if constexpr (NL == 1) {
+            // far wing: when every bin's profile argument a = fl(fl(B delta + A) rdv)
+            // has a^2 >= 128, ex2.approx.ftz(-a^2) is exactly 0 and the optics are
+            // the continuum's (bit for bit).  A and B rise with the bin, so over the
+            // tile B delta + A lies in [min(tf, tl) - W, max(tf, tl) + W] with
+            // W = (B_last - B_first) |delta|; |a| >= 12.1 leaves margin for every
+            // rounding.  The record carries the verdict as a negative 1/dv.
+            if (sg.wing) {
+                const float dl = o[0];
+                const float tf = fmaf(sg.wb[0], dl, sg.wa[0]), tl = fmaf(sg.wb[1], dl, sg.wa[1]);
+                const float W = 1.01f * (sg.wb[1] - sg.wb[0]) * fabsf(dl);
+                const float lo = (fminf(tf, tl) - W) * o[1], hi = (fmaxf(tf, tl) + W) * o[1];
+                if (lo >= 12.1f || hi <= -12.1f) o[1] = -o[1];
+            }
+        }
         o[4] = sg.hq[k];
         o[5] = sg.thr[k];
     } else {
@@ -746,8 +762,16 @@ __device__ __forceinline__ bool sample_step(const R (&v)[Stage<R, NL>::kS], int 
                                             const bool (&act)[BPL], Sweep<R, P> (&w)[BPL]) {
     const R dl = v[0], rdv = v[1], hq = v[4], thr = v[5];
     R chi_q[BPL], eta_q[BPL];
+    if (sizeof(R) == 4 && NL == 1 && rdv < R(0)) {  // far wing of every bin: the continuum (as ex2 gives 0)
 #pragma unroll
-    for (int i = 0; i < BPL; ++i) optics<R, NL>(dl, rdv, v[2], v[3], v + 6, f[i], chi_q[i], eta_q[i]);
+        for (int i = 0; i < BPL; ++i) {
+            chi_q[i] = v[2];
+            eta_q[i] = v[3];
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < BPL; ++i) optics<R, NL>(dl, rdv, v[2], v[3], v + 6, f[i], chi_q[i], eta_q[i]);
+    }
     bool split = false;
     R cq = chi_q[0];
     if constexpr (sizeof(R) == 4) {
@@ -1041,7 +1065,7 @@ struct Occ {
     static constexpr int kWarps = sizeof(R) == 8 ? 2 : 4;
     static constexpr int kThreads = 32 * kWarps;
     static constexpr int kMinBlocks =
-        sizeof(R) == 8 ? 1 : sizeof(P) == 8 ? (NL == 1 ? 4 : 2) : (NL == 1 ? 7 : NL <= 4 ? 4 : 3);
+        sizeof(R) == 8 ? 1 : sizeof(P) == 8 ? (NL == 1 ? 4 : 2) : (NL == 1 ? 8 : NL <= 4 ? 4 : 3);
 };
 
 // J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
@@ -1102,8 +1126,18 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
         R chi_o, eta_o;
         optics<R, NL>(R(0), rdvo, __ldg(Pts<R>::chic(Ln) + o), __ldg(Pts<R>::etac(Ln) + o), oce, f, chi_o, eta_o);
         ln.So[i][lane] = eta_o / chi_o;
-        ln.js[i][lane] = 0.0;
-        ln.jc[i][lane] = 0.0;
+    }
+    if constexpr (sizeof(R) == 4 && NL == 1) {
+        // the profile constants of the tile's first and last bin (the far-wing test of gen_sample)
+        __syncwarp();
+        if (lane == 0) {
+            const int32_t jl = (NB - 1 - tile * 32 * BPL) < 32 * BPL - 1 ? NB - 1 - tile * 32 * BPL : 32 * BPL - 1;
+            sg.wa[0] = sg.fA[0][0][0];
+            sg.wb[0] = sg.fB[0][0][0];
+            sg.wa[1] = sg.fA[0][jl / 32][jl % 32];
+            sg.wb[1] = sg.fB[0][jl / 32][jl % 32];
+            sg.wing = L == 1;
+        }
     }
     if constexpr (sizeof(R) == 4) {
         // largest |A|, |B| of each line over the warp's bins (the opacity bound of Eq. 2)
@@ -1122,6 +1156,9 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
     }
 
     const int64_t h0 = int64_t(oc) * Rs.npairs * 2;
+    double js[BPL], jc[BPL];  // each bin's J: Neumaier sum and compensation
+#pragma unroll
+    for (int i = 0; i < BPL; ++i) js[i] = jc[i] = 0.0;
 #pragma unroll 1
     for (int32_t p = 0; p < Rs.npairs; ++p) {
         const uint32_t ray = __ldg(Rs.rays + int64_t(o) * Rs.npairs + p);
@@ -1165,12 +1202,11 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
             const int32_t b = lane_bin<BPL>(sg, i, lane);
             if (a.u_out && b < NB) a.u_out[(int64_t(oc) * Rs.npairs + p) * NB + b] = double(u);
             const double xv = w2 * double(u);
-            double sum = ln.js[i][lane], comp = ln.jc[i][lane];
+            const double sum = js[i];
             const double t = sum + xv;  // Neumaier compensated sum
-            if (fabs(sum) >= fabs(xv)) comp += (sum - t) + xv;
-            else comp += (xv - t) + sum;
-            ln.js[i][lane] = t;
-            ln.jc[i][lane] = comp;
+            if (fabs(sum) >= fabs(xv)) jc[i] += (sum - t) + xv;
+            else jc[i] += (xv - t) + sum;
+            js[i] = t;
         }
         __syncwarp();
     }
@@ -1179,7 +1215,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
     for (int i = 0; i < BPL; ++i) {
         const int32_t b = lane_bin<BPL>(sg, i, lane);
         if (b < NB) {
-            a.J[int64_t(o) * NB + b] = ln.js[i][lane] + ln.jc[i][lane];
+            a.J[int64_t(o) * NB + b] = js[i] + jc[i];
             ++n_act;
         }
     }
