@@ -327,9 +327,10 @@ struct Stage {
     int sk[kCap];                           // slot | (sample index j << 6) of each record
     R d[33], w[33], cc[33], ec[33];         // delta, Doppler width, continuum
     R ce[2 * NL][33];                       // chi0 and eta0 per line
-    R hq[33], thr[33], rnv[33];             // half the sample spacing, Eq. 2 threshold, 1 / nv
-    R de[kF], E[kF], qlo[kF], qhi[kF];      // bound of |delta - delta64|, of |chi - chi64|, Eq. 2 ratio factors
-    double z[33];                           // exact Z
+    R hq[33], thr[33];                      // half the sample spacing, Eq. 2 threshold
+    R E[kF], qlo[kF], qhi[kF];              // bound of |chi - chi64|, Eq. 2 ratio factors
+    R de0;                                  // single precision: bound of |delta - delta64| of the carried point
+    double z[sizeof(R) == 8 ? 33 : 1];      // exact Z (single precision: the carried point's only)
     int id[33], nv[33], so[33];             // point (-1: the origin), velocity samples, their offset
     R Am[NL], Bm[NL];                       // largest |A|, |B| of each line over the warp's bins
     double r[3], xo[3], vo[3];              // pair direction, origin position and velocity (double)
@@ -366,7 +367,6 @@ struct Lane {
     P cpp[2][2][32];                             // backward half: D Fh, dtb/2
     R cpr[kCR][2][32];
     R cm[32];
-    R So[2][32];
 };
 
 // Projected distance Z = (x_n - x_o).d exactly as the tracer and its
@@ -411,17 +411,20 @@ __device__ __noinline__ int redo_velocity_samples(const DevMesh &m, const DevLin
 
 // Eq. 2's n_inter for bin `bin` on the sub-interval between the velocity
 // samples j-1 and j (counted from the farther point a, 0 = a, nv = b) of the
-// interval from point ia (projected distance za) to point ib (zb), -1 being
-// the origin.  The two samples are formed as the definition lays out the pair
+// interval from point ia to point ib, -1 being the origin.  The two samples are formed as the definition lays out the pair
 // line: ordered along +r (the backward half from its far end, the forward half
 // from the origin), each quantity interpolated linearly from the earlier point
 // with t = i / nv; the opacity is the line optics of Magritte I evaluated in
 // that order; n_inter = ceil(max(chi) ds / dtau_max), at least 1.
 __device__ __noinline__ int redo_n_inter(const DevMesh &m, const DevLines &Ln, const double *r, const double *vo,
-                                         int32_t o, double sgn, int32_t ia, int32_t ib, double za, double zb, int nv,
-                                         int j, int32_t bin, double dtau_max) {
+                                         int32_t o, double sgn, int32_t ia, int32_t ib, int nv, int j, int32_t bin,
+                                         double dtau_max) {
     const bool bwd = sgn < 0.0;
     const double e0 = sgn * r[0], e1 = sgn * r[1], e2 = sgn * r[2];
+    // the exact Z of the two points (0 at the origin, id -1)
+    const double xo = m.x[o], yo = m.y[o], zo = m.z[o];
+    const double za = ia < 0 ? 0.0 : exact_Z(m, ia, xo, yo, zo, e0, e1, e2);
+    const double zb = ib < 0 ? 0.0 : exact_Z(m, ib, xo, yo, zo, e0, e1, e2);
     const int32_t p0 = bwd ? ia : ib, p1 = bwd ? ib : ia;  // base points in the definition's order
     const double z0 = bwd ? za : zb, z1 = bwd ? zb : za;
     const int ilo = bwd ? j - 1 : nv - j;  // indices of the two samples from p0
@@ -465,10 +468,11 @@ __device__ __noinline__ int redo_n_inter(const DevMesh &m, const DevLines &Ln, c
 // ---- staging ----------------------------------------------------------------
 
 // Point q of the half (q < cnt: traced entry cnt-1-q, far end first; q == cnt:
-// the origin) into `slot`.
+// the origin) into `slot`; its exact Z and (single precision) the bound of
+// its delta's error are also returned, for the interval to it.
 template <typename R, int NL>
 __device__ __forceinline__ void stage_point(const DevMesh &m, const DevLines &Ln, Stage<R, NL> &sg, int32_t q,
-                                            int32_t cnt, int slot, int sign) {
+                                            int32_t cnt, int slot, int sign, double &zq, R &deq) {
     const HalfList &hl = sg.hl;
     const double sgn = double(sign);
     const int32_t L = Ln.L;
@@ -492,9 +496,10 @@ __device__ __forceinline__ void stage_point(const DevMesh &m, const DevLines &Ln
         }
     }
     sg.id[slot] = q < cnt ? id : -1;
-    sg.z[slot] = z;
+    if constexpr (sizeof(R) == 8) sg.z[slot] = z;
+    zq = z;
+    deq = de;
     sg.d[slot] = d;
-    if constexpr (sizeof(R) == 4) sg.de[slot] = de;
     sg.w[slot] = __ldg(Pts<R>::dvw(Ln) + id);
     sg.cc[slot] = __ldg(Pts<R>::chic(Ln) + id);
     sg.ec[slot] = __ldg(Pts<R>::etac(Ln) + id);
@@ -507,10 +512,13 @@ __device__ __forceinline__ void stage_point(const DevMesh &m, const DevLines &Ln
 
 // The interval from the point in slot-1 (farther) to the point in `slot`:
 // its number of velocity samples (Section 2.1.1) and, in single precision,
-// the constants of Eq. 2 with the bound on the opacity's error.
+// the constants of Eq. 2 with the bound on the opacity's error.  za, zb are
+// the exact Z of the farther and the nearer point, dea, deb the bounds of
+// their deltas' errors (single precision).
 template <typename R, int NL>
 __device__ __forceinline__ int stage_interval(const DevMesh &m, const DevLines &Ln, const SolveArgs &a,
-                                              Stage<R, NL> &sg, int slot, int sign) {
+                                              Stage<R, NL> &sg, int slot, int sign, double za, double zb, R dea,
+                                              R deb) {
     const int pa = slot - 1;
     if constexpr (sizeof(R) == 8) {
         // as defined: ceil(|delta_b - delta_a| / (dv_max min(dv_a, dv_b))) when that exceeds one
@@ -527,7 +535,6 @@ __device__ __forceinline__ int stage_interval(const DevMesh &m, const DevLines &
             dev_fail(a.status, kDevSubdivLimit);
             nv = kMaxSubdiv;
         }
-        sg.rnv[slot] = 1.0 / double(nv);
         return nv;
     } else {
         const float da = sg.d[pa], db = sg.d[slot], wa = sg.w[pa], wb = sg.w[slot];
@@ -535,7 +542,7 @@ __device__ __forceinline__ int stage_interval(const DevMesh &m, const DevLines &
         if (a.dv_max > 0.0) {
             // q64 = jump64 / lim64 lies in [(jump - ej) / lim (1 - k), (jump + ej) / lim (1 + k)]
             const float jump = fabsf(db - da);
-            const float ej = sg.de[pa] + sg.de[slot] + 2.f * kU * jump;
+            const float ej = dea + deb + 2.f * kU * jump;
             const float rl = 1.f / (float(a.dv_max) * fminf(wa, wb));
             const float nhi = ceilf((jump + ej) * rl * (1.f + 16.f * kU));
             if (nhi > 1.f) {
@@ -553,7 +560,7 @@ __device__ __forceinline__ int stage_interval(const DevMesh &m, const DevLines &
                 }
             }
         }
-        const float ds = float(sg.z[pa] - sg.z[slot]);  // distance increment, differenced in double
+        const float ds = float(za - zb);  // distance increment, differenced in double
         const float rn = 1.f / float(nv);
         const float hs = ds * rn;
         // Bound E of |chi32 - chi64| at every sample of the interval (both
@@ -564,7 +571,7 @@ __device__ __forceinline__ int stage_interval(const DevMesh &m, const DevLines &
         const float k6 = 6.f * kU + kERcp;  // interpolation in single precision
         const float ada = fabsf(da), adb = fabsf(db);
         const float dmax = fmaxf(ada, adb);
-        const float edi = sg.de[pa] + sg.de[slot] + k6 * (ada + adb);
+        const float edi = dea + deb + k6 * (ada + adb);
         const float rdvmin = 1.f / fminf(wa, wb);
         const float rho = kERcp + k6 * (wa + wb) * rdvmin + 4.f * kU;
         float E = 0.f, csum = fmaxf(sg.cc[pa], sg.cc[slot]);
@@ -581,11 +588,10 @@ __device__ __forceinline__ int stage_interval(const DevMesh &m, const DevLines &
         // Eq. 2: n_inter = max(1, ceil(fl(fl(chi64 ds64) / dtau_max))); ds64, the
         // definition's sample spacing, is within (3u + rho_s) of hs, rho_s the
         // rounding of its interpolated distances (8 u64 max|Z| / hs)
-        const float zmax = float(fmax(sg.z[pa], sg.z[slot]));
+        const float zmax = float(fmax(za, zb));
         const float kap = 15.f * kU + 9.0e-16f * zmax / hs + 1e-15f;
         const float dtm = float(a.dtau_max);
         const float qs = hs * float(1.0 / a.dtau_max);
-        sg.rnv[slot] = rn;
         sg.hq[slot] = 0.5f * hs;
         sg.thr[slot] = (dtm / hs) * (1.f - kap) - E * (1.f + 4.f * kU);
         sg.qlo[slot] = qs * (1.f - kap);
@@ -620,7 +626,7 @@ __device__ __forceinline__ void gen_sample(Stage<R, NL> &sg, int s_abs, int s_re
 #pragma unroll
             for (int c = 0; c < 2 * NL; ++c) o[6 + c] = sg.ce[c][k];
         } else {
-            const float t = float(j) * sg.rnv[k];
+            const float t = float(j) * (1.f / float(nv));  // rn of the interval, formed again
             o[0] = fmaf(sg.d[k] - sg.d[pa], t, sg.d[pa]);
             wv = fmaf(sg.w[k] - sg.w[pa], t, sg.w[pa]);
             o[2] = fmaf(sg.cc[k] - sg.cc[pa], t, sg.cc[pa]);
@@ -734,8 +740,8 @@ __device__ __noinline__ void resolve_n_inter(Stage<R, NL> &sg, const DevMesh &m,
     for (int i = 0; i < 2; ++i) {
         if (sg.fix[i][lane] >= 0) continue;
         const int32_t b = i == 0 ? bin0 : bin1;
-        int n = redo_n_inter(m, Ln, sg.r, sg.vo, sg.o, double(sign), sg.id[k - 1], sg.id[k], sg.z[k - 1], sg.z[k],
-                             sg.nv[k], j, b < sg.NB ? b : sg.NB - 1, a.dtau_max);
+        int n = redo_n_inter(m, Ln, sg.r, sg.vo, sg.o, double(sign), sg.id[k - 1], sg.id[k], sg.nv[k], j,
+                             b < sg.NB ? b : sg.NB - 1, a.dtau_max);
         if (n > kMaxSubdiv) {
             dev_fail(a.status, kDevSubdivLimit);
             n = kMaxSubdiv;
@@ -953,8 +959,7 @@ __device__ __forceinline__ void carry_slot(Stage<R, NL> &sg, int from) {
     sg.ec[0] = sg.ec[from];
 #pragma unroll
     for (int c = 0; c < 2 * NL; ++c) sg.ce[c][0] = sg.ce[c][from];
-    if constexpr (sizeof(R) == 4) sg.de[0] = sg.de[from];
-    sg.z[0] = sg.z[from];
+    if constexpr (sizeof(R) == 8) sg.z[0] = sg.z[from];  // single precision: carried by stage_chunk
     sg.id[0] = sg.id[from];
 }
 
@@ -971,10 +976,25 @@ __device__ __noinline__ int stage_chunk(const DevMesh &m, const DevLines &Ln, co
     const int nch = npt - qb < 32 ? int(npt - qb) : 32;
     const int slot = lane + 1;
     const int32_t q = qb + lane;
-    if (lane < nch) stage_point<R, NL>(m, Ln, sg, q, cnt, slot, sign);
+    double zq = 0.0;
+    R deq = R(0);
+    if (lane < nch) stage_point<R, NL>(m, Ln, sg, q, cnt, slot, sign, zq, deq);
+    // the farther point's Z and delta bound: the previous lane's, or the carried point's for lane 0
+    double zf = __shfl_up_sync(kFull, zq, 1);
+    R def = __shfl_up_sync(kFull, deq, 1);
+    if (lane == 0) {
+        zf = sg.z[0];
+        if constexpr (sizeof(R) == 4) def = sg.de0;
+    }
     __syncwarp();
+    if constexpr (sizeof(R) == 4) {
+        if (lane == nch - 1) {  // the next chunk's farther point
+            sg.z[0] = zq;
+            sg.de0 = deq;
+        }
+    }
     int nvk = 0;  // the far end (q = 0) starts the line: no interval
-    if (lane < nch && q > 0) nvk = stage_interval<R, NL>(m, Ln, a, sg, slot, sign);
+    if (lane < nch && q > 0) nvk = stage_interval<R, NL>(m, Ln, a, sg, slot, sign, zf, zq, def, deq);
     int incl = nvk;
 #pragma unroll
     for (int sh = 1; sh < 32; sh <<= 1) {
@@ -1058,14 +1078,19 @@ __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs
 
 // CTAs of 4 warps (2 in double precision, whose per-warp stage is twice as
 // large); the minimum resident CTAs per SM caps the registers
-// (65536 / (threads x CTAs)).  One line: 7 CTAs (72 registers; the shared
-// staging of 7 CTAs just fits 228 KB), measured 9 % faster than 6 on GB300.
-template <typename R, int NL, int BPL, typename P = R>
+// (65536 / (threads x CTAs)).  One line, second order: 9 CTAs (56 registers;
+// the shared staging of 9 CTAs, 24.5 KB each plus 1 KB reserved, fits 228 KB),
+// measured 4 % faster than 8 and 10 % faster than 7 on GB300.  The Hermitian
+// scheme's lane state is larger: 6 CTAs.
+template <typename R, int NL, int BPL, typename P = R, int ORD = 2>
 struct Occ {
     static constexpr int kWarps = sizeof(R) == 8 ? 2 : 4;
     static constexpr int kThreads = 32 * kWarps;
     static constexpr int kMinBlocks =
-        sizeof(R) == 8 ? 1 : sizeof(P) == 8 ? (NL == 1 ? 4 : 2) : (NL == 1 ? 8 : NL <= 4 ? 4 : 3);
+        sizeof(R) == 8 ? 1
+        : sizeof(P) == 8 ? (NL == 1 ? 4 : 2)
+        : ORD == 4 ? (NL == 1 ? 6 : NL <= 4 ? 4 : 3)
+                   : (NL == 1 ? 9 : NL <= 4 ? 4 : 3);
 };
 
 // J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
@@ -1103,6 +1128,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
 
     // frequency of each bin of this lane and its profile constants
     float am[NL], bm[NL];
+    R So_[BPL];  // the source function at the origin of each bin
 #pragma unroll
     for (int l = 0; l < NL; ++l) am[l] = bm[l] = 0.f;
 #pragma unroll
@@ -1125,7 +1151,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
         }
         R chi_o, eta_o;
         optics<R, NL>(R(0), rdvo, __ldg(Pts<R>::chic(Ln) + o), __ldg(Pts<R>::etac(Ln) + o), oce, f, chi_o, eta_o);
-        ln.So[i][lane] = eta_o / chi_o;
+        So_[i] = eta_o / chi_o;
     }
     if constexpr (sizeof(R) == 4 && NL == 1) {
         // the profile constants of the tile's first and last bin (the far-wing test of gen_sample)
@@ -1197,7 +1223,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
                 wb.Sp = ln.cpr[2][i][lane];
                 wb.rh = ln.cpr[3][i][lane];
             }
-            const R So = ln.So[i][lane];
+            const R So = So_[i];
             const R u = ORD == 4 ? origin_u4(wb, wf[i], So, R(a.I_bdy)) : origin_u2(wb, wf[i], So);
             const int32_t b = lane_bin<BPL>(sg, i, lane);
             if (a.u_out && b < NB) a.u_out[(int64_t(oc) * Rs.npairs + p) * NB + b] = double(u);
@@ -1236,7 +1262,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
 
 // Grid-mapped launch: warp w of the grid solves item w = oc * n_tiles + tile.
 template <typename R, int NL, int BPL, int ORD, typename P>
-__global__ void __launch_bounds__(Occ<R, NL, BPL, P>::kThreads, (Occ<R, NL, BPL, P>::kMinBlocks))
+__global__ void __launch_bounds__(Occ<R, NL, BPL, P, ORD>::kThreads, (Occ<R, NL, BPL, P, ORD>::kMinBlocks))
 k_solve(const __grid_constant__ DevMesh m, const __grid_constant__ DevLines Ln, const __grid_constant__ DevRays Rs,
         const __grid_constant__ SolveArgs a) {
     __shared__ Stage<R, NL> stage[Occ<R, NL, BPL, P>::kWarps];  // one per warp
@@ -1253,7 +1279,7 @@ k_solve(const __grid_constant__ DevMesh m, const __grid_constant__ DevLines Ln, 
 // models: each warp takes the next item from a global counter until the list
 // is exhausted.
 template <typename R, int NL, int BPL, int ORD, typename P>
-__global__ void __launch_bounds__(Occ<R, NL, BPL, P>::kThreads, (Occ<R, NL, BPL, P>::kMinBlocks))
+__global__ void __launch_bounds__(Occ<R, NL, BPL, P, ORD>::kThreads, (Occ<R, NL, BPL, P, ORD>::kMinBlocks))
 k_solve_queue(const BatchSlot *__restrict__ slots, const uint2 *__restrict__ work, int64_t n_work,
               unsigned long long *__restrict__ next) {
     __shared__ Stage<R, NL> stage[Occ<R, NL, BPL, P>::kWarps];
