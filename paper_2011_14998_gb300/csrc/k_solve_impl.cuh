@@ -360,8 +360,8 @@ __device__ __forceinline__ int32_t lane_bin(const St &sg, int i, int lane) {
 // (D Fh, dtb/2) are kept in the pivot precision P.
 template <typename R, int ORD, typename P = R>
 struct Lane {
-    static constexpr int kWR = ORD == 4 ? 7 : 3;  // zh, chi, eta (Hermitian: + Sp, Sc, hp, rh)
-    static constexpr int kCR = ORD == 4 ? 4 : 1;  // zh (Hermitian: + hp, Sp, rh)
+    static constexpr int kWR = ORD == 4 ? 6 : 3;  // zh, chi, eta (Hermitian: + Sp, Sc, hp; rh = 1/hp re-formed)
+    static constexpr int kCR = ORD == 4 ? 3 : 1;  // zh (Hermitian: + hp, Sp)
     P wp[2][2][32];                              // D Fh, dtb/2
     R wr[kWR][2][32];
     P cpp[2][2][32];                             // backward half: D Fh, dtb/2
@@ -867,7 +867,6 @@ __device__ __forceinline__ void put_sweep(Lane<R, ORD, P> &ln, const Sweep<R, P>
             ln.wr[3][i][lane] = w[i].Sp;
             ln.wr[4][i][lane] = w[i].Sc;
             ln.wr[5][i][lane] = w[i].hp;
-            ln.wr[6][i][lane] = w[i].rh;
         }
     }
 }
@@ -886,7 +885,8 @@ __device__ __forceinline__ void get_sweep(const Lane<R, ORD, P> &ln, Sweep<R, P>
             w[i].Sp = ln.wr[3][i][lane];
             w[i].Sc = ln.wr[4][i][lane];
             w[i].hp = ln.wr[5][i][lane];
-            w[i].rh = ln.wr[6][i][lane];
+            // the reciprocal of the last increment, formed again as the row formed it
+            w[i].rh = w[i].hp < R(0) ? R(0) : Ar<R>::rcp(w[i].hp);
         } else {
             w[i].Sp = w[i].Sc = w[i].hp = w[i].rh = R(0);
         }
@@ -1081,7 +1081,7 @@ __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs
 // (65536 / (threads x CTAs)).  One line, second order: 9 CTAs (56 registers;
 // the shared staging of 9 CTAs, 24.5 KB each plus 1 KB reserved, fits 228 KB),
 // measured 4 % faster than 8 and 10 % faster than 7 on GB300.  The Hermitian
-// scheme's lane state is larger: 6 CTAs.
+// scheme's lane state is larger: 7 CTAs (72 registers).
 template <typename R, int NL, int BPL, typename P = R, int ORD = 2>
 struct Occ {
     static constexpr int kWarps = sizeof(R) == 8 ? 2 : 4;
@@ -1089,7 +1089,7 @@ struct Occ {
     static constexpr int kMinBlocks =
         sizeof(R) == 8 ? 1
         : sizeof(P) == 8 ? (NL == 1 ? 4 : 2)
-        : ORD == 4 ? (NL == 1 ? 6 : NL <= 4 ? 4 : 3)
+        : ORD == 4 ? (NL == 1 ? 7 : NL <= 4 ? 4 : 3)
                    : (NL == 1 ? 9 : NL <= 4 ? 4 : 3);
 };
 
@@ -1202,7 +1202,6 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
             if constexpr (ORD == 4) {
                 ln.cpr[1][i][lane] = ln.wr[5][i][lane];  // hp
                 ln.cpr[2][i][lane] = ln.wr[3][i][lane];  // Sp
-                ln.cpr[3][i][lane] = ln.wr[6][i][lane];  // rh
             }
         }
         if (lane == 0) sg.hl = half_list(a, hb + 1);
@@ -1221,7 +1220,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
             if constexpr (ORD == 4) {
                 wb.hp = ln.cpr[1][i][lane];
                 wb.Sp = ln.cpr[2][i][lane];
-                wb.rh = ln.cpr[3][i][lane];
+                wb.rh = wb.hp < R(0) ? R(0) : Ar<R>::rcp(wb.hp);
             }
             const R So = So_[i];
             const R u = ORD == 4 ? origin_u4(wb, wf[i], So, R(a.I_bdy)) : origin_u2(wb, wf[i], So);
