@@ -354,18 +354,16 @@ __device__ __forceinline__ int32_t lane_bin(const St &sg, int i, int lane) {
 // Per-lane state that lives across chunks of samples, kept in shared memory
 // so that no register holds it across the out-of-line staging calls: the
 // elimination state of each of the lane's (at most two) bins (D and Fh enter
-// every step only as their product, which is what is kept), the running
-// maximum of chi, the compensated J sums, the origin's source function, and
-// the backward half's coupling to the origin row.  The pivot quantities
-// (D Fh, dtb/2) are kept in the pivot precision P.
+// every step only as their product, which is what is kept) and the running
+// maximum of chi.  The pivot quantities (D Fh, dtb/2) are kept in the pivot
+// precision P.  What is needed only once per pair (the J sums, the origin's
+// source function, the backward half's coupling to the origin row) stays in
+// the item loop's registers, so that 9 CTAs fit the shared memory.
 template <typename R, int ORD, typename P = R>
 struct Lane {
     static constexpr int kWR = ORD == 4 ? 6 : 3;  // zh, chi, eta (Hermitian: + Sp, Sc, hp; rh = 1/hp re-formed)
-    static constexpr int kCR = ORD == 4 ? 3 : 1;  // zh (Hermitian: + hp, Sp)
     P wp[2][2][32];                              // D Fh, dtb/2
     R wr[kWR][2][32];
-    P cpp[2][2][32];                             // backward half: D Fh, dtb/2
-    R cpr[kCR][2][32];
     R cm[32];
 };
 
@@ -1080,17 +1078,16 @@ __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs
 // large); the minimum resident CTAs per SM caps the registers
 // (65536 / (threads x CTAs)).  One line, second order: 9 CTAs (56 registers;
 // the shared staging of 9 CTAs, 24.5 KB each plus 1 KB reserved, fits 228 KB),
-// measured 4 % faster than 8 and 10 % faster than 7 on GB300.  The Hermitian
-// scheme's lane state is larger: 7 CTAs (72 registers).
-template <typename R, int NL, int BPL, typename P = R, int ORD = 2>
+// measured 4 % faster than 8 and 10 % faster than 7 on GB300 (the Hermitian
+// scheme: 3 % faster than 8).
+template <typename R, int NL, int BPL, typename P = R>
 struct Occ {
     static constexpr int kWarps = sizeof(R) == 8 ? 2 : 4;
     static constexpr int kThreads = 32 * kWarps;
     static constexpr int kMinBlocks =
         sizeof(R) == 8 ? 1
         : sizeof(P) == 8 ? (NL == 1 ? 4 : 2)
-        : ORD == 4 ? (NL == 1 ? 7 : NL <= 4 ? 4 : 3)
-                   : (NL == 1 ? 9 : NL <= 4 ? 4 : 3);
+        : (NL == 1 ? 9 : NL <= 4 ? 4 : 3);
 };
 
 // J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
@@ -1183,6 +1180,8 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
 
     const int64_t h0 = int64_t(oc) * Rs.npairs * 2;
     double js[BPL], jc[BPL];  // each bin's J: Neumaier sum and compensation
+    P cpD[BPL], cpT[BPL];     // the backward half's coupling to the origin row: D Fh, dtb / 2,
+    R cpZ[BPL], cpH[BPL], cpS[BPL];  // zh (Hermitian: + the last increment and S)
 #pragma unroll
     for (int i = 0; i < BPL; ++i) js[i] = jc[i] = 0.0;
 #pragma unroll 1
@@ -1196,12 +1195,12 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
         half_sweep<R, NL, BPL, ORD, P>(m, Ln, a, sg, ln, -1);
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {  // the backward half's coupling to the origin row
-            ln.cpp[0][i][lane] = ln.wp[0][i][lane];  // D Fh
-            ln.cpp[1][i][lane] = ln.wp[1][i][lane];  // dtb / 2
-            ln.cpr[0][i][lane] = ln.wr[0][i][lane];  // zh
+            cpD[i] = ln.wp[0][i][lane];  // D Fh
+            cpT[i] = ln.wp[1][i][lane];  // dtb / 2
+            cpZ[i] = ln.wr[0][i][lane];  // zh
             if constexpr (ORD == 4) {
-                ln.cpr[1][i][lane] = ln.wr[5][i][lane];  // hp
-                ln.cpr[2][i][lane] = ln.wr[3][i][lane];  // Sp
+                cpH[i] = ln.wr[5][i][lane];  // hp
+                cpS[i] = ln.wr[3][i][lane];  // Sp
             }
         }
         if (lane == 0) sg.hl = half_list(a, hb + 1);
@@ -1213,13 +1212,13 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
             Sweep<R, P> wb;
-            wb.Fh = ln.cpp[0][i][lane];
+            wb.Fh = cpD[i];
             wb.Dm = P(1);
-            wb.dtp = ln.cpp[1][i][lane];
-            wb.zh = ln.cpr[0][i][lane];
+            wb.dtp = cpT[i];
+            wb.zh = cpZ[i];
             if constexpr (ORD == 4) {
-                wb.hp = ln.cpr[1][i][lane];
-                wb.Sp = ln.cpr[2][i][lane];
+                wb.hp = cpH[i];
+                wb.Sp = cpS[i];
                 wb.rh = wb.hp < R(0) ? R(0) : Ar<R>::rcp(wb.hp);
             }
             const R So = So_[i];
@@ -1261,7 +1260,7 @@ __device__ __forceinline__ void solve_item(const DevMesh &m, const DevLines &Ln,
 
 // Grid-mapped launch: warp w of the grid solves item w = oc * n_tiles + tile.
 template <typename R, int NL, int BPL, int ORD, typename P>
-__global__ void __launch_bounds__(Occ<R, NL, BPL, P, ORD>::kThreads, (Occ<R, NL, BPL, P, ORD>::kMinBlocks))
+__global__ void __launch_bounds__(Occ<R, NL, BPL, P>::kThreads, (Occ<R, NL, BPL, P>::kMinBlocks))
 k_solve(const __grid_constant__ DevMesh m, const __grid_constant__ DevLines Ln, const __grid_constant__ DevRays Rs,
         const __grid_constant__ SolveArgs a) {
     __shared__ Stage<R, NL> stage[Occ<R, NL, BPL, P>::kWarps];  // one per warp
@@ -1278,7 +1277,7 @@ k_solve(const __grid_constant__ DevMesh m, const __grid_constant__ DevLines Ln, 
 // models: each warp takes the next item from a global counter until the list
 // is exhausted.
 template <typename R, int NL, int BPL, int ORD, typename P>
-__global__ void __launch_bounds__(Occ<R, NL, BPL, P, ORD>::kThreads, (Occ<R, NL, BPL, P, ORD>::kMinBlocks))
+__global__ void __launch_bounds__(Occ<R, NL, BPL, P>::kThreads, (Occ<R, NL, BPL, P>::kMinBlocks))
 k_solve_queue(const BatchSlot *__restrict__ slots, const uint2 *__restrict__ work, int64_t n_work,
               unsigned long long *__restrict__ next) {
     __shared__ Stage<R, NL> stage[Occ<R, NL, BPL, P>::kWarps];

@@ -104,3 +104,28 @@ def test_eq2_near_ties_take_the_definitions_count(ctx, orc):
     assert j_rel_err(u64, uo)[0] < 1e-10
     assert j_rel_err(u32, uo)[0] < 1e-4
     assert prof["decisions_redone"] > 0
+
+
+def test_fast_wind_far_wings_match_oracle(ctx, orc):
+    """A wind twenty times faster (300 km/s) puts most traced points far in the
+    wings of every bin, where the single-precision solve takes the continuum
+    without the profile (velocity sampling off, so that the oracle stays
+    quick): J of the FP32 form against the FP64 oracle (1e-4) on sampled
+    origins and against the GPU FP64 form everywhere."""
+    import synth
+
+    import paper_2011_14998_gb300 as mgx
+
+    m = synth.wind_model(1500, seed=61, n_freq=50, level=1, v_inf=300.0)
+    mid = ctx.load(m)
+    J32 = ctx.solve_J(mid, precision=mgx.MGX_FP32, dv_max=0.0)
+    J32b = ctx.solve_J_batch([mid], precision=mgx.MGX_FP32, dv_max=0.0)[0].cpu().numpy()
+    J64 = ctx.solve_J(mid, precision=mgx.MGX_FP64, dv_max=0.0)
+    rays = ctx.rays(mid)
+    ctx.free(mid)
+    origins = np.arange(0, 1500, 6)
+    Jo = orc.OracleModel(m, rays=rays).solve_J(orc.params(dv_max=0.0), origins=origins)
+    assert j_rel_err(J64[origins], Jo)[0] < 1e-10
+    assert j_rel_err(J32[origins], Jo)[0] < 1e-4
+    assert j_rel_err(J32, J64)[0] < 1e-4
+    assert j_rel_err(J32b, J32)[0] < 1e-5
