@@ -650,6 +650,15 @@ __device__ __forceinline__ void gen_sample(Stage<R, NL> &sg, int s_abs, int s_re
         }
         o[4] = sg.hq[k];
         o[5] = sg.thr[k];
+        if constexpr (NL == 1) {
+            // no bin can split anywhere on the interval when the largest opacity any
+            // sample of it (or the point before it) can reach, continuum plus line
+            // centre (the profile is at most 1; interpolation and the fused sums
+            // round within 4u), stays below the threshold: the record says so
+            // with an infinite threshold and the step skips the vote
+            const float cb = fmaxf(sg.cc[pa], sg.cc[k]) + fmaxf(sg.ce[0][pa], sg.ce[0][k]);
+            if (cb * (1.f + 8.f * kU) <= o[5]) o[5] = INFINITY;
+        }
     } else {
         // the definition's layout: samples interpolated from the earlier point
         // along +r with t = i / nv, exact end points; ds between consecutive samples
@@ -776,17 +785,20 @@ __device__ __forceinline__ bool sample_step(const R (&v)[Stage<R, NL>::kS], int 
 #pragma unroll
         for (int i = 0; i < BPL; ++i) optics<R, NL>(dl, rdv, v[2], v[3], v + 6, f[i], chi_q[i], eta_q[i]);
     }
-    bool split = false;
+    bool go;  // no bin needs a split (n_inter = 1 for all)
     R cq = chi_q[0];
     if constexpr (sizeof(R) == 4) {
 #pragma unroll
         for (int i = 1; i < BPL; ++i) cq = fmax(cq, chi_q[i]);
-        split = fmax(cmax, cq) > thr;
+        // an infinite threshold (uniform: the warp's record) means no bin of the interval can split
+        go = (NL == 1 && thr == R(INFINITY)) || !__any_sync(kFull, fmax(cmax, cq) > thr);
     } else {
+        bool split = false;
 #pragma unroll
         for (int i = 0; i < BPL; ++i) split |= fmax(w[i].chi, chi_q[i]) > thr;
+        go = !__any_sync(kFull, split);
     }
-    if (!__any_sync(kFull, split)) {
+    if (go) {
 #pragma unroll
         for (int i = 0; i < BPL; ++i) {
             R Sq = R(0);
