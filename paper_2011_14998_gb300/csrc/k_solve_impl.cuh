@@ -306,7 +306,10 @@ __device__ __forceinline__ HalfList half_list(const SolveArgs &a, int64_t h) {
 // Layout of one velocity-sample record, as the bins read it: delta, 1/dv,
 // continuum opacity and emissivity, half the distance to the previous sample,
 // the Eq. 2 threshold on chi, then chi0 and eta0 of each line; padded to whole
-// 16-byte words so that each word is one shared-memory load.
+// 16-byte words so that each word is one shared-memory load.  In single
+// precision with one line, a negative 1/dv marks a sample in the far wing of
+// every bin of the tile (the optics are the continuum's) and an infinite
+// threshold an interval on which no bin can need a split.
 template <typename R, int NL>
 struct Rec {
     static constexpr int kVals = 6 + 2 * NL;
