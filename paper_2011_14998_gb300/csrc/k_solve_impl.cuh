@@ -1094,7 +1094,9 @@ __device__ void half_sweep(const DevMesh &m, const DevLines &Ln, const SolveArgs
 // (65536 / (threads x CTAs)).  One line, second order: 9 CTAs (56 registers;
 // the shared staging of 9 CTAs, 24.5 KB each plus 1 KB reserved, fits 228 KB),
 // measured 4 % faster than 8 and 10 % faster than 7 on GB300 (the Hermitian
-// scheme: 3 % faster than 8).
+// scheme: 3 % faster than 8).  Two lines: 8 CTAs (64 registers; 18 % faster
+// than 4 on the clump octree); three and four: 6 (80 registers; 11 % faster
+// than 4 on a four-line wind).
 template <typename R, int NL, int BPL, typename P = R>
 struct Occ {
     static constexpr int kWarps = sizeof(R) == 8 ? 2 : 4;
@@ -1102,7 +1104,7 @@ struct Occ {
     static constexpr int kMinBlocks =
         sizeof(R) == 8 ? 1
         : sizeof(P) == 8 ? (NL == 1 ? 4 : 2)
-        : (NL == 1 ? 9 : NL <= 4 ? 4 : 3);
+        : (NL == 1 ? 9 : NL == 2 ? 8 : NL <= 4 ? 6 : 3);
 };
 
 // J of origin a.o_begin + oc for the bins of frequency tile `tile`, by one warp.
