@@ -377,14 +377,18 @@ mgx_status mgx_mlp_features(mgx_ctx *ctx, int32_t model, const double *rho, cons
 mgx_status mgx_reduce_mesh_learned(mgx_ctx *ctx, int32_t model, const float *X, double keep_fraction, uint8_t *keep,
                                    int64_t *n_kept);
 
-/* The approximate single-precision functions of the single-precision solve,
- * for tests of the error bounds its integer decisions (velocity-sample counts,
- * Eq. 2 sub-interval counts) are certified with; no counterpart in the paper.
- * kind 0: y = 2^x as the solve evaluates exp(-a^2); kind 1: y = 1/x.  x, y [n]
- * are device pointers on the context's device; the work is enqueued on the
- * context's stream (no synchronisation).  *bound (may be NULL) receives the
- * largest relative error the solve assumes for that function.  MGX_EINVAL for
- * another kind, n < 0, or null arrays with n > 0. */
+/* The approximate single-precision functions of the single-precision solve and
+ * ray-set screen, for tests of the error bounds their integer decisions
+ * (velocity-sample counts, Eq. 2 sub-interval counts, HEALPix pixels) are
+ * certified with; no counterpart in the paper.  kind 0: y = 2^x as the solve
+ * evaluates exp(-a^2); kind 1: y = 1/x; kind 2: y[i] = atan2f(x[n + i], x[i])
+ * as the ray set's single-precision vec2pix evaluates the azimuth (x holds 2n
+ * values: the n x-components, then the n y-components).  x, y are device
+ * pointers on the context's device; the work is enqueued on the context's
+ * stream (no synchronisation).  *bound (may be NULL) receives the largest
+ * error the certification assumes for that function: relative for kinds 0 and
+ * 1, absolute (radians) for kind 2.  MGX_EINVAL for another kind, n < 0, or
+ * null arrays with n > 0. */
 mgx_status mgx_eval_approx(mgx_ctx *ctx, int32_t kind, const float *x, int64_t n, float *y, float *bound);
 
 /* Measured throughput of the arithmetic pipes the formal solution runs on (no

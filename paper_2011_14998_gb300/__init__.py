@@ -370,11 +370,12 @@ def mgx_reduce_mesh(ctx, model, f, f_small, f_large, G_thres, seed):
 
 
 def mgx_eval_approx(ctx, kind: int, x, y) -> float:
-    """y = 2^x (kind 0) or 1/x (kind 1) by the solve's approximate single-precision
-    functions; x, y float32 device tensors of the same size.  Returns the relative
-    error bound the solve assumes for that function."""
+    """y = 2^x (kind 0), 1/x (kind 1) or atan2f(x[n:], x[:n]) (kind 2) by the
+    approximate single-precision functions the certified decisions rest on;
+    x, y float32 device tensors (x of y's size, twice it for kind 2).  Returns
+    the error bound assumed for that function (relative; absolute for kind 2)."""
     b = C.c_float(0.0)
-    _check(ctx, load_library().mgx_eval_approx(ctx, int(kind), _ptr(x), int(x.numel()), _ptr(y), C.byref(b)))
+    _check(ctx, load_library().mgx_eval_approx(ctx, int(kind), _ptr(x), int(y.numel()), _ptr(y), C.byref(b)))
     return float(b.value)
 
 

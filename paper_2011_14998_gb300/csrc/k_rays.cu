@@ -67,6 +67,97 @@ __device__ int32_t vec2pix_nest(int l, double dx, double dy, double dz) {
     return int32_t((face << (2 * l)) + spread2(x) + 2 * spread2(y));
 }
 
+// The same pixel in single precision, certified: returns false when a
+// rounding could move any of the decisions (the zone test, the face and the
+// in-face indices, all truncations of non-negative arguments) away from those
+// of vec2pix_nest above, which the caller then takes.  The translation unit is
+// compiled without contraction, so each operation rounds once (u = 2^-24):
+//   z = c / |v| within 7u |z| of the double z (inputs, sum of squares, sqrt, division);
+//   phi = atan2f(b, a) within kAtanErr of the double angle (3 ulp documented;
+//     the inputs' rounding adds at most u);
+//   t = phi 2/pi (+4) within et = 0.64 kAtanErr + 12u (and not within et of 0,
+//     where the wrap into [0, 4) jumps);
+//   equatorial arguments ns (0.5 + t) -+ ns 0.75 z within ns (et + 0.75 ez + 11u);
+//   polar w = ns sqrt(3 (1 - |z|)) within w ((ez + 2u) / (2 (1 - |z|)) + 2u), and
+//   a, b = trunc(tp w), trunc((1 - tp) w) within et w + ew + 2u w.
+// The double path's own rounding (about 1e-15) is inside these margins.
+constexpr float kAtanErr = 9.5367431640625e-7f;  // 2^-20 rad
+
+__device__ __forceinline__ bool trunc_certain(float v, float e, int64_t &k) {
+    // trunc of the double value equals trunc(v) when v is farther than e from
+    // every integer other than 0 (trunc maps (-1, 1) to 0)
+    if (!(v > -1.0f + e)) return false;
+    if (v < 1.0f - e) {
+        k = 0;
+        return true;
+    }
+    const float f = floorf(v);
+    if (v - f < e || f + 1.0f - v < e) return false;
+    k = int64_t(f);
+    return true;
+}
+
+__device__ bool vec2pix_nest_f(int l, float a, float b, float c, int32_t &pix) {
+    constexpr float kU = 5.9604644775390625e-8f;  // 2^-24
+    const int64_t ns = int64_t(1) << l;
+    const float fns = float(ns);
+    const float len = sqrtf(a * a + b * b + c * c);
+    const float z = c / len;
+    const float za = fabsf(z);
+    const float ez = 7.0f * kU * za + 1e-30f;
+    float t = atan2f(b, a) * 0.636619772367581343f;
+    const float et = 0.64f * kAtanErr + 12.0f * kU;
+    // the wrap into [0, 4) is discontinuous at t = 0: both precisions must be on the same side
+    if (fabsf(t) < et) return false;
+    if (t < 0.0f) t = t + 4.0f;
+    if (t >= 4.0f) t = t - 4.0f;
+    constexpr float kTwoThirds = 0.666666666666666667f;
+    int64_t face, x, y;
+    if (za <= kTwoThirds - ez - 2.0f * kU) {
+        const float c1 = fns * (0.5f + t), c2 = fns * (0.75f * z);
+        const float eA = fns * (et + 0.75f * ez + 11.0f * kU);
+        int64_t asc, dsc;
+        if (!trunc_certain(c1 - c2, eA, asc) || !trunc_certain(c1 + c2, eA, dsc)) return false;
+        const int64_t fa = asc >> l, fd = dsc >> l;
+        face = (fa == fd) ? (fa | 4) : (fa < fd ? fa : fd + 8);
+        x = dsc & (ns - 1);
+        y = ns - 1 - (asc & (ns - 1));
+    } else if (za > kTwoThirds + ez + 2.0f * kU) {
+        int64_t q;
+        if (t > 3.0f + et) q = 3;
+        else if (!trunc_certain(t, et, q)) return false;
+        const float tp = t - float(q);
+        const float om = 1.0f - za;
+        const float w = fns * sqrtf(3.0f * om);
+        const float ew = w * ((ez + 2.0f * kU) / (2.0f * om) + 2.0f * kU);
+        if (!(ew < 0.25f)) return false;  // next to the pole
+        int64_t ia, ib;
+        if (!trunc_certain(tp * w, et * w + ew + 2.0f * kU * w, ia)) return false;
+        if (!trunc_certain((1.0f - tp) * w, et * w + ew + 2.0f * kU * w, ib)) return false;
+        if (ia > ns - 1) ia = ns - 1;
+        if (ib > ns - 1) ib = ns - 1;
+        if (z >= 0.0f) {
+            face = q;
+            x = ns - 1 - ib;
+            y = ns - 1 - ia;
+        } else {
+            face = q + 8;
+            x = ia;
+            y = ib;
+        }
+    } else {
+        return false;  // at the zone boundary
+    }
+    pix = int32_t((face << (2 * l)) + spread2(x) + 2 * spread2(y));
+    return true;
+}
+
+// atan2f as the single-precision ray-set screen evaluates it (for the tests of kAtanErr).
+__global__ void k_eval_atan2(const float *__restrict__ x, int64_t n, float *__restrict__ y) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        y[i] = atan2f(x[n + i], x[i]);
+}
+
 __global__ void k_rays_fixed(int32_t n, int32_t level, int32_t npairs, const uint32_t *__restrict__ pairs,
                              uint32_t *__restrict__ rays) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -106,7 +197,11 @@ k_rays_adaptive(DevMesh m, int32_t lmin, int32_t lmax, int32_t npairs, int64_t n
         if (j == o || j < 0 || j >= m.n) continue;
         const double dx = __dsub_rn(m.x[j], xo), dy = __dsub_rn(m.y[j], yo), dz = __dsub_rn(m.z[j], zo);
         if (dx == 0.0 && dy == 0.0 && dz == 0.0) continue;
-        atomicAdd(&hist[lmax][vec2pix_nest(lmax, dx, dy, dz)], 1u);
+        // single precision when the screen certifies the pixel, else the double path
+        int32_t pix;
+        if (!vec2pix_nest_f(lmax, __double2float_rn(dx), __double2float_rn(dy), __double2float_rn(dz), pix))
+            pix = vec2pix_nest(lmax, dx, dy, dz);
+        atomicAdd(&hist[lmax][pix], 1u);
     }
     __syncthreads();
     for (int l = lmax - 1; l >= lmin; --l) {
@@ -163,6 +258,15 @@ k_rays_adaptive(DevMesh m, int32_t lmin, int32_t lmax, int32_t npairs, int64_t n
 }
 
 }  // namespace
+
+void launch_eval_atan2(const float *x, int64_t n, float *y, cudaStream_t st) {
+    if (n <= 0) return;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_eval_atan2<<<unsigned(blocks), 256, 0, st>>>(x, n, y);
+}
+
+float atan2_bound() { return kAtanErr; }
 
 void launch_rays_fixed(int32_t n, int32_t level, int32_t npairs, const uint32_t *pairs, uint32_t *rays,
                        cudaStream_t st) {

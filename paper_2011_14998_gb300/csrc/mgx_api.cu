@@ -1736,11 +1736,12 @@ mgx_status mgx_reduce_mesh_learned_weighted(mgx_ctx *ctx, int32_t model, const f
 mgx_status mgx_eval_approx(mgx_ctx *ctx, int32_t kind, const float *x, int64_t n, float *y, float *bound) {
     if (!ctx) return MGX_EINVAL;
     ctx->err.clear();
-    if (kind != 0 && kind != 1) return fail(ctx, MGX_EINVAL, "eval_approx: kind must be 0 or 1");
+    if (kind < 0 || kind > 2) return fail(ctx, MGX_EINVAL, "eval_approx: kind must be 0, 1 or 2");
     if (n < 0 || (n > 0 && (!x || !y))) return fail(ctx, MGX_EINVAL, "eval_approx: bad arrays");
-    if (bound) *bound = approx_bound(kind);
+    if (bound) *bound = kind == 2 ? atan2_bound() : approx_bound(kind);
     DeviceGuard g(ctx->device);
-    launch_eval_approx(kind, x, n, y, ctx->stream);
+    if (kind == 2) launch_eval_atan2(x, n, y, ctx->stream);
+    else launch_eval_approx(kind, x, n, y, ctx->stream);
     CK(cudaGetLastError());
     return MGX_OK;
 }

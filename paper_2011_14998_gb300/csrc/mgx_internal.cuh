@@ -248,6 +248,8 @@ void launch_select_top(const float *score, int64_t n, int64_t k, int32_t *ids, f
 // relative error bound the solve's decisions take for each
 void launch_eval_approx(int kind, const float *x, int64_t n, float *y, cudaStream_t st);
 float approx_bound(int kind);
+void launch_eval_atan2(const float *x, int64_t n, float *y, cudaStream_t st);  // k_rays.cu
+float atan2_bound();
 
 // ---- arithmetic-pipe throughput microbenchmarks (k_peaks.cu)
 cudaError_t alu_peaks(cudaStream_t st, int reps, double out[4]);

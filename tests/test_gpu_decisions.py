@@ -52,7 +52,37 @@ def test_approximation_error_bounds(ctx):
     assert e_ex2 < 0.5 * b_ex2
     assert e_rcp < 0.5 * b_rcp
     with pytest.raises(mgx.MgxError):
-        mgx.mgx_eval_approx(ctx.ptr, 2, xd, yd)
+        mgx.mgx_eval_approx(ctx.ptr, 3, xd, yd)
+
+
+def test_atan2_error_bound(ctx):
+    """atan2f as the single-precision ray-set screen evaluates it stays within
+    half the absolute bound its pixel certification takes, over random
+    directions (all quadrants, up to 1e4 in ratio), the axes and the branch cut."""
+    import torch
+
+    import paper_2011_14998_gb300 as mgx
+
+    rng = np.random.default_rng(4)
+    n = 1 << 22
+    ang = rng.uniform(-np.pi, np.pi, n)
+    r = 10.0 ** rng.uniform(-3, 3, n)
+    xs = (r * np.cos(ang)).astype(np.float32)
+    ys = (r * np.sin(ang)).astype(np.float32)
+    extra_x = np.array([1, -1, 0, 0, -1, -1, 1e-4, -1e-4, 3.0], np.float32)
+    extra_y = np.array([0, 0, 1, -1, 1e-30, -1e-30, 1.0, 1.0, 1e-7], np.float32)
+    xs, ys = np.concatenate([xs, extra_x]), np.concatenate([ys, extra_y])
+    m = len(xs)
+    xd = torch.from_numpy(np.concatenate([xs, ys])).cuda()
+    yd = torch.empty(m, dtype=torch.float32, device="cuda")
+    bound = mgx.mgx_eval_approx(ctx.ptr, 2, xd, yd)
+    torch.cuda.synchronize()
+    got = yd.cpu().numpy().astype(np.float64)
+    ref = np.arctan2(ys.astype(np.float64), xs.astype(np.float64))
+    err = np.abs(got - ref)
+    err = np.minimum(err, 2 * np.pi - err)  # the branch cut: +pi and -pi are the same direction
+    print(f"atan2f max abs err {err.max():.3e} (bound {bound:.3e})")
+    assert err.max() < 0.5 * bound
 
 
 def test_ex2_flushes_far_wings_to_zero(ctx):
