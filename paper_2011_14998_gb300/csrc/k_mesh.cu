@@ -61,17 +61,23 @@ void launch_ingest_mesh(int32_t n, const double *pos_aos, const double *vel_aos,
 // neighbour records for the tracer's single-precision screen: the position of
 // nbr[e] rounded to float, next to its id, in CSR order
 __global__ void k_pack_neighbours(int32_t n, const int32_t *__restrict__ off, const int32_t *__restrict__ nbr,
-                                  const float4 *__restrict__ phi, float4 *__restrict__ nrec) {
+                                  float4 *__restrict__ phi, float4 *__restrict__ nrec) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     if (i >= n) return;
+    const float4 hi = phi[i];
+    float smax = 0.0f;
     for (int32_t e = off[i]; e < off[i + 1]; ++e) {
         const int32_t j = nbr[e];
         const float4 h = phi[j];
         nrec[e] = make_float4(h.x, h.y, h.z, __int_as_float(j));
+        // |x_j - x_i|_1 exactly as the tracer's screen forms it
+        const float dx = h.x - hi.x, dy = h.y - hi.y, dz = h.z - hi.z;
+        smax = fmaxf(smax, fabsf(dx) + fabsf(dy) + fabsf(dz));
     }
+    phi[i].w = smax;  // only w: the positions other threads read stay as they are
 }
 
-void launch_pack_neighbours(int32_t n, const int32_t *off, const int32_t *nbr, const float4 *phi, float4 *nrec,
+void launch_pack_neighbours(int32_t n, const int32_t *off, const int32_t *nbr, float4 *phi, float4 *nrec,
                             cudaStream_t st) {
     const int tb = 256;
     k_pack_neighbours<<<unsigned((n + tb - 1) / tb), tb, 0, st>>>(n, off, nbr, phi, nrec);

@@ -99,7 +99,10 @@ struct Walk {
 // The definition's own double rounding adds at most g0 to a Z difference
 // (16 u64 max|x|_1 against g0 = 32 u^2 max|x|_1) and g0 (E1 + de) + g0^2 to q
 // (16.2 u64 |x_n - x_o|_1 |e|_1 + 3.01 u64 q + 197 u64^2 |x_n - x_o|_1^2).
-// Returns the next point (-1: the half-ray ends; -2: undecided); when it
+// In the loop the S-dependent parts of edZ and de take the largest S over the
+// point's neighbours (stored with the mesh), so that per neighbour only dZ, e,
+// |e|_1, q and eq are formed; the winner's own de is formed again for the next
+// step.  Returns the next point (-1: the half-ray ends; -2: undecided); when it
 // decides a next point it moves the walk's position and lateral offset to it.
 __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const int32_t c = wk.c;
@@ -111,6 +114,14 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const int32_t e1 = m.off[c + 1];
     // the screen of neighbour record e (the same arithmetic for the loop and the winner)
     const float bz = fmaf(4.0f * kU, hc.w, m.g0), be0 = fmaf(8.0f * kU, hc.w, eec);
+    // bounds shared by every neighbour of c, from Smax = max_n S (the mesh
+    // stores it in phi[c].w, formed as S is below): edZ <= edZs, and de <= des
+    // through |e|_1 <= E1max (|w|_1 <= S (1 + |f|_1) <= 2.74 S), each raised by
+    // 16u for its own rounding; the q-interval keeps each neighbour's own |e|_1
+    const float smax = m.phi[c].w;
+    const float edZs = fmaf(8.0f * kU, smax, bz) * (1.0f + 16.0f * kU);
+    const float E1max = (fabsf(ecx) + fabsf(ecy) + fabsf(ecz) + 2.74f * smax) * (1.0f + 16.0f * kU);
+    const float des = fmaf(15.0f * kU, smax, fmaf(2.0f * kU, E1max, be0)) * (1.0f + 16.0f * kU);
     auto screen = [&](const float4 &rec, float &dZ, float &edZ, float &ex, float &ey, float &ez, float &S) {
         const float dx = rec.x - hc.x, dy = rec.y - hc.y, dz = rec.z - hc.z;
         S = fabsf(dx) + fabsf(dy) + fabsf(dz);
@@ -123,14 +134,15 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     auto bound = [&](float S, float E1) { return fmaf(15.0f * kU, S, fmaf(2.0f * kU, E1, be0)); };
     for (int32_t e = m.off[c]; e < e1; ++e) {
         const float4 rec = __ldg(m.nrec + e);
-        float dZ, edZ, ex, ey, ez, S;
-        screen(rec, dZ, edZ, ex, ey, ez, S);
-        if (dZ < -edZ) continue;  // surely not forward
-        const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
+        const float dx = rec.x - hc.x, dy = rec.y - hc.y, dz = rec.z - hc.z;
+        const float dZ = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
+        if (dZ < -edZs) continue;  // surely not forward
+        const float ex = ecx + fmaf(-dZ, f0, dx), ey = ecy + fmaf(-dZ, f1, dy), ez = ecz + fmaf(-dZ, f2, dz);
         const float q = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
-        const float de = bound(S, E1);
-        const float eq = fmaf(fmaf(2.02f, E1, 3.03f * de), de, fmaf(6.0f * kU, q, fmaf(m.g0, E1 + de, g02)));
+        const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
+        const float eq = fmaf(fmaf(2.02f, E1, 3.03f * des), des, fmaf(6.0f * kU, q, fmaf(m.g0, E1 + des, g02)));
         const float lo = q - eq, hi = q + eq;
+        const float edZ = edZs;
         const int32_t nb = __float_as_int(rec.w);
         if (lo < lo1) {
             lo2 = lo1;

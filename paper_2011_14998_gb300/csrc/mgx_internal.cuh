@@ -42,7 +42,7 @@ struct DevMesh {
     const float *vxf, *vyf, *vzf;
     const int32_t *off;  // [n+1]
     const int32_t *nbr;  // [E]
-    const float4 *phi;        // positions rounded to float (w unused)
+    const float4 *phi;        // positions rounded to float; w: the largest |x_n - x|_1 over the neighbours (float)
     const float4 *nrec;       // [E] neighbour records: fl32 position of nbr[e], id in w (as int bits)
     float g0;                 // 32 u^2 max_n (|x|+|y|+|z|) + 1e-37: floor of the screen's error bounds
 };
@@ -97,7 +97,7 @@ void launch_ingest_mesh(int32_t n, const double *pos_aos, const double *vel_aos,
                         double *vz, float *vxf, float *vyf, float *vzf, int32_t *off32,
                         const int32_t *nbr, float4 *phi, unsigned int *xmax_bits, int *status,
                         cudaStream_t st);
-void launch_pack_neighbours(int32_t n, const int32_t *off, const int32_t *nbr, const float4 *phi,
+void launch_pack_neighbours(int32_t n, const int32_t *off, const int32_t *nbr, float4 *phi,
                             float4 *nrec, cudaStream_t st);
 void launch_ingest_lines(int32_t n, int32_t L, const double *chi0, const double *eta0,
                          const double *dvw, const double *chic, const double *etac, float *chi0f,
