@@ -508,6 +508,9 @@ mgx_status finish_batch_step(mgx_ctx *ctx, BatchPlan &pl) {
     return sync_status(ctx);
 }
 
+// Device memory the fixed-width rows of a batched plan may take.
+constexpr size_t kRowsBudget = size_t(96) << 30;
+
 // Row width of the padded layout: the narrowest power of two that leaves at
 // most `permille` / 1000 of the traced points to the tail pass, within the
 // memory budget for the rows (else the widest that fits).
@@ -1273,7 +1276,9 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     }
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
-    pl.pad = choose_pad(tot, pl.total_half, std::min(ctx->arena_budget, free_b / 3),
+    // the rows may take up to a third of free device memory (at most kRowsBudget): every point
+    // they do not hold is walked a second time by the tail pass
+    pl.pad = choose_pad(tot, pl.total_half, std::min(kRowsBudget, free_b / 3),
                         pl.tune.tail_permille > 0 ? pl.tune.tail_permille : 20);
     int j = 0;
     while ((int32_t(1) << j) < pl.pad) ++j;
