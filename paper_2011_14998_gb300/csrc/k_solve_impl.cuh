@@ -483,7 +483,9 @@ __device__ __forceinline__ void stage_point(const DevMesh &m, const DevLines &Ln
     R d = R(0), de = R(0);
     if (q < cnt) {
         const int32_t k = cnt - 1 - q;
-        id = k < hl.n_main ? __ldg(hl.main + k) : __ldg(hl.tail + (hl.tail_off + k));
+        // the traced ids stream through once: evict-first, so that they do not push the
+        // mesh and the spilled item state out of L2
+        id = k < hl.n_main ? __ldcs(hl.main + k) : __ldcs(hl.tail + (hl.tail_off + k));
         z = exact_Z(m, id, sg.xo[0], sg.xo[1], sg.xo[2], e0, e1, e2);
         if constexpr (sizeof(R) == 8) {
             d = proj64(m, id, sg.vo, e0, e1, e2);
