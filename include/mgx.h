@@ -267,8 +267,10 @@ enum {
  *           copies back (one copy per model, on the context's stream) after
  *           each step; a graph replay then copies too
  *   flags   MGX_BATCH_RAYS: the step starts by rebuilding the ray sets;
- *           MGX_BATCH_GRAPH: the first call plans the layout (one host
- *           synchronisation), runs the step and captures it as a CUDA graph;
+ *           MGX_BATCH_GRAPH: the first call plans the layout (the row width
+ *           from the traced lengths of a sample of the origins, the tail from
+ *           the first step's own padded trace: two host synchronisations),
+ *           runs the step and captures it as a CUDA graph;
  *           later calls with the same models, parameters, outputs, flags and
  *           tuning replay the graph without host work.  A replay whose traced
  *           lists no longer fit the planned layout fails with MGX_ERANGE and

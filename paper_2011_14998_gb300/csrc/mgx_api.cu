@@ -458,7 +458,9 @@ constexpr int kScratchSize = kScratchTotals + kPadCandidates + 1;
 
 // One step of a batched solve: (ray sets,) padded trace, tail offsets, tail
 // trace, work list, persistent solve.
-mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
+// The first part of a batched step: ray sets (when asked for), the padded
+// trace and the prefix sums of the excesses that place the tail.
+mgx_status enqueue_batch_front(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
     if (pl.flags & MGX_BATCH_RAYS)
         for (Model *m : ms) enqueue_rays(ctx, *m);
     int64_t hb = 0;
@@ -475,8 +477,14 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
         CK(cub::DeviceScan::InclusiveSum(pl.cub_tmp, pl.cub_bytes, pl.excess, pl.offs + 1, pl.total_half,
                                          ctx->stream));
     }
+    CK(cudaGetLastError());
+    return MGX_OK;
+}
+
+// The rest: the tail trace, the work list and the persistent solve.
+mgx_status enqueue_batch_back(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
+    int64_t hb = 0;
     if (pl.tail_cap > 0) {
-        hb = 0;
         for (Model *m : ms) {
             Timed t(ctx, MGX_K_TRACE_EMIT);
             launch_trace_tail(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.pad, pl.lens + hb, pl.resume + hb,
@@ -500,6 +508,11 @@ mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> 
     return MGX_OK;
 }
 
+mgx_status enqueue_batch_step(mgx_ctx *ctx, BatchPlan &pl, std::vector<Model *> &ms) {
+    const mgx_status s = enqueue_batch_front(ctx, pl, ms);
+    return s != MGX_OK ? s : enqueue_batch_back(ctx, pl, ms);
+}
+
 // Copy the staged outputs of a batched step to their host buffers (one copy
 // per model, after the step on the same stream) and wait for the stream.
 mgx_status finish_batch_step(mgx_ctx *ctx, BatchPlan &pl) {
@@ -510,6 +523,9 @@ mgx_status finish_batch_step(mgx_ctx *ctx, BatchPlan &pl) {
 
 // Device memory the fixed-width rows of a batched plan may take.
 constexpr size_t kRowsBudget = size_t(96) << 30;
+// The planning sample of half-ray lengths: kSampleChunks runs of origins per
+// model, 1/kSampleShare of them in all.
+constexpr int32_t kSampleChunks = 32, kSampleShare = 32;
 
 // Row width of the padded layout: the narrowest power of two that leaves at
 // most `permille` / 1000 of the traced points to the tail pass, within the
@@ -1255,15 +1271,28 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     CK(cudaMallocAsync(&pl.cub_tmp, pl.cub_bytes ? pl.cub_bytes : 1, ctx->stream));
     CK(cudaMemcpyAsync(pl.geo, geo.data(), geo.size() * sizeof(BatchGeom), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(pl.obase, obase.data(), obase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-    // plan the layout from the half-ray lengths (the only host synchronisation)
+    // the row width from the lengths of a sample of the half-rays: every model's origins in
+    // kSampleChunks evenly spaced runs of about 1/kSampleShare of them (all of a small model);
+    // the rest of the lengths stay 0 and add nothing to the totals, whose ratios pick the width
     if (flags & MGX_BATCH_RAYS)
         for (Model *m : ms) enqueue_rays(ctx, *m, false);  // planning is not part of a step's profile
+    CK(cudaMemsetAsync(pl.lens, 0, size_t(pl.total_half) * sizeof(int64_t), ctx->stream));
     {
         int64_t hb = 0;
         for (Model *m : ms) {
-            launch_trace_count(mesh_view(*m), rays_view(ctx, *m), 0, m->n, pl.lens + hb, ctx->d_status, nullptr,
-                               ctx->stream);
-            hb += int64_t(m->n) * m->npairs * 2;
+            const int32_t n = m->n, np2 = 2 * m->npairs;
+            if (n <= kSampleChunks * kSampleShare) {
+                launch_trace_count(mesh_view(*m), rays_view(ctx, *m), 0, n, pl.lens + hb, ctx->d_status, nullptr,
+                                   ctx->stream);
+            } else {
+                const int32_t run = (n + kSampleChunks * kSampleShare - 1) / (kSampleChunks * kSampleShare);
+                for (int32_t c = 0; c < kSampleChunks; ++c) {
+                    const int32_t o0 = int32_t(int64_t(n) * c / kSampleChunks), o1 = std::min(n, o0 + run);
+                    launch_trace_count(mesh_view(*m), rays_view(ctx, *m), o0, o1, pl.lens + hb + int64_t(o0) * np2,
+                                       ctx->d_status, nullptr, ctx->stream);
+                }
+            }
+            hb += int64_t(n) * np2;
         }
     }
     launch_excess_totals(pl.lens, pl.total_half, pl.scratch + kScratchTotals, ctx->stream);
@@ -1282,9 +1311,22 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
                         pl.tune.tail_permille > 0 ? pl.tune.tail_permille : 20);
     int j = 0;
     while ((int32_t(1) << j) < pl.pad) ++j;
+    CK(dalloc(ctx, &pl.rows, size_t(pl.total_half) * size_t(pl.pad)));
+    // the first step's padded trace gives every length: the exact tail, then the rest of the step
+    s = enqueue_batch_front(ctx, pl, ms);
+    if (s != MGX_OK) {
+        free_plan(ctx, pl);
+        return s;
+    }
+    launch_excess_totals(pl.lens, pl.total_half, pl.scratch + kScratchTotals, ctx->stream);
+    CK(cudaMemcpyAsync(tot, pl.scratch + kScratchTotals, sizeof tot, cudaMemcpyDeviceToHost, ctx->stream));
+    s = sync_status(ctx);
+    if (s != MGX_OK) {
+        free_plan(ctx, pl);
+        return s;
+    }
     pl.tail_cap = int64_t(tot[j]);
     pl.total_points = int64_t(tot[kPadCandidates]);
-    CK(dalloc(ctx, &pl.rows, size_t(pl.total_half) * size_t(pl.pad)));
     CK(dalloc(ctx, &pl.tail, size_t(std::max<int64_t>(pl.tail_cap, 1))));
     std::vector<BatchSlot> slots(static_cast<size_t>(n_models));
     for (int32_t k = 0; k < n_models; ++k) {
@@ -1314,7 +1356,7 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     }
     ctx->trace_points += pl.total_points;
     CK(cudaMemcpyAsync(pl.slots, slots.data(), slots.size() * sizeof(BatchSlot), cudaMemcpyHostToDevice, ctx->stream));
-    s = enqueue_batch_step(ctx, pl, ms);
+    s = enqueue_batch_back(ctx, pl, ms);
     if (s != MGX_OK) {
         free_plan(ctx, pl);
         return s;
