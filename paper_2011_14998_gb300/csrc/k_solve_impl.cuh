@@ -644,7 +644,7 @@ __device__ __forceinline__ void gen_sample(Stage<R, NL> &sg, int s_abs, int s_re
             // the continuum's (bit for bit).  A and B rise with the bin, so over the
             // tile B delta + A lies in [min(tf, tl) - W, max(tf, tl) + W] with
             // W = (B_last - B_first) |delta|; |a| >= 12.1 leaves margin for every
-            // rounding.  The record carries the verdict as a negative 1/dv.
+            // rounding.  The record carries the outcome as a negative 1/dv.
             if (sg.wing) {
                 const float dl = o[0];
                 const float tf = fmaf(sg.wb[0], dl, sg.wa[0]), tl = fmaf(sg.wb[1], dl, sg.wa[1]);
