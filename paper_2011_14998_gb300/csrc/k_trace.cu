@@ -122,6 +122,8 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const float edZs = fmaf(8.0f * kU, smax, bz) * (1.0f + 16.0f * kU);
     const float E1max = (fabsf(ecx) + fabsf(ecy) + fabsf(ecz) + 2.74f * smax) * (1.0f + 16.0f * kU);
     const float des = fmaf(15.0f * kU, smax, fmaf(2.0f * kU, E1max, be0)) * (1.0f + 16.0f * kU);
+    // eq = (2.02 E1 + 3.03 de) de + 6u q + g0 (E1 + de) + g0^2 regrouped around E1 and q
+    const float k1 = fmaf(2.02f, des, m.g0), k0 = fmaf(fmaf(3.03f, des, m.g0), des, g02);
     auto screen = [&](const float4 &rec, float &dZ, float &edZ, float &ex, float &ey, float &ez, float &S) {
         const float dx = rec.x - hc.x, dy = rec.y - hc.y, dz = rec.z - hc.z;
         S = fabsf(dx) + fabsf(dy) + fabsf(dz);
@@ -140,7 +142,7 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
         const float ex = ecx + fmaf(-dZ, f0, dx), ey = ecy + fmaf(-dZ, f1, dy), ez = ecz + fmaf(-dZ, f2, dz);
         const float q = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
-        const float eq = fmaf(fmaf(2.02f, E1, 3.03f * des), des, fmaf(6.0f * kU, q, fmaf(m.g0, E1 + des, g02)));
+        const float eq = fmaf(k1, E1, fmaf(6.0f * kU, q, k0));
         const float lo = q - eq, hi = q + eq;
         const float edZ = edZs;
         const int32_t nb = __float_as_int(rec.w);
