@@ -108,8 +108,9 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const int32_t c = wk.c;
     const float4 hc = wk.hc;
     const float f0 = wk.f0, f1 = wk.f1, f2 = wk.f2, ecx = wk.ecx, ecy = wk.ecy, ecz = wk.ecz, eec = wk.eec;
-    int32_t best = -1, lo1_id = -1, be = 0;
-    float hib = INFINITY, lo1 = INFINITY, lo2 = INFINITY;
+    int32_t lo1_id = -1, be = 0;
+    float lo1 = INFINITY, lo2 = INFINITY, hi1 = INFINITY;
+    bool sf1 = false;  // the candidate of lo1 is surely forward
     const float g02 = m.g0 * m.g0;
     const int32_t e1 = m.off[c + 1];
     // the screen of neighbour record e (the same arithmetic for the loop and the winner)
@@ -144,23 +145,22 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
         const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
         const float eq = fmaf(k1, E1, fmaf(6.0f * kU, q, k0));
         const float lo = q - eq, hi = q + eq;
-        const float edZ = edZs;
-        const int32_t nb = __float_as_int(rec.w);
+        // the candidate with the smallest lower bound decides the step when it is surely
+        // forward and its whole interval lies below every other candidate's
         if (lo < lo1) {
             lo2 = lo1;
             lo1 = lo;
-            lo1_id = nb;
-        } else if (lo < lo2) {
-            lo2 = lo;
-        }
-        if (dZ > edZ && hi < hib) {  // surely forward
-            hib = hi;
-            best = nb;
+            hi1 = hi;
+            sf1 = dZ > edZs;
+            lo1_id = __float_as_int(rec.w);
             be = e;
+        } else {
+            lo2 = fminf(lo2, lo);
         }
     }
     if (lo1_id < 0) return -1;  // no neighbour can be forward: the half-ray ends
-    if (best < 0 || best != lo1_id || !(hib < lo2)) return -2;
+    if (!sf1 || !(hi1 < lo2)) return -2;
+    const int32_t best = lo1_id;
     // the winner's offset and bound, formed again from its record as in the loop
     const float4 rec = __ldg(m.nrec + be);
     float dZ, edZ, ex, ey, ez, S;
