@@ -330,9 +330,9 @@ mgx_status mgx_autotune(mgx_ctx *ctx, const int32_t *models, int32_t n_models, c
  * MGX_ERANGE when the ray set has too many pairs for the array or when one
  * origin's traced point lists alone do not fit (more than about 14 million
  * points).  No cudaMalloc, cudaFree or allocating library routine is called.
- * The first call on a device looks up the array's device address (set-up).
- * The call cannot be captured in a CUDA graph: for every chunk it reads the
- * traced total back to the host and synchronises the stream.  Every call
+ * The first call on a device looks up the array's device address (set-up);
+ * make that first call before any stream capture.  For every chunk the call
+ * reads the traced total back to the host and synchronises the stream.  Every call
  * shares the array: calls that overlap on the GPU (other streams or contexts
  * on the same device) race on it. */
 mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_params *params,
