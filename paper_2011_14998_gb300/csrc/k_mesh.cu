@@ -58,8 +58,9 @@ void launch_ingest_mesh(int32_t n, const double *pos_aos, const double *vel_aos,
     k_check_nbr<<<unsigned((n + tb - 1) / tb), tb, 0, st>>>(n, off32, nbr, status);
 }
 
-// neighbour records for the tracer's single-precision screen: the position of
-// nbr[e] rounded to float, next to its id, in CSR order
+// neighbour records for the tracer's single-precision screen: the float
+// position of nbr[e] minus the float position of its point, next to its id, in
+// CSR order (the spare record after the last stays zero)
 __global__ void k_pack_neighbours(int32_t n, const int32_t *__restrict__ off, const int32_t *__restrict__ nbr,
                                   float4 *__restrict__ phi, float4 *__restrict__ nrec) {
     const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -69,9 +70,9 @@ __global__ void k_pack_neighbours(int32_t n, const int32_t *__restrict__ off, co
     for (int32_t e = off[i]; e < off[i + 1]; ++e) {
         const int32_t j = nbr[e];
         const float4 h = phi[j];
-        nrec[e] = make_float4(h.x, h.y, h.z, __int_as_float(j));
-        // |x_j - x_i|_1 exactly as the tracer's screen forms it
+        // x_j - x_i exactly as the tracer's screen forms it (differences of the float positions)
         const float dx = h.x - hi.x, dy = h.y - hi.y, dz = h.z - hi.z;
+        nrec[e] = make_float4(dx, dy, dz, __int_as_float(j));
         smax = fmaxf(smax, fabsf(dx) + fabsf(dy) + fabsf(dz));
     }
     phi[i].w = smax;  // only w: the positions other threads read stay as they are

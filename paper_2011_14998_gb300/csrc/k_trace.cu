@@ -10,7 +10,10 @@
 //
 // GB300 executes double precision at a small fraction of its single-precision
 // rate, so each step first screens the neighbours in single precision: each
-// CSR edge carries its neighbour's position rounded to float.  The screen
+// CSR edge carries the difference of the float-rounded positions of its
+// neighbour and its own point, Delta32 = fl(x_n32 - x_c32), next to the
+// neighbour's id; the records are read two at a time (one 32-byte load per
+// lane, which halves the load instructions of the walk).  The screen
 // works relative to the current point c rather than to the origin: with
 // Delta = x_n - x_c, the increment Z_n - Z_c = Delta.d and the lateral offset
 // e_n = e_c + Delta - (Delta.d) d (q_n = |e_n|^2) involve only differences of
@@ -76,7 +79,6 @@ __device__ __forceinline__ double exact_Z(const DevMesh &m, int32_t c, double xo
 // it up executes no double-precision operation.
 struct Walk {
     int64_t w;                // write base of the entries (not kept by the padded pass: h * pad)
-    float4 hc;                // position of the current point (float; w = its |x|_1)
     float f0, f1, f2;         // direction (float)
     float ecx, ecy, ecz, eec; // lateral offset of the current point from the ray (float) and its bound
     int32_t c, k, expect;
@@ -84,8 +86,10 @@ struct Walk {
 
 
 // Single-precision screen of one step over the neighbour records of c (the
-// float position of each neighbour stored next to its id, read sequentially).
-// The walk holds c's float position hc (w = |hc|_1), (ecx, ecy, ecz)
+// difference Delta32 of the float positions, neighbour minus c, stored next to
+// the neighbour's id, read in aligned pairs; the mesh stores one spare record
+// after the last so that a pair never leaves the array).  hc is c's float
+// position, loaded with c's largest neighbour distance; the walk holds (ecx, ecy, ecz)
 // approximating c's lateral offset e_c = (x_c - x_o) - Z_c d componentwise
 // within eec, and the direction f rounded to float.  Bounds, with a_i = |hn_i| + |hc_i|,
 // S = |Delta32|_1, X = |hn|_1 + |hc|_1 <= 2 Xc + 1.01 S (Xc = |hc|_1) and
@@ -103,10 +107,12 @@ struct Walk {
 // point's neighbours (stored with the mesh), so that per neighbour only dZ, e,
 // |e|_1, q and eq are formed; the winner's own de is formed again for the next
 // step.  Returns the next point (-1: the half-ray ends; -2: undecided); when it
-// decides a next point it moves the walk's position and lateral offset to it.
+// decides a next point it moves the walk's lateral offset to it.
 __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const int32_t c = wk.c;
-    const float4 hc = wk.hc;
+    // hc: c's float position (only Xc = |hc|_1 enters the bounds) and its largest neighbour distance
+    const float4 pc = m.phi[c];
+    const float hcw = fabsf(pc.x) + fabsf(pc.y) + fabsf(pc.z);
     const float f0 = wk.f0, f1 = wk.f1, f2 = wk.f2, ecx = wk.ecx, ecy = wk.ecy, ecz = wk.ecz, eec = wk.eec;
     int32_t lo1_id = -1, be = 0;
     float lo1 = INFINITY, lo2 = INFINITY, hi1 = INFINITY;
@@ -114,19 +120,19 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const float g02 = m.g0 * m.g0;
     const int32_t e1 = m.off[c + 1];
     // the screen of neighbour record e (the same arithmetic for the loop and the winner)
-    const float bz = fmaf(4.0f * kU, hc.w, m.g0), be0 = fmaf(8.0f * kU, hc.w, eec);
+    const float bz = fmaf(4.0f * kU, hcw, m.g0), be0 = fmaf(8.0f * kU, hcw, eec);
     // bounds shared by every neighbour of c, from Smax = max_n S (the mesh
     // stores it in phi[c].w, formed as S is below): edZ <= edZs, and de <= des
     // through |e|_1 <= E1max (|w|_1 <= S (1 + |f|_1) <= 2.74 S), each raised by
     // 16u for its own rounding; the q-interval keeps each neighbour's own |e|_1
-    const float smax = m.phi[c].w;
+    const float smax = pc.w;
     const float edZs = fmaf(8.0f * kU, smax, bz) * (1.0f + 16.0f * kU);
     const float E1max = (fabsf(ecx) + fabsf(ecy) + fabsf(ecz) + 2.74f * smax) * (1.0f + 16.0f * kU);
     const float des = fmaf(15.0f * kU, smax, fmaf(2.0f * kU, E1max, be0)) * (1.0f + 16.0f * kU);
     // eq = (2.02 E1 + 3.03 de) de + 6u q + g0 (E1 + de) + g0^2 regrouped around E1 and q
     const float k1 = fmaf(2.02f, des, m.g0), k0 = fmaf(fmaf(3.03f, des, m.g0), des, g02);
     auto screen = [&](const float4 &rec, float &dZ, float &edZ, float &ex, float &ey, float &ez, float &S) {
-        const float dx = rec.x - hc.x, dy = rec.y - hc.y, dz = rec.z - hc.z;
+        const float dx = rec.x, dy = rec.y, dz = rec.z;  // the record holds x_n - x_c in float
         S = fabsf(dx) + fabsf(dy) + fabsf(dz);
         dZ = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
         edZ = fmaf(8.0f * kU, S, bz);
@@ -135,18 +141,20 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
         ez = ecz + fmaf(-dZ, f2, dz);
     };
     auto bound = [&](float S, float E1) { return fmaf(15.0f * kU, S, fmaf(2.0f * kU, E1, be0)); };
-    for (int32_t e = m.off[c]; e < e1; ++e) {
-        const float4 rec = __ldg(m.nrec + e);
-        const float dx = rec.x - hc.x, dy = rec.y - hc.y, dz = rec.z - hc.z;
+    // the neighbour records two at a time (one 32-byte load per lane; the records
+    // before off[c] and from off[c + 1] on in a pair take no part)
+    auto consider = [&](const float4 &rec, int32_t e, bool valid) {
+        const float dx = rec.x, dy = rec.y, dz = rec.z;  // the record holds x_n - x_c in float
         const float dZ = fmaf(dz, f2, fmaf(dy, f1, dx * f0));
-        if (dZ < -edZs) continue;  // surely not forward
         const float ex = ecx + fmaf(-dZ, f0, dx), ey = ecy + fmaf(-dZ, f1, dy), ez = ecz + fmaf(-dZ, f2, dz);
         const float q = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
         const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
         const float eq = fmaf(k1, E1, fmaf(6.0f * kU, q, k0));
-        const float lo = q - eq, hi = q + eq;
+        // surely not forward, or not a neighbour of c: no part in the decision
+        const float lo = (valid && !(dZ < -edZs)) ? q - eq : INFINITY, hi = q + eq;
         // the candidate with the smallest lower bound decides the step when it is surely
-        // forward and its whole interval lies below every other candidate's
+        // forward and its whole interval lies below every other candidate's (ascending
+        // record order, as one record at a time would take them)
         if (lo < lo1) {
             lo2 = lo1;
             lo1 = lo;
@@ -157,6 +165,15 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
         } else {
             lo2 = fminf(lo2, lo);
         }
+    };
+    const int32_t eb = m.off[c];
+    for (int32_t e = eb & ~1; e < e1; e += 2) {
+        float4 ra, rb;  // records e and e + 1: one 256-bit read-only load (32-byte aligned, e even)
+        asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+            : "=f"(ra.x), "=f"(ra.y), "=f"(ra.z), "=f"(ra.w), "=f"(rb.x), "=f"(rb.y), "=f"(rb.z), "=f"(rb.w)
+            : "l"(m.nrec + e));
+        consider(ra, e, e >= eb);
+        consider(rb, e + 1, e + 1 < e1);
     }
     if (lo1_id < 0) return -1;  // no neighbour can be forward: the half-ray ends
     if (!sf1 || !(hi1 < lo2)) return -2;
@@ -167,7 +184,6 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     screen(rec, dZ, edZ, ex, ey, ez, S);
     const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
     wk.eec = bound(S, E1) * (1.0f + 8.0f * kU);  // with the rounding of the bound itself
-    wk.hc = make_float4(rec.x, rec.y, rec.z, fabsf(rec.x) + fabsf(rec.y) + fabsf(rec.z));
     wk.ecx = ex;
     wk.ecy = ey;
     wk.ecz = ez;
@@ -176,19 +192,22 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
 
 // Origin of half-ray h (two halves per pair, npairs pairs per origin).
 __device__ __forceinline__ int32_t walk_origin(const DevRays &R, int32_t o_begin, int64_t h) {
-    return o_begin + int32_t((h >> 1) / R.npairs);
+    const int64_t pr = h >> 1;  // pair index from o_begin's first pair
+    // a 32-bit division whenever the index fits (always, short of 2^32 pairs in one call)
+    return o_begin + (pr < (int64_t(1) << 32) ? int32_t(uint32_t(pr) / uint32_t(R.npairs)) : int32_t(pr / R.npairs));
 }
 
 // Table index of half-ray h's pair direction.
-__device__ __forceinline__ int32_t walk_pix(const DevRays &R, int32_t o, int64_t h) {
-    const uint32_t ray = R.rays[int64_t(o) * R.npairs + ((h >> 1) % R.npairs)];
+__device__ __forceinline__ int32_t walk_pix(const DevRays &R, int32_t o_begin, int64_t h) {
+    // the rays of origin o_begin + pr / npairs, entry pr % npairs: entry pr from o_begin's row
+    const uint32_t ray = R.rays[int64_t(o_begin) * R.npairs + (h >> 1)];
     return int32_t(level_offset(int(ray >> 28)) + (ray & 0x0FFFFFFFu));
 }
 
 // The double direction of half-ray h (a backward half, h even, negated).
 __device__ __forceinline__ void walk_dir(const DevRays &R, int32_t o_begin, int64_t h, double &d0, double &d1,
                                          double &d2) {
-    const double *r = R.dir + 3 * int64_t(walk_pix(R, walk_origin(R, o_begin, h), h));
+    const double *r = R.dir + 3 * int64_t(walk_pix(R, o_begin, h));
     const bool back = (h & 1) == 0;
     d0 = back ? -r[0] : r[0];
     d1 = back ? -r[1] : r[1];
@@ -218,9 +237,8 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
         expect_len = lens[h];
         if (expect_len <= pad) return false;
     }
-    const int64_t pr = h >> 1;
-    const int32_t o = o_begin + int32_t(pr / R.npairs);
-    const float4 df = R.dirf[walk_pix(R, o, h)];
+    const int32_t o = walk_origin(R, o_begin, h);
+    const float4 df = R.dirf[walk_pix(R, o_begin, h)];
     const bool back = (h & 1) == 0;  // backward half: exact negation of the pair direction
     wk.f0 = back ? -df.x : df.x;
     wk.f1 = back ? -df.y : df.y;
@@ -260,8 +278,6 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
         const double Z = exact_Z(m, wk.c, xo, yo, zo, d0, d1, d2);
         lateral(m, wk, Z, d0, d1, d2, xo, yo, zo);
     }
-    wk.hc = m.phi[wk.c];
-    wk.hc.w = fabsf(wk.hc.x) + fabsf(wk.hc.y) + fabsf(wk.hc.z);
     return true;
 }
 
@@ -369,8 +385,6 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
                     wk.c = x.next;
                     lateral(m, wk, x.Z, d0, d1, d2, m.x[o], m.y[o], m.z[o]);
                     wk.c = c;
-                    wk.hc = m.phi[x.next];
-                    wk.hc.w = fabsf(wk.hc.x) + fabsf(wk.hc.y) + fabsf(wk.hc.z);
                 }
             }
         }

@@ -671,7 +671,16 @@ mgx_status mgx_load_mesh(mgx_ctx *ctx, int64_t n, const double *pos, const doubl
     CK(dalloc(ctx, &m.off, size_t(n + 1)));
     CK(dalloc(ctx, &m.nbr, size_t(E)));
     CK(dalloc(ctx, &m.phi, size_t(n)));
-    CK(dalloc(ctx, &m.nrec, size_t(E)));
+    // one spare record after the last: the tracer reads the records in aligned pairs
+    CK(dalloc(ctx, &m.nrec, size_t(E) + 1));
+    CK(cudaMemsetAsync(m.nrec, 0, (size_t(E) + 1) * sizeof(float4), ctx->stream));
+    if (reinterpret_cast<uintptr_t>(m.nrec) % 32 != 0) {  // the pair loads need 32-byte alignment
+        dfree(ctx, pos_d);
+        dfree(ctx, vel_d);
+        dfree(ctx, off64);
+        free_model(ctx, m);
+        return fail(ctx, MGX_ECUDA, "load_mesh: neighbour records not 32-byte aligned");
+    }
     unsigned int *xmax = nullptr;
     CK(dalloc(ctx, &xmax, 1));
     CK(cudaMemsetAsync(xmax, 0, sizeof(unsigned int), ctx->stream));

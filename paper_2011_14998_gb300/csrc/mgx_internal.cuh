@@ -43,7 +43,7 @@ struct DevMesh {
     const int32_t *off;  // [n+1]
     const int32_t *nbr;  // [E]
     const float4 *phi;        // positions rounded to float; w: the largest |x_n - x|_1 over the neighbours (float)
-    const float4 *nrec;       // [E] neighbour records: fl32 position of nbr[e], id in w (as int bits)
+    const float4 *nrec;       // [E + 1] neighbour records: fl32 position of nbr[e] minus that of its point, id in w (int bits)
     float g0;                 // 32 u^2 max_n (|x|+|y|+|z|) + 1e-37: floor of the screen's error bounds
 };
 
