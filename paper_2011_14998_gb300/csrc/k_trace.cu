@@ -214,6 +214,18 @@ __device__ __forceinline__ void walk_dir(const DevRays &R, int32_t o_begin, int6
     d2 = back ? -r[2] : r[2];
 }
 
+// Half-ray of launch position h.  The counting pass (MODE 0) given a stride
+// > 1 (the `pad` argument, unused otherwise by that pass) counts a planning
+// sample: every stride-th origin from o_begin, position h standing for the
+// half-ray h % (2 npairs) of origin o_begin + (h / (2 npairs)) stride, whose
+// length it stores at that half-ray's own index.  Every other pass: h itself.
+template <int MODE>
+__device__ __forceinline__ int64_t sampled(const DevRays &R, int32_t stride, int64_t h) {
+    if (MODE != 0 || stride <= 1) return h;
+    const int64_t np2 = 2 * int64_t(R.npairs);
+    return (h / np2) * stride * np2 + h % np2;
+}
+
 // The lateral offset of the walk's current point c (exact Z given) in
 // double, rounded to float, with its error bound (the float rounding plus g0).
 __device__ __forceinline__ void lateral(const DevMesh &m, Walk &wk, double Z, double d0, double d1, double d2,
@@ -237,9 +249,10 @@ __device__ __forceinline__ bool begin_walk(const DevMesh &m, const DevRays &R, i
         expect_len = lens[h];
         if (expect_len <= pad) return false;
     }
-    const int32_t o = walk_origin(R, o_begin, h);
-    const float4 df = R.dirf[walk_pix(R, o_begin, h)];
-    const bool back = (h & 1) == 0;  // backward half: exact negation of the pair direction
+    const int64_t hs = sampled<MODE>(R, pad, h);
+    const int32_t o = walk_origin(R, o_begin, hs);
+    const float4 df = R.dirf[walk_pix(R, o_begin, hs)];
+    const bool back = (hs & 1) == 0;  // backward half: exact negation of the pair direction
     wk.f0 = back ? -df.x : df.x;
     wk.f1 = back ? -df.y : df.y;
     wk.f2 = back ? -df.z : df.z;
@@ -325,7 +338,8 @@ __device__ Step step_exact_warp(const DevMesh &m, int32_t c, int32_t o, double d
     return Step{best, zbest};
 }
 
-// MODE 0: count the points of each half-ray; MODE 1: write their ids;
+// MODE 0: count the points of each half-ray (with pad > 1: of every pad-th
+// origin only, see sampled); MODE 1: write their ids;
 // MODE 2: write ids, exact double Z and (optionally) projected velocities;
 // MODE 3: padded pass (ids k < pad to row h, length to lens[h], excess over
 // the row to excess[h], the walk state after entry pad - 1 to resume[h] when
@@ -367,10 +381,10 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
             const int L = __ffs(todo) - 1;
             todo &= todo - 1;
             const int32_t c = __shfl_sync(0xffffffffu, wk.c, L);
-            const int64_t hL = __shfl_sync(0xffffffffu, h, L);
+            const int64_t hL = sampled<MODE>(R, pad, __shfl_sync(0xffffffffu, h, L));
             const int32_t o = walk_origin(R, o_begin, hL);
             double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-            if (lane == L) walk_dir(R, o_begin, h, d0, d1, d2);
+            if (lane == L) walk_dir(R, o_begin, hL, d0, d1, d2);
             d0 = __shfl_sync(0xffffffffu, d0, L);
             d1 = __shfl_sync(0xffffffffu, d1, L);
             d2 = __shfl_sync(0xffffffffu, d2, L);
@@ -434,7 +448,7 @@ k_trace(DevMesh m, DevRays R, int32_t o_begin, int64_t n_half, int64_t *__restri
         }
         if (ended) {
             if (MODE == 0) {
-                lens[h] = wk.k;
+                lens[sampled<MODE>(R, pad, h)] = wk.k;
             } else if (MODE == 3) {
                 lens[h] = wk.k;
                 excess[h] = wk.k > pad ? wk.k - pad : 0;
@@ -471,11 +485,13 @@ unsigned trace_grid(int64_t n_half, int ctas_per_sm = 0) {
 }  // namespace
 
 void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
-                        int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st) {
-    const int64_t n_half = int64_t(o_end - o_begin) * R.npairs * 2;
+                        int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st,
+                        int32_t o_stride) {
+    if (o_stride < 1) o_stride = 1;
+    const int64_t n_half = (int64_t(o_end - o_begin) + o_stride - 1) / o_stride * R.npairs * 2;
     if (n_half == 0) return;
     k_trace<0><<<trace_grid<0>(n_half), 128, 0, st>>>(m, R, o_begin, n_half, lens, nullptr, 0, 0, nullptr, nullptr,
-                                                  nullptr, status, counters, 0, nullptr, nullptr);
+                                                  nullptr, status, counters, o_stride, nullptr, nullptr);
 }
 
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,

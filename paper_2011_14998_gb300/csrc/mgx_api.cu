@@ -523,9 +523,10 @@ mgx_status finish_batch_step(mgx_ctx *ctx, BatchPlan &pl) {
 
 // Device memory the fixed-width rows of a batched plan may take.
 constexpr size_t kRowsBudget = size_t(96) << 30;
-// The planning sample of half-ray lengths: kSampleChunks runs of origins per
-// model, 1/kSampleShare of them in all.
-constexpr int32_t kSampleChunks = 32, kSampleShare = 32;
+// The planning sample of half-ray lengths: every kSampleShare-th origin of a
+// model with more than kSampleAll origins (all of a smaller one), counted by
+// one launch per model.
+constexpr int32_t kSampleShare = 32, kSampleAll = 1024;
 
 // Row width of the padded layout: the narrowest power of two that leaves at
 // most `permille` / 1000 of the traced points to the tail pass, within the
@@ -1280,9 +1281,9 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
     CK(cudaMallocAsync(&pl.cub_tmp, pl.cub_bytes ? pl.cub_bytes : 1, ctx->stream));
     CK(cudaMemcpyAsync(pl.geo, geo.data(), geo.size() * sizeof(BatchGeom), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(pl.obase, obase.data(), obase.size() * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
-    // the row width from the lengths of a sample of the half-rays: every model's origins in
-    // kSampleChunks evenly spaced runs of about 1/kSampleShare of them (all of a small model);
-    // the rest of the lengths stay 0 and add nothing to the totals, whose ratios pick the width
+    // the row width from the lengths of a sample of the half-rays: every kSampleShare-th origin
+    // of each model (all of a small model), one launch per model; the rest of the lengths stay
+    // 0 and add nothing to the totals, whose ratios pick the width
     if (flags & MGX_BATCH_RAYS)
         for (Model *m : ms) enqueue_rays(ctx, *m, false);  // planning is not part of a step's profile
     CK(cudaMemsetAsync(pl.lens, 0, size_t(pl.total_half) * sizeof(int64_t), ctx->stream));
@@ -1290,17 +1291,8 @@ mgx_status mgx_solve_J_batch(mgx_ctx *ctx, const int32_t *models, int32_t n_mode
         int64_t hb = 0;
         for (Model *m : ms) {
             const int32_t n = m->n, np2 = 2 * m->npairs;
-            if (n <= kSampleChunks * kSampleShare) {
-                launch_trace_count(mesh_view(*m), rays_view(ctx, *m), 0, n, pl.lens + hb, ctx->d_status, nullptr,
-                                   ctx->stream);
-            } else {
-                const int32_t run = (n + kSampleChunks * kSampleShare - 1) / (kSampleChunks * kSampleShare);
-                for (int32_t c = 0; c < kSampleChunks; ++c) {
-                    const int32_t o0 = int32_t(int64_t(n) * c / kSampleChunks), o1 = std::min(n, o0 + run);
-                    launch_trace_count(mesh_view(*m), rays_view(ctx, *m), o0, o1, pl.lens + hb + int64_t(o0) * np2,
-                                       ctx->d_status, nullptr, ctx->stream);
-                }
-            }
+            launch_trace_count(mesh_view(*m), rays_view(ctx, *m), 0, n, pl.lens + hb, ctx->d_status, nullptr,
+                               ctx->stream, n <= kSampleAll ? 1 : kSampleShare);
             hb += int64_t(n) * np2;
         }
     }

@@ -113,8 +113,10 @@ void launch_rays_adaptive(const DevMesh &m, int32_t lmin, int32_t lmax, int32_t 
                           int *status, cudaStream_t st);
 
 // ---- tracing (k_trace.cu)
+// o_stride > 1: only every o_stride-th origin from o_begin (a sample), each length at its own index.
 void launch_trace_count(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
-                        int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st);
+                        int64_t *lens, int *status, unsigned long long *counters, cudaStream_t st,
+                        int32_t o_stride = 1);
 // Z == nullptr: ids only (the solver's arena); otherwise also exact Z (and delta if given).
 // Entries beyond cap (relative to base) are refused with kDevArenaOverflow.
 void launch_trace_emit(const DevMesh &m, const DevRays &R, int32_t o_begin, int32_t o_end,
