@@ -105,8 +105,9 @@ struct Walk {
 // (16.2 u64 |x_n - x_o|_1 |e|_1 + 3.01 u64 q + 197 u64^2 |x_n - x_o|_1^2).
 // In the loop the S-dependent parts of edZ and de take the largest S over the
 // point's neighbours (stored with the mesh), so that per neighbour only dZ, e,
-// |e|_1, q and eq are formed; the winner's own de is formed again for the next
-// step.  Returns the next point (-1: the half-ray ends; -2: undecided); when it
+// |e|_1, q and eq are formed, and only the two smallest lower bounds and the
+// leader's record are kept; the leader's upper bound and forward test, and the
+// winner's own de for the next step, are formed again from its record.  Returns the next point (-1: the half-ray ends; -2: undecided); when it
 // decides a next point it moves the walk's lateral offset to it.
 __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const int32_t c = wk.c;
@@ -114,9 +115,8 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const float4 pc = m.phi[c];
     const float hcw = fabsf(pc.x) + fabsf(pc.y) + fabsf(pc.z);
     const float f0 = wk.f0, f1 = wk.f1, f2 = wk.f2, ecx = wk.ecx, ecy = wk.ecy, ecz = wk.ecz, eec = wk.eec;
-    int32_t lo1_id = -1, be = 0;
-    float lo1 = INFINITY, lo2 = INFINITY, hi1 = INFINITY;
-    bool sf1 = false;  // the candidate of lo1 is surely forward
+    int32_t be = -1;  // record of the candidate with the smallest lower bound (-1: none yet)
+    float lo1 = INFINITY, lo2 = INFINITY;  // the smallest lower bound, and the smallest of the others
     const float g02 = m.g0 * m.g0;
     const int32_t e1 = m.off[c + 1];
     // the screen of neighbour record e (the same arithmetic for the loop and the winner)
@@ -151,20 +151,15 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
         const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
         const float eq = fmaf(k1, E1, fmaf(6.0f * kU, q, k0));
         // surely not forward, or not a neighbour of c: no part in the decision
-        const float lo = (valid && !(dZ < -edZs)) ? q - eq : INFINITY, hi = q + eq;
+        const float lo = (valid && !(dZ < -edZs)) ? q - eq : INFINITY;
         // the candidate with the smallest lower bound decides the step when it is surely
         // forward and its whole interval lies below every other candidate's (ascending
-        // record order, as one record at a time would take them)
-        if (lo < lo1) {
-            lo2 = lo1;
-            lo1 = lo;
-            hi1 = hi;
-            sf1 = dZ > edZs;
-            lo1_id = __float_as_int(rec.w);
-            be = e;
-        } else {
-            lo2 = fminf(lo2, lo);
-        }
+        // record order, as one record at a time would take them); its upper bound and
+        // forward test are formed again from its record after the loop
+        const bool lead = lo < lo1;
+        lo2 = lead ? lo1 : fminf(lo2, lo);
+        lo1 = lead ? lo : lo1;
+        be = lead ? e : be;
     };
     const int32_t eb = m.off[c];
     for (int32_t e = eb & ~1; e < e1; e += 2) {
@@ -175,14 +170,18 @@ __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
         consider(ra, e, e >= eb);
         consider(rb, e + 1, e + 1 < e1);
     }
-    if (lo1_id < 0) return -1;  // no neighbour can be forward: the half-ray ends
-    if (!sf1 || !(hi1 < lo2)) return -2;
-    const int32_t best = lo1_id;
-    // the winner's offset and bound, formed again from its record as in the loop
+    if (be < 0) return -1;  // no neighbour can be forward: the half-ray ends
+    // the leading candidate's interval and forward test, formed again from its record
+    // with the loop's arithmetic (so bit for bit the loop's values)
     const float4 rec = __ldg(m.nrec + be);
     float dZ, edZ, ex, ey, ez, S;
     screen(rec, dZ, edZ, ex, ey, ez, S);
+    const float q = fmaf(ez, ez, fmaf(ey, ey, ex * ex));
     const float E1 = fabsf(ex) + fabsf(ey) + fabsf(ez);
+    const float hi1 = q + fmaf(k1, E1, fmaf(6.0f * kU, q, k0));
+    if (!(dZ > edZs) || !(hi1 < lo2)) return -2;
+    const int32_t best = __float_as_int(rec.w);
+    // the winner's offset and bound for the next step
     wk.eec = bound(S, E1) * (1.0f + 8.0f * kU);  // with the rounding of the bound itself
     wk.ecx = ex;
     wk.ecy = ey;
