@@ -107,7 +107,8 @@ struct Walk {
 // point's neighbours (stored with the mesh), so that per neighbour only dZ, e,
 // |e|_1, q and eq are formed, and only the two smallest lower bounds and the
 // leader's record are kept; the leader's upper bound and forward test, and the
-// winner's own de for the next step, are formed again from its record.  Returns the next point (-1: the half-ray ends; -2: undecided); when it
+// winner's own de for the next step, are formed again from its record.
+// Returns the next point (-1: the half-ray ends; -2: undecided); when it
 // decides a next point it moves the walk's lateral offset to it.
 __device__ __forceinline__ int32_t step_screen(const DevMesh &m, Walk &wk) {
     const int32_t c = wk.c;
