@@ -12,7 +12,8 @@
 // library holds its 64 MiB until the process exits.  Host code cannot use the
 // variable's name as a device address; the first call on each device looks
 // the address up with cudaGetSymbolAddress (with that device current) and
-// caches it.  Every call shares the array and leaves the previous call's
+// caches it, so that first call should come before any stream capture.  Every
+// call shares the array and leaves the previous call's
 // contents in it; calls that overlap on the GPU (different streams, or several
 // contexts on one device) race on it.
 #include <algorithm>
