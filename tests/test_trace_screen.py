@@ -143,6 +143,20 @@ def test_screen_certifies_only_exact_steps_on_clouds(orc, shift, ratio):
     assert cert > ratio * und  # the screen decides most steps of a generic cloud
 
 
+def test_screen_certifies_only_exact_steps_on_the_wind(orc):
+    # element sizes growing a hundredfold from the star outwards
+    import synth
+
+    m = synth.wind_model(1500, seed=9, n_freq=3)
+    pos, off, nbr = m["pos"], np.asarray(m["nbr_off"]), np.asarray(m["nbr_idx"], np.int32)
+    om = _model(orc, pos, off, nbr)
+    r = np.linalg.norm(pos, axis=1)
+    origins = [int(np.argmin(r)), int(np.argmax(r))] + list(np.random.default_rng(2).choice(len(pos), 6, replace=False))
+    cert, und, wrong = check_walks(om, pos, off, nbr, origins, _healpix_dirs(orc, 2))
+    assert wrong == 0
+    assert cert > 10 * und
+
+
 def test_screen_leaves_lattice_ties_undecided(orc):
     import synth
 
