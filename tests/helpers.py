@@ -24,3 +24,13 @@ def line_model(vel_a, vel_b, dv=1.0):
     return dict(pos=pos, vel=vel, nbr_off=off, nbr_idx=nbr, nu0=np.array([1e11]), chi0=one,
                 eta0=one, dvw=np.full(3, dv), chi_c=np.full(3, 1e-3), eta_c=np.full(3, 1e-3),
                 n_freq=3, x_span=2.0, l_min=0, l_max=0)
+
+
+def oracle_model_of(orc, pos, off, nbr):
+    """An oracle model of a bare mesh (one static line of unit data, no ray set),
+    for tracing only."""
+    n = len(pos)
+    m = dict(pos=pos, vel=np.zeros((n, 3)), nbr_off=off, nbr_idx=nbr, nu0=np.array([1.0]), chi0=np.ones((n, 1)),
+             eta0=np.ones((n, 1)), dvw=np.ones(n), chi_c=np.ones(n), eta_c=np.ones(n), n_freq=1, x_span=0.0,
+             l_min=0, l_max=0)
+    return orc.OracleModel(m, rays=np.zeros((n, 6), np.uint32))

@@ -15,6 +15,8 @@ the unit roundoff the bounds take.  CPU only."""
 import numpy as np
 import pytest
 
+from helpers import oracle_model_of as _model
+
 f32 = np.float32
 U = f32(2.0 ** -24)
 INF = f32(np.inf)
@@ -113,14 +115,6 @@ def check_walks(orc_model, pos, off, nbr, origins, dirs, margins=True):
                         break
                 c, e_c, eec = exact, e_n, eec_n
     return certified, undecided, wrong
-
-
-def _model(orc, pos, off, nbr):
-    n = len(pos)
-    m = dict(pos=pos, vel=np.zeros((n, 3)), nbr_off=off, nbr_idx=nbr, nu0=np.array([1.0]), chi0=np.ones((n, 1)),
-             eta0=np.ones((n, 1)), dvw=np.ones(n), chi_c=np.ones(n), eta_c=np.ones(n), n_freq=1, x_span=0.0,
-             l_min=0, l_max=0)
-    return orc.OracleModel(m, rays=np.zeros((n, 6), np.uint32))
 
 
 def _healpix_dirs(orc, l):
