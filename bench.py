@@ -60,6 +60,11 @@ def max_over_ranks(t: float, ws: int, device=None) -> float:
     return float(tt.item())
 
 
+# a rank that fails or never arrives ends the others' next collective with an
+# error after this long, instead of leaving them waiting
+PG_TIMEOUT_S = 600
+
+
 def job_throughput(ws: int, units_per_rank_step: float, steps: int, t_max: float) -> float:
     """Whole-job throughput: every rank's units over the slowest rank's time."""
     return ws * units_per_rank_step * steps / t_max
@@ -205,7 +210,10 @@ def run_mgx(args):
     if ws > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        import datetime
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local),
+                                timeout=datetime.timedelta(seconds=PG_TIMEOUT_S))
     torch.cuda.set_device(local)
     mgx.build()
     m = make_workload()

@@ -67,3 +67,49 @@ def test_single_rank_defaults(monkeypatch):
     assert bench.dist_env() == (1, 0, 0)
     assert bench.max_over_ranks(3.0, 1) == 3.0
     assert bench.job_throughput(1, 10.0, 3, 2.0) == 15.0
+
+
+def _failing_rank_main(rank, ws, port, out_dir):
+    import datetime
+
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=ws,
+                            timeout=datetime.timedelta(seconds=30))
+    if rank == 1:
+        os._exit(3)  # a replica that dies between steps, with nothing of it in flight
+    try:
+        bench.max_over_ranks(1.0, ws)
+        outcome = "returned"
+    except Exception as e:  # the surviving rank learns of it from its next collective
+        outcome = "error: " + type(e).__name__
+    with open(os.path.join(out_dir, f"r{rank}.txt"), "w") as f:
+        f.write(outcome)
+
+
+def test_a_failed_rank_ends_the_others_collective(tmp_path):
+    # host-side failure detection: the timing reduction of a rank whose peer has
+    # died raises within the process-group timeout instead of waiting forever
+    pytest.importorskip("torch")
+    import multiprocessing as mp
+    import time
+
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    alive = [p.is_alive() for p in procs]
+    for p in procs:
+        if p.is_alive():
+            p.kill()
+    assert not any(alive)
+    assert procs[1].exitcode == 3
+    assert (tmp_path / "r0.txt").read_text().startswith("error")
+    assert time.time() - t0 < 120
