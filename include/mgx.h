@@ -84,10 +84,12 @@ typedef struct {
 } mgx_solve_params;
 
 /* Create a context on CUDA device `device`, enqueuing on `stream` (a cudaStream_t;
- * NULL selects the legacy default stream). */
+ * NULL selects the legacy default stream).  Library lifecycle: no counterpart in
+ * the paper. */
 mgx_status mgx_create(int device, void *stream, mgx_ctx **out);
 
-/* Release the context and every model in it.  NULL is allowed. */
+/* Release the context and every model in it.  NULL is allowed.  Library
+ * lifecycle: no counterpart in the paper. */
 void mgx_destroy(mgx_ctx *ctx);
 
 /* Message of the last failing call on this context ("" if none).  The pointer
@@ -251,7 +253,8 @@ enum {
 };
 
 /* Mean intensity of several models in one launch (the batched form of
- * mgx_solve_J, same results).  All models' half-rays are traced together into
+ * mgx_solve_J, Eqs. 1-3 of Section 2.1, same results; the batching itself has no
+ * counterpart in the paper).  All models' half-rays are traced together into
  * fixed-width rows (the width chosen from the length distribution when the
  * call plans) plus a packed overflow for the longer ones; each (model, origin,
  * frequency tile) item's cost is the number of points on its traced lines,
@@ -296,7 +299,8 @@ typedef struct {
 } mgx_tuning;
 
 /* Set (NULL: reset to automatic) or read the context's tuning; out-of-range
- * fields give MGX_EINVAL.  Setting it drops a planned batch. */
+ * fields give MGX_EINVAL.  Setting it drops a planned batch.  Launch tuning of
+ * the batched solve: no counterpart in the paper. */
 mgx_status mgx_set_tuning(mgx_ctx *ctx, const mgx_tuning *tuning);
 mgx_status mgx_get_tuning(mgx_ctx *ctx, mgx_tuning *tuning);
 
@@ -306,7 +310,7 @@ typedef struct {
     double step_ms; /* median device time of one step (CUDA events on the context's stream) */
 } mgx_tune_trial;
 
-/* Autotuner of the batched solve: times candidate tunings of
+/* Autotuner of the batched solve (no counterpart in the paper): times candidate tunings of
  * mgx_solve_J_batch(ctx, models, n_models, params, J_out, flags) by coordinate
  * descent (bins per lane 1/2 in single precision, tracer CTAs per SM 4/6/8,
  * tail share 5/20/80 per mille, work-list schedule 0/1), each candidate planned once and then run
@@ -356,12 +360,15 @@ mgx_status mgx_solve_J_noalloc(mgx_ctx *ctx, int32_t model, const mgx_solve_para
 mgx_status mgx_mlp_set_params(mgx_ctx *ctx, const float *theta);
 /* Copy the current parameters to the host. */
 mgx_status mgx_mlp_get_params(mgx_ctx *ctx, float *theta);
-/* y [n] = network(X [n][8]) (host arrays). */
+/* y [n] = network(X [n][8]) (host arrays): the learned reduction's network,
+ * which the paper does not have. */
 mgx_status mgx_mlp_forward(mgx_ctx *ctx, const float *X, int64_t n, float *y);
-/* Gradient of the mean squared error over all n rows (one batch), host
+/* Training of the learned reduction's network (no counterpart in the paper).
+ * Gradient of the mean squared error over all n rows (one batch), host
  * [MGX_MLP_NPARAM]; *loss (may be NULL) receives the loss.  No update. */
 mgx_status mgx_mlp_grad(mgx_ctx *ctx, const float *X, const float *t, int64_t n, float *grad, float *loss);
-/* Adam training for `epochs` passes in shuffled mini-batches of `batch` rows
+/* Training of the learned reduction's network (no counterpart in the paper):
+ * Adam for `epochs` passes in shuffled mini-batches of `batch` rows
  * (shuffles from SplitMix64 seeded with `seed`); loss_per_epoch [epochs]
  * (may be NULL) receives each epoch's mean loss. */
 mgx_status mgx_mlp_train(mgx_ctx *ctx, const float *X, const float *t, int64_t n, int32_t epochs, int32_t batch,

@@ -60,3 +60,20 @@ def test_healpix_host_exports_match_oracle(orc):
         mgx.mgx_antipode(9, 0)
     with pytest.raises(ValueError):
         mgx.mgx_pix2vec(1, 48)
+
+
+def test_every_declaration_cites_its_passage():
+    # each entry point's comment (or its group's, within the last three comment
+    # blocks) names the passage of the paper it implements, or says it has none
+    import re
+
+    txt = open(os.path.join(ROOT, "include", "mgx.h")).read()
+    comments = [(m.end(), m.group(0)) for m in re.finditer(r"/\*.*?\*/", txt, flags=re.S)]
+    cite = re.compile(r"Section|Eqs?\.|Fig\.|Table|no counterpart|paper does not|paper has no|Gorski")
+    decl = re.compile(r"^(?:mgx_status|int64_t|int32_t|void|const char \*|double)\s+(mgx_\w+)\s*\(", re.M)
+    names = []
+    for m in decl.finditer(txt):
+        before = [c for end, c in comments if end <= m.start()][-3:]
+        if not any(cite.search(c) for c in before):
+            names.append(m.group(1))
+    assert names == [], names
